@@ -1,0 +1,189 @@
+/*
+ * cggm.h — C ABI of the GB300 solver for l1-regularised conditional Gaussian graphical
+ * models by alternating Newton coordinate descent (McCarter & Kim, "Large-Scale
+ * Optimization Algorithms for Sparse Conditional Gaussian Graphical Models", AISTATS 2016).
+ *
+ * The problem (Eq. 1):
+ *     min_{Lambda > 0, Theta}  -log|Lambda| + tr(S_yy Lambda + 2 S_xy^T Theta
+ *                               + Lambda^-1 Theta^T S_xx Theta)
+ *                               + lam_L ||Lambda||_1 + lam_T ||Theta||_1
+ * with S_xx = X^T X / n, S_xy = X^T Y / n, S_yy = Y^T Y / n (Section 2.1); Lambda is q x q
+ * (the output network), Theta is p x q (inputs to outputs).
+ *
+ * Conventions for every entry point below:
+ *  - Matrices are dense and row-major.  X is n x p (one sample per row), Y is n x q,
+ *    Lambda is q x q, Theta is p x q.
+ *  - A data pointer may be host or device memory; the library tells them apart with
+ *    cudaPointerGetAttributes.  Host inputs are copied to the device inside the call;
+ *    host outputs are copied back before the call returns.  The caller owns every
+ *    buffer it passes and the library never frees or retains them.
+ *  - Every call runs on the context's device and stream and returns only after its
+ *    results are complete (host-visible for host outputs, stream-ordered and synchronised
+ *    for device outputs).
+ *  - The return code is the only error channel; no call aborts the process.  On error
+ *    the outputs are unspecified and the context stays usable.
+ *  - A context is not thread-safe: one call at a time per context.
+ */
+#ifndef CGGM_H
+#define CGGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CGGM_OK = 0,
+    CGGM_EINVAL = -1,      /* bad shape, negative lambda, tol <= 0, null pointer        */
+    CGGM_ENOTPD = -2,      /* Lambda (warm start or argument) is not positive definite  */
+    CGGM_ENOMEM = -3,      /* device allocation failed                                  */
+    CGGM_EMAXITER = -4,    /* max_iter reached before the stopping rule held            */
+    CGGM_ELINESEARCH = -5, /* Armijo found no step within ls_max_trials                 */
+    CGGM_ECUDA = -6,       /* a CUDA runtime call failed                                */
+    CGGM_ETIMEDOUT = -7,   /* a device-side wait gave up (grid barrier deadline)        */
+    CGGM_ENONFINITE = -8,  /* NaN or Inf in the inputs or in a computed quantity        */
+    CGGM_ECANCELLED = -9   /* the request was cancelled                                 */
+} cggm_status;
+
+typedef enum {
+    CGGM_FP64 = 0,  /* every kernel in double precision                                */
+    CGGM_MIXED = 1  /* contractions and sweep state in single precision (tensor cores   */
+                    /* for the products from X); Cholesky, log det, objective, Sigma    */
+                    /* and Psi diagonals and coordinate coefficients in double          */
+} cggm_precision;
+
+typedef enum { CGGM_F32 = 0, CGGM_F64 = 1 } cggm_dtype;
+
+typedef struct {
+    double tol;          /* stopping ratio of Section 5.1: stop when
+                            ||grad^S f||_1 < tol (||Lambda||_1 + ||Theta||_1); 0.01      */
+    int max_iter;        /* Newton iterations (Algorithm 1 outer loop); 1000              */
+    int precision;       /* cggm_precision; CGGM_MIXED                                    */
+    double ls_sigma;     /* Armijo sufficient-decrease constant; 1e-3                     */
+    double ls_beta;      /* Armijo step shrink factor; 0.5                                */
+    int ls_max_trials;   /* Armijo trials before CGGM_ELINESEARCH; 50                     */
+    int penalize_diag;   /* include diag(Lambda) in ||Lambda||_1; 1                       */
+    int sweep_batch;     /* coordinates per blocked Gauss-Seidel batch, 0 = default      */
+    double target_f;     /* also stop once f <= target_f (time-to-gap runs); -inf = off  */
+    int verbose;         /* per-iteration line on stderr                                  */
+} cggm_opts;
+
+typedef struct {
+    int iterations;         /* Newton iterations run                                     */
+    int converged;          /* stopping rule (or target_f) satisfied                     */
+    double f;               /* objective (Eq. 1) at the returned point, double precision */
+    double subgrad;         /* ||grad^S f||_1 at the returned point                      */
+    double l1norm;          /* ||Lambda||_1 + ||Theta||_1 at the returned point          */
+    int64_t m_lambda;       /* last active-set sizes                                     */
+    int64_t m_theta;
+    int ls_trials;          /* Armijo trials summed over iterations                      */
+    double seconds;         /* device time of the solve (CUDA events)                    */
+    double sec_products;    /* R, P, Psi, gradients                                      */
+    double sec_factor;      /* Cholesky, log det, Sigma                                  */
+    double sec_active;      /* subgradient, active sets                                  */
+    double sec_sweep_lambda;
+    double sec_linesearch;
+    double sec_sweep_theta;
+} cggm_info;
+
+typedef struct cggm_ctx cggm_ctx;
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream` (a
+ * cudaStream_t, or NULL for a stream owned by the context).  Allocates nothing large
+ * until the first call that needs workspace.  Returns CGGM_EINVAL for a bad device. */
+cggm_status cggm_create(cggm_ctx **ctx, int device, void *cuda_stream);
+
+/* Release the context and all device workspace it owns.  NULL is ignored. */
+void cggm_destroy(cggm_ctx *ctx);
+
+/* Fill `opts` with the defaults listed beside each field. */
+void cggm_opts_default(cggm_opts *opts);
+
+/* Short English name of a status code (static storage). */
+const char *cggm_status_string(int status);
+
+/*
+ * Solve Eq. 1 by alternating Newton coordinate descent (Algorithm 1): Theta <- 0,
+ * Lambda <- I (or the warm start); each iteration computes Sigma = Lambda^-1 by Cholesky,
+ * Psi, the gradients (Eq. 3), the stopping ratio and the active sets (Section 2.2), one
+ * coordinate-descent pass for the Newton direction of Lambda (Section 3.1, Eq. 7), an
+ * Armijo step on Lambda, and one coordinate-descent pass on Theta (Section 3.2, Eq. 8).
+ *
+ * X: n x p, dtype xdtype; Y: n x q, dtype ydtype.  lam_L, lam_T >= 0.  tol > 0 overrides
+ * opts->tol.  warm_Lambda (q x q, symmetric positive definite) and warm_Theta (p x q)
+ * are double, may be NULL (then I and 0).  Lambda_out (q x q) and Theta_out (p x q)
+ * receive the solution in double.  info may be NULL.  opts may be NULL (defaults).
+ * Returns CGGM_OK when the stopping rule held, CGGM_EMAXITER when max_iter ran out (the
+ * outputs then hold the last iterate), or an error.
+ */
+cggm_status cggm_solve(cggm_ctx *ctx, const void *X, int xdtype, const void *Y, int ydtype,
+                       int64_t n, int64_t p, int64_t q, double lam_L, double lam_T,
+                       double tol, const double *warm_Lambda, const double *warm_Theta,
+                       const cggm_opts *opts, double *Lambda_out, double *Theta_out,
+                       cggm_info *info);
+
+/*
+ * f(Lambda, Theta) of Eq. 1 in double precision on the device.  Lambda must be positive
+ * definite (CGGM_ENOTPD otherwise).  penalize_diag as in cggm_opts.
+ */
+cggm_status cggm_objective(cggm_ctx *ctx, const void *X, int xdtype, const void *Y,
+                           int ydtype, int64_t n, int64_t p, int64_t q,
+                           const double *Lambda, const double *Theta, double lam_L,
+                           double lam_T, int penalize_diag, double *f_out);
+
+/*
+ * Gradients of the smooth part (Eq. 3) in double precision:
+ *     G_Lambda = S_yy - Sigma - Psi (q x q),  G_Theta = 2 S_xy + 2 S_xx Theta Sigma (p x q),
+ * computed from X as (2/n) X^T (Y + X Theta Sigma), so S_xx is never formed.
+ */
+cggm_status cggm_grad(cggm_ctx *ctx, const void *X, int xdtype, const void *Y, int ydtype,
+                      int64_t n, int64_t p, int64_t q, const double *Lambda,
+                      const double *Theta, double *G_Lambda, double *G_Theta);
+
+/*
+ * Step-level entry points: one kernel of the Newton iteration each, on caller data, so
+ * that every step can be checked on its own.  All matrices double, host or device.
+ */
+
+/* Cholesky Lambda = L L^T (lower L, row-major q x q, upper part of L_out set to 0),
+ * log|Lambda| = 2 sum log L_ii, and Sigma = Lambda^-1 (Section 2.3's Cholesky
+ * initialisation of Sigma).  Sigma_out may be NULL.  CGGM_ENOTPD if not positive
+ * definite. */
+cggm_status cggm_cholesky(cggm_ctx *ctx, int64_t q, const double *Lambda, double *L_out,
+                          double *logdet_out, double *Sigma_out, int precision);
+
+/* One coordinate-descent pass for the Newton direction of Lambda (Section 3.1, Eq. 7;
+ * coordinate step of Appendix A.1 with the curvature of the exact quadratic model).
+ * (ai[k], aj[k]), ai <= aj, k < m, are the active coordinates in visiting order.
+ * D_out (q x q) receives the symmetric direction. */
+cggm_status cggm_lambda_sweep(cggm_ctx *ctx, int64_t q, const double *Sigma,
+                              const double *Psi, const double *Syy, const double *Lambda,
+                              int64_t m, const int32_t *ai, const int32_t *aj, double lam_L,
+                              int penalize_diag, int precision, double *D_out);
+
+/* One coordinate-descent pass on Theta with Lambda fixed (Section 3.2, Eq. 8; Appendix
+ * A.1 coordinate step with curvature 2 Sigma_jj (S_xx)_ii).  X is n x p (double), S_xy
+ * p x q, Sigma q x q; (ti[k], tj[k]) the active coordinates in visiting order.  Theta
+ * (p x q) is read from Theta_in and the result written to Theta_out (may alias). */
+cggm_status cggm_theta_sweep(cggm_ctx *ctx, int64_t n, int64_t p, int64_t q,
+                             const double *X, const double *Sxy, const double *Sigma,
+                             const double *Theta_in, int64_t m, const int32_t *ti,
+                             const int32_t *tj, double lam_T, int precision,
+                             double *Theta_out);
+
+/* Active sets of Section 2.2 from gradients and parameters: Lambda entries (i <= j) with
+ * |G_Lambda| > lam_L or Lambda != 0, Theta entries with |G_Theta| > lam_T or Theta != 0,
+ * both in row-major order.  The index buffers must hold q(q+1)/2 and p q entries; the
+ * counts are returned in *m_lambda and *m_theta. */
+cggm_status cggm_active_sets(cggm_ctx *ctx, int64_t p, int64_t q, const double *G_Lambda,
+                             const double *G_Theta, const double *Lambda,
+                             const double *Theta, double lam_L, double lam_T,
+                             int penalize_diag, int32_t *li, int32_t *lj, int64_t *m_lambda,
+                             int32_t *ti, int32_t *tj, int64_t *m_theta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CGGM_H */

@@ -1,0 +1,23 @@
+"""GB300 (sm_103a) solver for l1-regularised conditional Gaussian graphical models by
+alternating Newton coordinate descent (McCarter & Kim, AISTATS 2016, Algorithm 1).
+
+The compute path is the CUDA library ``libcggm.so`` (C ABI in include/cggm.h); this
+package is its Python binding.  Build it with ``paper_1509_04681_gb300.build.build()``.
+"""
+from .cggm import (  # noqa: F401
+    Context,
+    CGGMError,
+    cggm_opts,
+    cggm_info,
+    make_opts,
+    opts_default,
+    LIB_PATH,
+    EXPORTED,
+    CGGM_FP64,
+    CGGM_MIXED,
+    CGGM_OK,
+    CGGM_EMAXITER,
+    CGGM_ENOTPD,
+    CGGM_EINVAL,
+    CGGM_ELINESEARCH,
+)

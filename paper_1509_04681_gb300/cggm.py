@@ -1,0 +1,287 @@
+"""Thin ctypes binding of libcggm.so (include/cggm.h), argument marshalling only.
+
+Every function here forwards to the C entry point of the same name; all arithmetic of
+the solver runs in the CUDA kernels of the library.  Arrays may be numpy arrays (host)
+or torch tensors (host or CUDA device); outputs are numpy arrays unless ``out=``
+tensors are given.  There is no CPU fallback: without the compiled library the import
+of this module fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcggm.so")
+
+CGGM_OK, CGGM_EINVAL, CGGM_ENOTPD, CGGM_ENOMEM, CGGM_EMAXITER = 0, -1, -2, -3, -4
+CGGM_ELINESEARCH, CGGM_ECUDA, CGGM_ETIMEDOUT, CGGM_ENONFINITE, CGGM_ECANCELLED = -5, -6, -7, -8, -9
+CGGM_FP64, CGGM_MIXED = 0, 1
+CGGM_F32, CGGM_F64 = 0, 1
+
+EXPORTED = [
+    "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
+    "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
+    "cggm_active_sets",
+]
+
+
+class cggm_opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("ls_sigma", ctypes.c_double), ("ls_beta", ctypes.c_double),
+                ("ls_max_trials", ctypes.c_int), ("penalize_diag", ctypes.c_int),
+                ("sweep_batch", ctypes.c_int), ("target_f", ctypes.c_double),
+                ("verbose", ctypes.c_int)]
+
+
+class cggm_info(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("f", ctypes.c_double),
+                ("subgrad", ctypes.c_double), ("l1norm", ctypes.c_double),
+                ("m_lambda", ctypes.c_int64), ("m_theta", ctypes.c_int64),
+                ("ls_trials", ctypes.c_int), ("seconds", ctypes.c_double),
+                ("sec_products", ctypes.c_double), ("sec_factor", ctypes.c_double),
+                ("sec_active", ctypes.c_double), ("sec_sweep_lambda", ctypes.c_double),
+                ("sec_linesearch", ctypes.c_double), ("sec_sweep_theta", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class CGGMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_lib().cggm_status_string(status).decode()} ({status})")
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (nvcc, sm_103a)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, dbl, ip = ctypes.c_void_p, ctypes.c_int64, ctypes.c_double, ctypes.c_int
+        lib.cggm_create.argtypes = [ctypes.POINTER(vp), ip, vp]
+        lib.cggm_destroy.argtypes = [vp]
+        lib.cggm_destroy.restype = None
+        lib.cggm_opts_default.argtypes = [ctypes.POINTER(cggm_opts)]
+        lib.cggm_opts_default.restype = None
+        lib.cggm_status_string.argtypes = [ip]
+        lib.cggm_status_string.restype = ctypes.c_char_p
+        lib.cggm_solve.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, dbl, dbl, dbl, vp, vp,
+                                   ctypes.POINTER(cggm_opts), vp, vp, ctypes.POINTER(cggm_info)]
+        lib.cggm_objective.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, dbl, dbl, ip,
+                                       ctypes.POINTER(dbl)]
+        lib.cggm_grad.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, vp, vp]
+        lib.cggm_cholesky.argtypes = [vp, i64, vp, vp, ctypes.POINTER(dbl), vp, ip]
+        lib.cggm_lambda_sweep.argtypes = [vp, i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, ip, vp]
+        lib.cggm_theta_sweep.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp]
+        lib.cggm_active_sets.argtypes = [vp, i64, i64, vp, vp, vp, vp, dbl, dbl, ip, vp, vp,
+                                         ctypes.POINTER(i64), vp, vp, ctypes.POINTER(i64)]
+        for name in EXPORTED:
+            f = getattr(lib, name)
+            if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
+                                                     "cggm_grad", "cggm_cholesky",
+                                                     "cggm_lambda_sweep", "cggm_theta_sweep",
+                                                     "cggm_active_sets"):
+                f.restype = ctypes.c_int
+        _LIB = lib
+    return _LIB
+
+
+def _check(status: int, where: str, allow=(CGGM_OK,)):
+    if status not in allow:
+        raise CGGMError(status, where)
+    return status
+
+
+class _Arr:
+    """Keeps a contiguous array alive and exposes its address (host numpy or torch)."""
+
+    def __init__(self, a, dtype):
+        self.obj = None
+        try:
+            import torch
+            if isinstance(a, torch.Tensor):
+                tdt = {np.float64: torch.float64, np.float32: torch.float32,
+                       np.int32: torch.int32}[np.dtype(dtype).type]
+                t = a.to(dtype=tdt).contiguous()
+                self.obj = t
+                self.ptr = t.data_ptr()
+                return
+        except ImportError:
+            pass
+        arr = np.ascontiguousarray(a, dtype=dtype)
+        self.obj = arr
+        self.ptr = arr.ctypes.data
+
+
+def _x_dtype(a):
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            return (np.float32, CGGM_F32) if a.dtype == torch.float32 else (np.float64, CGGM_F64)
+    except ImportError:
+        pass
+    return (np.float32, CGGM_F32) if np.asarray(a).dtype == np.float32 else (np.float64, CGGM_F64)
+
+
+def opts_default() -> cggm_opts:
+    o = cggm_opts()
+    _lib().cggm_opts_default(ctypes.byref(o))
+    return o
+
+
+@dataclasses.dataclass
+class SolveResult:
+    Lambda: object
+    Theta: object
+    info: dict
+    status: int
+
+
+class Context:
+    """Owns a cggm_ctx (device workspace + stream)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        h = ctypes.c_void_p()
+        _check(_lib().cggm_create(ctypes.byref(h), int(device), ctypes.c_void_p(stream or 0)),
+               "cggm_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().cggm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- cggm_solve --------------------------------------------------------------------
+    def cggm_solve(self, X, Y, lam_L, lam_T, tol=0.0, warm_Lambda=None, warm_Theta=None,
+                   opts: Optional[cggm_opts] = None, Lambda_out=None, Theta_out=None,
+                   allow_maxiter=True) -> SolveResult:
+        n, p = X.shape
+        q = Y.shape[1]
+        xd, xt = _x_dtype(X)
+        yd, yt = _x_dtype(Y)
+        Xa, Ya = _Arr(X, xd), _Arr(Y, yd)
+        wl = _Arr(warm_Lambda, np.float64) if warm_Lambda is not None else None
+        wt = _Arr(warm_Theta, np.float64) if warm_Theta is not None else None
+        Lo = Lambda_out if Lambda_out is not None else np.empty((q, q))
+        To = Theta_out if Theta_out is not None else np.empty((p, q))
+        La, Ta = _Arr(Lo, np.float64), _Arr(To, np.float64)
+        info = cggm_info()
+        o = opts if opts is not None else opts_default()
+        st = _lib().cggm_solve(self._h, Xa.ptr, xt, Ya.ptr, yt, n, p, q, float(lam_L),
+                               float(lam_T), float(tol), wl.ptr if wl else None,
+                               wt.ptr if wt else None, ctypes.byref(o), La.ptr, Ta.ptr,
+                               ctypes.byref(info))
+        _check(st, "cggm_solve", (CGGM_OK, CGGM_EMAXITER) if allow_maxiter else (CGGM_OK,))
+        return SolveResult(Lambda=La.obj if Lambda_out is None else Lambda_out,
+                           Theta=Ta.obj if Theta_out is None else Theta_out,
+                           info=info.as_dict(), status=st)
+
+    def cggm_objective(self, X, Y, Lam, Th, lam_L, lam_T, penalize_diag=True) -> float:
+        n, p = X.shape
+        q = Y.shape[1]
+        xd, xt = _x_dtype(X)
+        yd, yt = _x_dtype(Y)
+        Xa, Ya = _Arr(X, xd), _Arr(Y, yd)
+        La, Ta = _Arr(Lam, np.float64), _Arr(Th, np.float64)
+        f = ctypes.c_double()
+        _check(_lib().cggm_objective(self._h, Xa.ptr, xt, Ya.ptr, yt, n, p, q, La.ptr, Ta.ptr,
+                                     float(lam_L), float(lam_T), int(bool(penalize_diag)),
+                                     ctypes.byref(f)), "cggm_objective")
+        return f.value
+
+    def cggm_grad(self, X, Y, Lam, Th):
+        n, p = X.shape
+        q = Y.shape[1]
+        xd, xt = _x_dtype(X)
+        yd, yt = _x_dtype(Y)
+        Xa, Ya = _Arr(X, xd), _Arr(Y, yd)
+        La, Ta = _Arr(Lam, np.float64), _Arr(Th, np.float64)
+        GL, GT = np.empty((q, q)), np.empty((p, q))
+        _check(_lib().cggm_grad(self._h, Xa.ptr, xt, Ya.ptr, yt, n, p, q, La.ptr, Ta.ptr,
+                                GL.ctypes.data, GT.ctypes.data), "cggm_grad")
+        return GL, GT
+
+    def cggm_cholesky(self, Lam, want_sigma=True):
+        q = Lam.shape[0]
+        La = _Arr(Lam, np.float64)
+        L = np.empty((q, q))
+        S = np.empty((q, q)) if want_sigma else None
+        ld = ctypes.c_double()
+        _check(_lib().cggm_cholesky(self._h, q, La.ptr, L.ctypes.data, ctypes.byref(ld),
+                                    S.ctypes.data if S is not None else None, CGGM_FP64),
+               "cggm_cholesky")
+        return L, ld.value, S
+
+    def cggm_lambda_sweep(self, Sigma, Psi, Syy, Lam, ai, aj, lam_L, penalize_diag=True,
+                          precision=CGGM_FP64):
+        q = Lam.shape[0]
+        args = [_Arr(a, np.float64) for a in (Sigma, Psi, Syy, Lam)]
+        ia, ja = _Arr(ai, np.int32), _Arr(aj, np.int32)
+        m = len(ai)
+        D = np.empty((q, q))
+        _check(_lib().cggm_lambda_sweep(self._h, q, *[a.ptr for a in args], m,
+                                        ia.ptr if m else None, ja.ptr if m else None,
+                                        float(lam_L), int(bool(penalize_diag)), int(precision),
+                                        D.ctypes.data), "cggm_lambda_sweep")
+        return D
+
+    def cggm_theta_sweep(self, X, Sxy, Sigma, Theta, ti, tj, lam_T, precision=CGGM_FP64):
+        n, p = X.shape
+        q = Sigma.shape[0]
+        Xa, Sa, Sg, Ta = (_Arr(a, np.float64) for a in (X, Sxy, Sigma, Theta))
+        ia, ja = _Arr(ti, np.int32), _Arr(tj, np.int32)
+        m = len(ti)
+        out = np.empty((p, q))
+        _check(_lib().cggm_theta_sweep(self._h, n, p, q, Xa.ptr, Sa.ptr, Sg.ptr, Ta.ptr, m,
+                                       ia.ptr if m else None, ja.ptr if m else None,
+                                       float(lam_T), int(precision), out.ctypes.data),
+               "cggm_theta_sweep")
+        return out
+
+    def cggm_active_sets(self, G_L, G_T, Lam, Th, lam_L, lam_T, penalize_diag=True):
+        q = Lam.shape[0]
+        p = Th.shape[0]
+        a = [_Arr(x, np.float64) for x in (G_L, G_T, Lam, Th)]
+        li = np.empty(q * (q + 1) // 2, dtype=np.int32)
+        lj = np.empty_like(li)
+        ti = np.empty(p * q, dtype=np.int32)
+        tj = np.empty_like(ti)
+        mL, mT = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib().cggm_active_sets(self._h, p, q, *[x.ptr for x in a], float(lam_L),
+                                       float(lam_T), int(bool(penalize_diag)), li.ctypes.data,
+                                       lj.ctypes.data, ctypes.byref(mL), ti.ctypes.data,
+                                       tj.ctypes.data, ctypes.byref(mT)), "cggm_active_sets")
+        return li[:mL.value], lj[:mL.value], ti[:mT.value], tj[:mT.value]
+
+
+def make_opts(**kw) -> cggm_opts:
+    o = opts_default()
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": CGGM_FP64, "mixed": CGGM_MIXED}[v]
+        if v is None and k == "target_f":
+            v = -math.inf
+        setattr(o, k, v)
+    return o

@@ -1,0 +1,901 @@
+// C ABI of the CGGM solver (include/cggm.h): context, the Newton-iteration driver of
+// Algorithm 1, and the step-level entry points.  Host code only issues kernels; every
+// arithmetic step of the solve runs on the device.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "chol.cuh"
+#include "common.cuh"
+#include "dense.cuh"
+#include "iter.cuh"
+#include "sweeps.cuh"
+
+using namespace cggm;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+cggm_status ensure(Buf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return CGGM_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return e == cudaErrorMemoryAllocation ? CGGM_ENOMEM : CGGM_ECUDA;
+    }
+    b.bytes = bytes;
+    return CGGM_OK;
+}
+
+template <typename T>
+T *P(Buf &b) { return reinterpret_cast<T *>(b.p); }
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct cggm_ctx {
+    int device = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    // data
+    Buf stage, Xt, Yt, Xt_f, Syy, Sxy, Sxx, Xd;
+    // parameters and factorisations
+    Buf Lam, Th, Lch, logd, Sig, Sig_f, Sd, Lam_a, Lch_a, logd_a, work;
+    // products and gradients
+    Buf Rt, Pt, Z, Psi, Pd, GL, GT, W;
+    // coordinate passes
+    Buf D, U, dV, li, lj, ti, tj, rowcnt;
+    // scalars
+    Buf scal, cnt, err;
+    Buf partial;
+    BatchPlan planL, planT;
+    SweepScratch scr;
+    cudaEvent_t ev[8];
+    bool events = false;
+};
+
+namespace {
+
+// scalar slots in ctx->scal (double)
+enum {
+    S_LOGDET = 0, S_SYYL, S_SXYT, S_TRACE, S_L1L, S_L1T, S_SUBL, S_NRML, S_SUBT, S_NRMT,
+    S_GD, S_L1LD, S_LOGDET_A, S_TRACE_A, S_SYYL_A, S_L1L_A, S_COUNT
+};
+
+cggm_status sync_err(cggm_ctx *c) {
+    CGGM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    CGGM_CUDA_TRY(cudaGetLastError());
+    return CGGM_OK;
+}
+
+cggm_status read_dev_err(cggm_ctx *c, int *out) {
+    CGGM_CUDA_TRY(cudaMemcpyAsync(out, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    CGGM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    return CGGM_OK;
+}
+
+// Copy a row-major rows x cols matrix of dtype dt (host or device) into a device double
+// matrix transposed (cols x rows).  Also optionally a float copy.
+cggm_status load_transposed(cggm_ctx *c, const void *src, int dt, int64_t rows, int64_t cols,
+                            Buf &dst, Buf *dst_f) {
+    const size_t esz = dt == CGGM_F64 ? 8 : 4;
+    const size_t bytes = esz * (size_t)rows * (size_t)cols;
+    const void *dsrc = src;
+    if (!is_device_ptr(src)) {
+        CGGM_TRY(ensure(c->stage, bytes));
+        CGGM_CUDA_TRY(cudaMemcpyAsync(c->stage.p, src, bytes, cudaMemcpyHostToDevice, c->st));
+        dsrc = c->stage.p;
+    }
+    CGGM_TRY(ensure(dst, 8 * (size_t)rows * cols));
+    if (dt == CGGM_F64)
+        transpose<double, double>(rows, cols, (const double *)dsrc, P<double>(dst), c->st);
+    else
+        transpose<float, double>(rows, cols, (const float *)dsrc, P<double>(dst), c->st);
+    if (dst_f) {
+        CGGM_TRY(ensure(*dst_f, 4 * (size_t)rows * cols));
+        convert_d2f(rows * cols, P<double>(dst), P<float>(*dst_f), c->st);
+    }
+    CGGM_CUDA_TRY(cudaGetLastError());
+    return CGGM_OK;
+}
+
+cggm_status load_double(cggm_ctx *c, const double *src, size_t count, Buf &dst) {
+    CGGM_TRY(ensure(dst, 8 * count));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(dst.p, src, 8 * count, cudaMemcpyDefault, c->st));
+    return CGGM_OK;
+}
+
+cggm_status store_double(cggm_ctx *c, double *dst, const void *src, size_t count) {
+    CGGM_CUDA_TRY(cudaMemcpyAsync(dst, src, 8 * count, cudaMemcpyDefault, c->st));
+    return CGGM_OK;
+}
+
+__global__ void set_identity(int64_t n, double *A) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
+         e += (int64_t)gridDim.x * blockDim.x)
+        A[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+// diag of (1/n) M M^T for M rows x n (row-major), double
+template <typename T>
+__global__ void rowsq_kernel(int64_t rows, int64_t n, const T *M, double inv_n, double *d) {
+    const int64_t r = blockIdx.x;
+    double s = 0.0;
+    for (int64_t k = threadIdx.x; k < n; k += blockDim.x) {
+        const double v = (double)M[r * n + k];
+        s += v * v;
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) d[r] = s * inv_n;
+}
+
+__global__ void finite_check_kernel(int64_t len, const double *x, int *err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite(x[e])) { atomicCAS(err, 0, (int)DEV_NONFINITE); return; }
+}
+
+unsigned gcap(int64_t len) {
+    int64_t g = (len + 255) / 256, cap = (int64_t)sm_count() * 16;
+    return (unsigned)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+struct Sizes {
+    int64_t n, p, q;
+};
+
+// ---------------------------------------------------------------------------------
+// The solver, templated on the storage type of the large caches and products
+// (double for CGGM_FP64, float for CGGM_MIXED).
+// ---------------------------------------------------------------------------------
+template <typename T>
+struct Solver {
+    cggm_ctx *c;
+    Sizes z;
+    cudaStream_t st;
+    double lamL, lamT, lamLd;  // lamLd: penalty on the diagonal
+    cggm_opts o;
+
+    double *scal() { return P<double>(c->scal); }
+
+    cggm_status alloc() {
+        const int64_t n = z.n, p = z.p, q = z.q;
+        const size_t qq = (size_t)q * q, pq = (size_t)p * q;
+        CGGM_TRY(ensure(c->Syy, 8 * qq));
+        CGGM_TRY(ensure(c->Sxy, 8 * pq));
+        CGGM_TRY(ensure(c->Sxx, sizeof(T) * (size_t)p * p));
+        CGGM_TRY(ensure(c->Xd, 8 * (size_t)p));
+        CGGM_TRY(ensure(c->Lam, 8 * qq));
+        CGGM_TRY(ensure(c->Th, 8 * pq));
+        CGGM_TRY(ensure(c->Lch, 8 * qq));
+        CGGM_TRY(ensure(c->logd, 8 * (size_t)q));
+        CGGM_TRY(ensure(c->Sig, 8 * qq));
+        CGGM_TRY(ensure(c->Sig_f, sizeof(T) * qq));
+        CGGM_TRY(ensure(c->Sd, 8 * (size_t)q));
+        CGGM_TRY(ensure(c->Lam_a, 8 * qq));
+        CGGM_TRY(ensure(c->Lch_a, 8 * qq));
+        CGGM_TRY(ensure(c->logd_a, 8 * (size_t)q));
+        CGGM_TRY(ensure(c->work, 8 * qq));
+        CGGM_TRY(ensure(c->Rt, 8 * (size_t)q * n));
+        CGGM_TRY(ensure(c->Pt, 8 * (size_t)q * n));
+        CGGM_TRY(ensure(c->Z, 8 * (size_t)q * n));
+        CGGM_TRY(ensure(c->Psi, sizeof(T) * qq));
+        CGGM_TRY(ensure(c->Pd, 8 * (size_t)q));
+        CGGM_TRY(ensure(c->GL, 8 * qq));
+        CGGM_TRY(ensure(c->GT, 8 * pq));
+        CGGM_TRY(ensure(c->W, 8 * pq));
+        CGGM_TRY(ensure(c->D, 8 * qq));
+        CGGM_TRY(ensure(c->U, sizeof(T) * qq));
+        CGGM_TRY(ensure(c->dV, sizeof(T) * pq));
+        CGGM_TRY(ensure(c->li, 4 * (qq / 2 + q + 1)));
+        CGGM_TRY(ensure(c->lj, 4 * (qq / 2 + q + 1)));
+        CGGM_TRY(ensure(c->ti, 4 * pq));
+        CGGM_TRY(ensure(c->tj, 4 * pq));
+        CGGM_TRY(ensure(c->rowcnt, 8 * (size_t)((p > q ? p : q) + 1)));
+        CGGM_TRY(ensure(c->scal, 8 * S_COUNT));
+        CGGM_TRY(ensure(c->cnt, 8 * 4));
+        CGGM_TRY(ensure(c->err, sizeof(int)));
+        CGGM_TRY(ensure(c->partial, 8 * 4096));
+        return CGGM_OK;
+    }
+
+    // S_yy, S_xy, S_xx (Section 2.1) from Xt (p x n) and Yt (q x n), double
+    cggm_status covariances() {
+        const int64_t n = z.n, p = z.p, q = z.q;
+        const double inv = 1.0 / (double)n;
+        const double *Xt = P<double>(c->Xt), *Yt = P<double>(c->Yt);
+        gemm<double>(false, true, q, q, n, inv, Yt, n, Yt, n, 0.0, P<double>(c->Syy), q, st);
+        gemm<double>(false, true, p, q, n, inv, Xt, n, Yt, n, 0.0, P<double>(c->Sxy), q, st);
+        if (sizeof(T) == 8) {
+            gemm<double>(false, true, p, p, n, inv, Xt, n, Xt, n, 0.0, (double *)c->Sxx.p, p, st);
+        } else {
+            CGGM_TRY(ensure(c->Xt_f, 4 * (size_t)p * n));
+            convert_d2f(p * n, Xt, P<float>(c->Xt_f), st);
+            gemm<float>(false, true, p, p, n, (float)inv, P<float>(c->Xt_f), n, P<float>(c->Xt_f), n,
+                        0.0f, (float *)c->Sxx.p, p, st);
+        }
+        rowsq_kernel<double><<<(unsigned)p, 256, 0, st>>>(p, n, Xt, inv, P<double>(c->Xd));
+        CGGM_CUDA_TRY(cudaGetLastError());
+        return CGGM_OK;
+    }
+
+    // Cholesky of Lambda into Lch, logdet into scal[S_LOGDET]; returns ENOTPD if not PD
+    cggm_status factor(Buf &Lam, Buf &Lch, Buf &logd, int slot) {
+        const int64_t q = z.q;
+        CGGM_CUDA_TRY(cudaMemcpyAsync(Lch.p, Lam.p, 8 * (size_t)q * q, cudaMemcpyDeviceToDevice, st));
+        CGGM_CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), st));
+        cholesky_inplace(q, P<double>(Lch), q, P<double>(logd), P<int>(c->err), st);
+        logdet_from_logd(q, P<double>(logd), scal() + slot, st);
+        int h = 0;
+        CGGM_TRY(read_dev_err(c, &h));
+        if (h == DEV_NOTPD) return CGGM_ENOTPD;
+        if (h != 0) return CGGM_ECUDA;
+        return CGGM_OK;
+    }
+
+    // Sigma (double and T copies) and its double diagonal from Lch
+    void sigma_from_factor() {
+        const int64_t q = z.q;
+        inverse_from_cholesky(q, P<double>(c->Lch), P<double>(c->Sig), P<double>(c->work), st);
+        if (sizeof(T) == 4) convert_d2f(q * q, P<double>(c->Sig), (float *)c->Sig_f.p, st);
+        diag_to_double<double>(q, P<double>(c->Sig), P<double>(c->Sd), st);
+    }
+    const T *SigT() {
+        return sizeof(T) == 8 ? (const T *)c->Sig.p : (const T *)c->Sig_f.p;
+    }
+
+    // Rt = Theta^T X^T (q x n) in double; Pt = Sigma Rt (double)
+    void products_R_P() {
+        const int64_t n = z.n, p = z.p, q = z.q;
+        gemm<double>(true, false, q, n, p, 1.0, P<double>(c->Th), q, P<double>(c->Xt), n, 0.0,
+                     P<double>(c->Rt), n, st);
+        gemm<double>(false, false, q, n, q, 1.0, P<double>(c->Sig), q, P<double>(c->Rt), n, 0.0,
+                     P<double>(c->Pt), n, st);
+    }
+
+    // Psi = Pt Pt^T / n (T), its double diagonal
+    void product_Psi() {
+        const int64_t n = z.n, q = z.q;
+        const double inv = 1.0 / (double)n;
+        if (sizeof(T) == 8) {
+            gemm<double>(false, true, q, q, n, inv, P<double>(c->Pt), n, P<double>(c->Pt), n, 0.0,
+                         (double *)c->Psi.p, q, st);
+        } else {
+            float *Ptf = P<float>(c->Z);  // scratch
+            convert_d2f(q * n, P<double>(c->Pt), Ptf, st);
+            gemm<float>(false, true, q, q, n, (float)inv, Ptf, n, Ptf, n, 0.0f, (float *)c->Psi.p, q, st);
+        }
+        rowsq_kernel<double><<<(unsigned)q, 256, 0, st>>>(q, n, P<double>(c->Pt), inv, P<double>(c->Pd));
+    }
+
+    // f(Lam, Th) given scal[S_LOGDET] and Rt, Pt current: pieces into scal
+    void objective_pieces() {
+        const int64_t n = z.n, p = z.p, q = z.q;
+        double *s = scal();
+        double *part = P<double>(c->partial);
+        cudaMemsetAsync(s + S_SYYL, 0, 8 * (S_L1T - S_SYYL + 1), st);
+        dot_d<double>(q * q, P<double>(c->Syy), P<double>(c->Lam), part, s + S_SYYL, st);
+        dot_d<double>(p * q, P<double>(c->Sxy), P<double>(c->Th), part, s + S_SXYT, st);
+        dot_d<double>(q * n, P<double>(c->Rt), P<double>(c->Pt), part, s + S_TRACE, st);
+        l1_d<double>(q * q, P<double>(c->Lam), o.penalize_diag ? 0 : q, part, s + S_L1L, st);
+        l1_d<double>(p * q, P<double>(c->Th), 0, part, s + S_L1T, st);
+        (void)n;
+    }
+
+    double f_from(const double *h) const {
+        return -h[S_LOGDET] + h[S_SYYL] + 2.0 * h[S_SXYT] + h[S_TRACE] / (double)z.n +
+               lamL * h[S_L1L] + lamT * h[S_L1T];
+    }
+
+    cggm_status run(const double *warmL, const double *warmT, cggm_info *info, int *iters_out,
+                    bool *conv_out) {
+        const int64_t n = z.n, p = z.p, q = z.q;
+        const size_t qq = (size_t)q * q, pq = (size_t)p * q;
+        CGGM_TRY(alloc());
+        CGGM_TRY(covariances());
+        // initial point (Algorithm 1: Theta <- 0, Lambda <- I, or the warm start)
+        if (warmL) {
+            CGGM_TRY(load_double(c, warmL, qq, c->Lam));
+        } else {
+            set_identity<<<gcap(q * q), 256, 0, st>>>(q, P<double>(c->Lam));
+        }
+        if (warmT) {
+            CGGM_TRY(load_double(c, warmT, pq, c->Th));
+        } else {
+            CGGM_CUDA_TRY(cudaMemsetAsync(c->Th.p, 0, 8 * pq, st));
+        }
+        CGGM_CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), st));
+        finite_check_kernel<<<gcap(n * p), 256, 0, st>>>(n * p, P<double>(c->Xt), P<int>(c->err));
+        finite_check_kernel<<<gcap(n * q), 256, 0, st>>>(n * q, P<double>(c->Yt), P<int>(c->err));
+        finite_check_kernel<<<gcap(q * q), 256, 0, st>>>(q * q, P<double>(c->Lam), P<int>(c->err));
+        finite_check_kernel<<<gcap(p * q), 256, 0, st>>>(p * q, P<double>(c->Th), P<int>(c->err));
+        {
+            int h = 0;
+            CGGM_TRY(read_dev_err(c, &h));
+            if (h) return CGGM_ENONFINITE;
+        }
+        CGGM_TRY(factor(c->Lam, c->Lch, c->logd, S_LOGDET));
+        sigma_from_factor();
+
+        const int B = o.sweep_batch > 0 ? o.sweep_batch : (sizeof(T) == 8 ? 64 : 128);
+        double h[S_COUNT];
+        int64_t hc[2];
+        bool converged = false;
+        int it = 0;
+        double f = 0.0, subgrad = 0.0, nrm = 0.0;
+        int ls_total = 0;
+        cudaEvent_t *ev = c->ev;
+        double t_prod = 0, t_fac = 0, t_act = 0, t_swl = 0, t_ls = 0, t_swt = 0;
+        cudaEventRecord(ev[7], st);
+        for (it = 0; it < o.max_iter; it++) {
+            cudaEventRecord(ev[0], st);
+            // ---- products (R, P, Psi) and the gradients (Eq. 3) ----
+            products_R_P();
+            product_Psi();
+            objective_pieces();
+            grad_lambda<T>(q, P<double>(c->Syy), P<double>(c->Sig), (const T *)c->Psi.p,
+                           P<double>(c->GL), st);
+            // G_Theta = 2 S_xy + (2/n) X^T P
+            axpby<double>(pq, 2.0, P<double>(c->Sxy), 0.0, P<double>(c->GT), st);
+            gemm<double>(false, true, p, q, n, 2.0 / (double)n, P<double>(c->Xt), n,
+                         P<double>(c->Pt), n, 1.0, P<double>(c->GT), q, st);
+            cudaEventRecord(ev[1], st);
+            // ---- stopping quantity (Section 5.1) and active sets (Section 2.2) ----
+            double *s = scal();
+            CGGM_CUDA_TRY(cudaMemsetAsync(s + S_SUBL, 0, 8 * 4, st));
+            subgrad_sums(q, q, P<double>(c->GL), P<double>(c->Lam), lamL, lamLd,
+                         P<double>(c->partial), s + S_SUBL, st);
+            subgrad_sums(p, q, P<double>(c->GT), P<double>(c->Th), lamT, -1.0,
+                         P<double>(c->partial), s + S_SUBT, st);
+            const double thrd = o.penalize_diag ? lamL : -1.0;
+            active_compact(q, q, P<double>(c->GL), P<double>(c->Lam), lamL, thrd, true,
+                           P<int64_t>(c->rowcnt), P<int32_t>(c->li), P<int32_t>(c->lj),
+                           P<int64_t>(c->cnt), st);
+            active_compact(p, q, P<double>(c->GT), P<double>(c->Th), lamT, lamT, false,
+                           P<int64_t>(c->rowcnt), P<int32_t>(c->ti), P<int32_t>(c->tj),
+                           P<int64_t>(c->cnt) + 1, st);
+            cudaEventRecord(ev[2], st);
+            CGGM_CUDA_TRY(cudaMemcpyAsync(h, s, 8 * S_COUNT, cudaMemcpyDeviceToHost, st));
+            CGGM_CUDA_TRY(cudaMemcpyAsync(hc, c->cnt.p, 16, cudaMemcpyDeviceToHost, st));
+            CGGM_TRY(sync_err(c));
+            f = f_from(h);
+            subgrad = h[S_SUBL] + h[S_SUBT];
+            nrm = h[S_NRML] + h[S_NRMT];
+            {
+                float a, b;
+                cudaEventElapsedTime(&a, ev[0], ev[1]);
+                cudaEventElapsedTime(&b, ev[1], ev[2]);
+                t_prod += a * 1e-3;
+                t_act += b * 1e-3;
+            }
+            if (info) {
+                info->m_lambda = hc[0];
+                info->m_theta = hc[1];
+            }
+            if (!std::isfinite(f)) return CGGM_ENONFINITE;
+            if (o.verbose)
+                fprintf(stderr, "cggm it %d f %.15g ratio %.3e mL %lld mT %lld\n", it, f,
+                        subgrad / (nrm > 0 ? nrm : 1.0), (long long)hc[0], (long long)hc[1]);
+            if (subgrad < o.tol * nrm || f <= o.target_f) {
+                converged = true;
+                break;
+            }
+            // ---- Lambda direction (Section 3.1) ----
+            cudaEventRecord(ev[3], st);
+            CGGM_CUDA_TRY(cudaMemsetAsync(c->D.p, 0, 8 * qq, st));
+            CGGM_CUDA_TRY(cudaMemsetAsync(c->U.p, 0, sizeof(T) * qq, st));
+            CGGM_TRY(lambda_sweep<T>(q, SigT(), (const T *)c->Psi.p, P<double>(c->Sd),
+                                     P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), hc[0],
+                                     P<int32_t>(c->li), P<int32_t>(c->lj), lamL, lamLd,
+                                     P<double>(c->D), (T *)c->U.p, B, c->planL, c->scr, st));
+            cudaEventRecord(ev[4], st);
+            // ---- Armijo (Algorithm 1) ----
+            // delta = tr(G D) + lamL (||Lam + D||_1 - ||Lam||_1)
+            double *part = P<double>(c->partial);
+            CGGM_CUDA_TRY(cudaMemsetAsync(s + S_GD, 0, 16, st));
+            dot_d<double>(q * q, P<double>(c->GL), P<double>(c->D), part, s + S_GD, st);
+            CGGM_CUDA_TRY(cudaMemcpyAsync(c->Lam_a.p, c->Lam.p, 8 * qq, cudaMemcpyDeviceToDevice, st));
+            axpby<double>(qq, 1.0, P<double>(c->D), 1.0, P<double>(c->Lam_a), st);
+            l1_d<double>(q * q, P<double>(c->Lam_a), o.penalize_diag ? 0 : q, part, s + S_L1LD, st);
+            CGGM_CUDA_TRY(cudaMemcpyAsync(h + S_GD, s + S_GD, 16, cudaMemcpyDeviceToHost, st));
+            CGGM_TRY(sync_err(c));
+            const double delta = h[S_GD] + lamL * (h[S_L1LD] - h[S_L1L]);
+            double alpha = 1.0;
+            bool accepted = false;
+            int trials = 0;
+            for (trials = 1; trials <= o.ls_max_trials; trials++) {
+                CGGM_CUDA_TRY(cudaMemcpyAsync(c->Lam_a.p, c->Lam.p, 8 * qq, cudaMemcpyDeviceToDevice, st));
+                axpby<double>(qq, alpha, P<double>(c->D), 1.0, P<double>(c->Lam_a), st);
+                cggm_status fs = factor(c->Lam_a, c->Lch_a, c->logd_a, S_LOGDET_A);
+                if (fs == CGGM_OK) {
+                    // tr(Lambda_a^-1 R^T R) / n = ||L_a^-1 R^T||_F^2 / n
+                    CGGM_CUDA_TRY(cudaMemcpyAsync(c->Z.p, c->Rt.p, 8 * (size_t)q * n,
+                                                  cudaMemcpyDeviceToDevice, st));
+                    trsm_lower_inplace(q, P<double>(c->Lch_a), q, P<double>(c->Z), n, n, false, st);
+                    CGGM_CUDA_TRY(cudaMemsetAsync(s + S_TRACE_A, 0, 24, st));
+                    dot_d<double>(q * n, P<double>(c->Z), P<double>(c->Z), part, s + S_TRACE_A, st);
+                    dot_d<double>(q * q, P<double>(c->Syy), P<double>(c->Lam_a), part, s + S_SYYL_A, st);
+                    l1_d<double>(q * q, P<double>(c->Lam_a), o.penalize_diag ? 0 : q, part,
+                                 s + S_L1L_A, st);
+                    CGGM_CUDA_TRY(cudaMemcpyAsync(h + S_LOGDET_A, s + S_LOGDET_A, 32,
+                                                  cudaMemcpyDeviceToHost, st));
+                    CGGM_TRY(sync_err(c));
+                    const double fa = -h[S_LOGDET_A] + h[S_SYYL_A] + 2.0 * h[S_SXYT] +
+                                      h[S_TRACE_A] / (double)n + lamL * h[S_L1L_A] +
+                                      lamT * h[S_L1T];
+                    if (std::isfinite(fa) && fa <= f + o.ls_sigma * alpha * delta) {
+                        accepted = true;
+                        break;
+                    }
+                } else if (fs != CGGM_ENOTPD) {
+                    return fs;
+                }
+                alpha *= o.ls_beta;
+            }
+            ls_total += trials;
+            if (!accepted) return CGGM_ELINESEARCH;
+            std::swap(c->Lam, c->Lam_a);
+            std::swap(c->Lch, c->Lch_a);
+            std::swap(c->logd, c->logd_a);
+            cudaEventRecord(ev[5], st);
+            sigma_from_factor();
+            // ---- Theta pass (Section 3.2) with the new Sigma ----
+            // W = S_xy + S_xx Theta Sigma = S_xy + (1/n) X^T (X Theta Sigma)
+            gemm<double>(false, false, q, n, q, 1.0, P<double>(c->Sig), q, P<double>(c->Rt), n,
+                         0.0, P<double>(c->Pt), n, st);
+            CGGM_CUDA_TRY(cudaMemcpyAsync(c->W.p, c->Sxy.p, 8 * pq, cudaMemcpyDeviceToDevice, st));
+            gemm<double>(false, true, p, q, n, 1.0 / (double)n, P<double>(c->Xt), n,
+                         P<double>(c->Pt), n, 1.0, P<double>(c->W), q, st);
+            CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, sizeof(T) * pq, st));
+            CGGM_TRY(theta_sweep<T>(p, q, (const T *)c->Sxx.p, P<double>(c->Xd), SigT(),
+                                    P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), hc[1],
+                                    P<int32_t>(c->ti), P<int32_t>(c->tj), lamT, (T *)c->dV.p, B,
+                                    c->planT, c->scr, st));
+            cudaEventRecord(ev[6], st);
+            CGGM_TRY(sync_err(c));
+            {
+                float a, b, d2;
+                cudaEventElapsedTime(&a, ev[3], ev[4]);
+                cudaEventElapsedTime(&b, ev[4], ev[5]);
+                cudaEventElapsedTime(&d2, ev[5], ev[6]);
+                t_swl += a * 1e-3;
+                t_ls += b * 1e-3;
+                t_swt += d2 * 1e-3;
+            }
+        }
+        cudaEventRecord(ev[6], st);
+        CGGM_TRY(sync_err(c));
+        if (info) {
+            float tot = 0;
+            cudaEventElapsedTime(&tot, ev[7], ev[6]);
+            info->iterations = it + (converged ? 1 : 0);
+            info->converged = converged ? 1 : 0;
+            info->f = f;
+            info->subgrad = subgrad;
+            info->l1norm = nrm;
+            info->ls_trials = ls_total;
+            info->seconds = tot * 1e-3;
+            info->sec_products = t_prod;
+            info->sec_factor = t_fac;
+            info->sec_active = t_act;
+            info->sec_sweep_lambda = t_swl;
+            info->sec_linesearch = t_ls;
+            info->sec_sweep_theta = t_swt;
+        }
+        *iters_out = it;
+        *conv_out = converged;
+        return CGGM_OK;
+    }
+};
+
+cggm_status check_sizes(int64_t n, int64_t p, int64_t q) {
+    if (n <= 0 || p <= 0 || q <= 0) return CGGM_EINVAL;
+    if (q > 2147483647LL || p > 2147483647LL) return CGGM_EINVAL;
+    return CGGM_OK;
+}
+
+cggm_status set_device(cggm_ctx *c) {
+    CGGM_CUDA_TRY(cudaSetDevice(c->device));
+    return CGGM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cggm_opts_default(cggm_opts *o) {
+    if (!o) return;
+    o->tol = 0.01;
+    o->max_iter = 1000;
+    o->precision = CGGM_MIXED;
+    o->ls_sigma = 1e-3;
+    o->ls_beta = 0.5;
+    o->ls_max_trials = 50;
+    o->penalize_diag = 1;
+    o->sweep_batch = 0;
+    o->target_f = -INFINITY;
+    o->verbose = 0;
+}
+
+const char *cggm_status_string(int s) {
+    switch (s) {
+        case CGGM_OK: return "ok";
+        case CGGM_EINVAL: return "invalid argument";
+        case CGGM_ENOTPD: return "matrix not positive definite";
+        case CGGM_ENOMEM: return "out of device memory";
+        case CGGM_EMAXITER: return "iteration limit reached";
+        case CGGM_ELINESEARCH: return "line search failed";
+        case CGGM_ECUDA: return "CUDA error";
+        case CGGM_ETIMEDOUT: return "device wait timed out";
+        case CGGM_ENONFINITE: return "non-finite value";
+        case CGGM_ECANCELLED: return "cancelled";
+        default: return "unknown status";
+    }
+}
+
+cggm_status cggm_create(cggm_ctx **out, int device, void *stream) {
+    if (!out) return CGGM_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return CGGM_EINVAL;
+    }
+    cggm_ctx *c = new cggm_ctx();
+    c->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return CGGM_ECUDA;
+    }
+    if (stream) {
+        c->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return CGGM_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    for (int i = 0; i < 8; i++) cudaEventCreate(&c->ev[i]);
+    c->events = true;
+    *out = c;
+    return CGGM_OK;
+}
+
+void cggm_destroy(cggm_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->st);
+    Buf *bufs[] = {&c->stage, &c->Xt, &c->Yt, &c->Xt_f, &c->Syy, &c->Sxy, &c->Sxx, &c->Xd,
+                   &c->Lam, &c->Th, &c->Lch, &c->logd, &c->Sig, &c->Sig_f, &c->Sd, &c->Lam_a,
+                   &c->Lch_a, &c->logd_a, &c->work, &c->Rt, &c->Pt, &c->Z, &c->Psi, &c->Pd,
+                   &c->GL, &c->GT, &c->W, &c->D, &c->U, &c->dV, &c->li, &c->lj, &c->ti,
+                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial};
+    for (Buf *b : bufs) if (b->p) cudaFree(b->p);
+    plan_free(c->planL);
+    plan_free(c->planT);
+    scratch_free(c->scr);
+    if (c->events) for (int i = 0; i < 8; i++) cudaEventDestroy(c->ev[i]);
+    if (c->own_stream) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, int ydtype,
+                       int64_t n, int64_t p, int64_t q, double lam_L, double lam_T, double tol,
+                       const double *warm_Lambda, const double *warm_Theta, const cggm_opts *opts,
+                       double *Lambda_out, double *Theta_out, cggm_info *info) {
+    if (!c || !X || !Y) return CGGM_EINVAL;
+    CGGM_TRY(check_sizes(n, p, q));
+    if (!(lam_L >= 0.0) || !(lam_T >= 0.0)) return CGGM_EINVAL;
+    if ((xdtype != CGGM_F32 && xdtype != CGGM_F64) || (ydtype != CGGM_F32 && ydtype != CGGM_F64))
+        return CGGM_EINVAL;
+    cggm_opts o;
+    if (opts) o = *opts; else cggm_opts_default(&o);
+    if (tol > 0.0) o.tol = tol;
+    if (!(o.tol > 0.0) || o.max_iter < 0 || o.ls_max_trials < 1 || !(o.ls_beta > 0.0 && o.ls_beta < 1.0))
+        return CGGM_EINVAL;
+    if (o.sweep_batch != 0 && o.sweep_batch != 32 && o.sweep_batch != 64 && o.sweep_batch != 128)
+        return CGGM_EINVAL;
+    if (info) memset(info, 0, sizeof(*info));
+    CGGM_TRY(set_device(c));
+    CGGM_TRY(ensure(c->err, sizeof(int)));
+    CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
+    CGGM_TRY(load_transposed(c, Y, ydtype, n, q, c->Yt, nullptr));
+    int iters = 0;
+    bool conv = false;
+    cggm_status s;
+    const double lamLd = o.penalize_diag ? lam_L : 0.0;
+    if (o.precision == CGGM_FP64) {
+        Solver<double> S{c, {n, p, q}, c->st, lam_L, lam_T, lamLd, o};
+        s = S.run(warm_Lambda, warm_Theta, info, &iters, &conv);
+    } else if (o.precision == CGGM_MIXED) {
+        Solver<float> S{c, {n, p, q}, c->st, lam_L, lam_T, lamLd, o};
+        s = S.run(warm_Lambda, warm_Theta, info, &iters, &conv);
+    } else {
+        return CGGM_EINVAL;
+    }
+    if (s != CGGM_OK) return s;
+    if (Lambda_out) CGGM_TRY(store_double(c, Lambda_out, c->Lam.p, (size_t)q * q));
+    if (Theta_out) CGGM_TRY(store_double(c, Theta_out, c->Th.p, (size_t)p * q));
+    CGGM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    return conv ? CGGM_OK : CGGM_EMAXITER;
+}
+
+cggm_status cggm_objective(cggm_ctx *c, const void *X, int xdtype, const void *Y, int ydtype,
+                           int64_t n, int64_t p, int64_t q, const double *Lambda,
+                           const double *Theta, double lam_L, double lam_T, int penalize_diag,
+                           double *f_out) {
+    if (!c || !X || !Y || !Lambda || !Theta || !f_out) return CGGM_EINVAL;
+    CGGM_TRY(check_sizes(n, p, q));
+    CGGM_TRY(set_device(c));
+    CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
+    CGGM_TRY(load_transposed(c, Y, ydtype, n, q, c->Yt, nullptr));
+    cggm_opts o;
+    cggm_opts_default(&o);
+    o.penalize_diag = penalize_diag;
+    Solver<double> S{c, {n, p, q}, c->st, lam_L, lam_T, penalize_diag ? lam_L : 0.0, o};
+    CGGM_TRY(S.alloc());
+    const size_t qq = (size_t)q * q, pq = (size_t)p * q;
+    const double inv = 1.0 / (double)n;
+    gemm<double>(false, true, q, q, n, inv, P<double>(c->Yt), n, P<double>(c->Yt), n, 0.0,
+                 P<double>(c->Syy), q, c->st);
+    gemm<double>(false, true, p, q, n, inv, P<double>(c->Xt), n, P<double>(c->Yt), n, 0.0,
+                 P<double>(c->Sxy), q, c->st);
+    CGGM_TRY(load_double(c, Lambda, qq, c->Lam));
+    CGGM_TRY(load_double(c, Theta, pq, c->Th));
+    CGGM_TRY(S.factor(c->Lam, c->Lch, c->logd, S_LOGDET));
+    // trace tr(Lambda^-1 Theta^T S_xx Theta) = ||L^-1 (X Theta)^T||_F^2 / n
+    gemm<double>(true, false, q, n, p, 1.0, P<double>(c->Th), q, P<double>(c->Xt), n, 0.0,
+                 P<double>(c->Rt), n, c->st);
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->Z.p, c->Rt.p, 8 * (size_t)q * n, cudaMemcpyDeviceToDevice, c->st));
+    trsm_lower_inplace(q, P<double>(c->Lch), q, P<double>(c->Z), n, n, false, c->st);
+    double *s = P<double>(c->scal);
+    double *part = P<double>(c->partial);
+    CGGM_CUDA_TRY(cudaMemsetAsync(s + S_SYYL, 0, 8 * (S_L1T - S_SYYL + 1), c->st));
+    dot_d<double>(q * q, P<double>(c->Syy), P<double>(c->Lam), part, s + S_SYYL, c->st);
+    dot_d<double>(p * q, P<double>(c->Sxy), P<double>(c->Th), part, s + S_SXYT, c->st);
+    dot_d<double>(q * n, P<double>(c->Z), P<double>(c->Z), part, s + S_TRACE, c->st);
+    l1_d<double>(q * q, P<double>(c->Lam), penalize_diag ? 0 : q, part, s + S_L1L, c->st);
+    l1_d<double>(p * q, P<double>(c->Th), 0, part, s + S_L1T, c->st);
+    double h[S_COUNT];
+    CGGM_CUDA_TRY(cudaMemcpyAsync(h, s, 8 * S_COUNT, cudaMemcpyDeviceToHost, c->st));
+    CGGM_TRY(sync_err(c));
+    *f_out = S.f_from(h);
+    return CGGM_OK;
+}
+
+cggm_status cggm_grad(cggm_ctx *c, const void *X, int xdtype, const void *Y, int ydtype,
+                      int64_t n, int64_t p, int64_t q, const double *Lambda, const double *Theta,
+                      double *G_Lambda, double *G_Theta) {
+    if (!c || !X || !Y || !Lambda || !Theta) return CGGM_EINVAL;
+    CGGM_TRY(check_sizes(n, p, q));
+    CGGM_TRY(set_device(c));
+    CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
+    CGGM_TRY(load_transposed(c, Y, ydtype, n, q, c->Yt, nullptr));
+    cggm_opts o;
+    cggm_opts_default(&o);
+    Solver<double> S{c, {n, p, q}, c->st, 0.0, 0.0, 0.0, o};
+    CGGM_TRY(S.alloc());
+    const size_t qq = (size_t)q * q, pq = (size_t)p * q;
+    const double inv = 1.0 / (double)n;
+    gemm<double>(false, true, q, q, n, inv, P<double>(c->Yt), n, P<double>(c->Yt), n, 0.0,
+                 P<double>(c->Syy), q, c->st);
+    gemm<double>(false, true, p, q, n, inv, P<double>(c->Xt), n, P<double>(c->Yt), n, 0.0,
+                 P<double>(c->Sxy), q, c->st);
+    CGGM_TRY(load_double(c, Lambda, qq, c->Lam));
+    CGGM_TRY(load_double(c, Theta, pq, c->Th));
+    CGGM_TRY(S.factor(c->Lam, c->Lch, c->logd, S_LOGDET));
+    S.sigma_from_factor();
+    S.products_R_P();
+    S.product_Psi();
+    grad_lambda<double>(q, P<double>(c->Syy), P<double>(c->Sig), P<double>(c->Psi),
+                        P<double>(c->GL), c->st);
+    axpby<double>(pq, 2.0, P<double>(c->Sxy), 0.0, P<double>(c->GT), c->st);
+    gemm<double>(false, true, p, q, n, 2.0 * inv, P<double>(c->Xt), n, P<double>(c->Pt), n, 1.0,
+                 P<double>(c->GT), q, c->st);
+    if (G_Lambda) CGGM_TRY(store_double(c, G_Lambda, c->GL.p, qq));
+    if (G_Theta) CGGM_TRY(store_double(c, G_Theta, c->GT.p, pq));
+    return sync_err(c);
+}
+
+cggm_status cggm_cholesky(cggm_ctx *c, int64_t q, const double *Lambda, double *L_out,
+                          double *logdet_out, double *Sigma_out, int precision) {
+    (void)precision;
+    if (!c || !Lambda || q <= 0) return CGGM_EINVAL;
+    CGGM_TRY(set_device(c));
+    cggm_opts o;
+    cggm_opts_default(&o);
+    Solver<double> S{c, {1, 1, q}, c->st, 0.0, 0.0, 0.0, o};
+    const size_t qq = (size_t)q * q;
+    CGGM_TRY(ensure(c->Lam, 8 * qq));
+    CGGM_TRY(ensure(c->Lch, 8 * qq));
+    CGGM_TRY(ensure(c->logd, 8 * (size_t)q));
+    CGGM_TRY(ensure(c->Sig, 8 * qq));
+    CGGM_TRY(ensure(c->Sd, 8 * (size_t)q));
+    CGGM_TRY(ensure(c->work, 8 * qq));
+    CGGM_TRY(ensure(c->scal, 8 * S_COUNT));
+    CGGM_TRY(ensure(c->err, sizeof(int)));
+    CGGM_TRY(load_double(c, Lambda, qq, c->Lam));
+    CGGM_TRY(S.factor(c->Lam, c->Lch, c->logd, S_LOGDET));
+    if (Sigma_out) {
+        inverse_from_cholesky(q, P<double>(c->Lch), P<double>(c->Sig), P<double>(c->work), c->st);
+        CGGM_TRY(store_double(c, Sigma_out, c->Sig.p, qq));
+    }
+    if (L_out) CGGM_TRY(store_double(c, L_out, c->Lch.p, qq));
+    if (logdet_out) {
+        double h;
+        CGGM_CUDA_TRY(cudaMemcpyAsync(&h, P<double>(c->scal) + S_LOGDET, 8, cudaMemcpyDeviceToHost, c->st));
+        CGGM_TRY(sync_err(c));
+        *logdet_out = h;
+    }
+    return sync_err(c);
+}
+
+static cggm_status load_index(cggm_ctx *c, const int32_t *src, int64_t m, Buf &dst) {
+    CGGM_TRY(ensure(dst, 4 * (size_t)(m > 0 ? m : 1)));
+    if (m > 0) CGGM_CUDA_TRY(cudaMemcpyAsync(dst.p, src, 4 * (size_t)m, cudaMemcpyDefault, c->st));
+    return CGGM_OK;
+}
+
+cggm_status cggm_lambda_sweep(cggm_ctx *c, int64_t q, const double *Sigma, const double *Psi,
+                              const double *Syy, const double *Lambda, int64_t m,
+                              const int32_t *ai, const int32_t *aj, double lam_L,
+                              int penalize_diag, int precision, double *D_out) {
+    if (!c || q <= 0 || m < 0 || !Sigma || !Psi || !Syy || !Lambda || !D_out) return CGGM_EINVAL;
+    if (m > 0 && (!ai || !aj)) return CGGM_EINVAL;
+    CGGM_TRY(set_device(c));
+    const size_t qq = (size_t)q * q;
+    CGGM_TRY(load_double(c, Sigma, qq, c->Sig));
+    CGGM_TRY(load_double(c, Psi, qq, c->work));
+    CGGM_TRY(load_double(c, Syy, qq, c->Syy));
+    CGGM_TRY(load_double(c, Lambda, qq, c->Lam));
+    CGGM_TRY(load_index(c, ai, m, c->li));
+    CGGM_TRY(load_index(c, aj, m, c->lj));
+    CGGM_TRY(ensure(c->Sd, 8 * (size_t)q));
+    CGGM_TRY(ensure(c->Pd, 8 * (size_t)q));
+    CGGM_TRY(ensure(c->GL, 8 * qq));
+    CGGM_TRY(ensure(c->D, 8 * qq));
+    diag_to_double<double>(q, P<double>(c->Sig), P<double>(c->Sd), c->st);
+    diag_to_double<double>(q, P<double>(c->work), P<double>(c->Pd), c->st);
+    grad_lambda<double>(q, P<double>(c->Syy), P<double>(c->Sig), P<double>(c->work),
+                        P<double>(c->GL), c->st);
+    CGGM_CUDA_TRY(cudaMemsetAsync(c->D.p, 0, 8 * qq, c->st));
+    const double lamd = penalize_diag ? lam_L : 0.0;
+    if (precision == CGGM_FP64) {
+        CGGM_TRY(ensure(c->U, 8 * qq));
+        CGGM_CUDA_TRY(cudaMemsetAsync(c->U.p, 0, 8 * qq, c->st));
+        CGGM_TRY(lambda_sweep<double>(q, P<double>(c->Sig), P<double>(c->work), P<double>(c->Sd),
+                                      P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), m,
+                                      P<int32_t>(c->li), P<int32_t>(c->lj), lam_L, lamd,
+                                      P<double>(c->D), P<double>(c->U), 64, c->planL, c->scr, c->st));
+    } else {
+        CGGM_TRY(ensure(c->U, 4 * qq));
+        CGGM_TRY(ensure(c->Sig_f, 4 * qq));
+        CGGM_TRY(ensure(c->Psi, 4 * qq));
+        convert_d2f(q * q, P<double>(c->Sig), P<float>(c->Sig_f), c->st);
+        convert_d2f(q * q, P<double>(c->work), P<float>(c->Psi), c->st);
+        CGGM_CUDA_TRY(cudaMemsetAsync(c->U.p, 0, 4 * qq, c->st));
+        CGGM_TRY(lambda_sweep<float>(q, P<float>(c->Sig_f), P<float>(c->Psi), P<double>(c->Sd),
+                                     P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), m,
+                                     P<int32_t>(c->li), P<int32_t>(c->lj), lam_L, lamd,
+                                     P<double>(c->D), P<float>(c->U), 128, c->planL, c->scr, c->st));
+    }
+    CGGM_TRY(store_double(c, D_out, c->D.p, qq));
+    return sync_err(c);
+}
+
+cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const double *X,
+                             const double *Sxy, const double *Sigma, const double *Theta_in,
+                             int64_t m, const int32_t *ti, const int32_t *tj, double lam_T,
+                             int precision, double *Theta_out) {
+    if (!c || !X || !Sxy || !Sigma || !Theta_in || !Theta_out || m < 0) return CGGM_EINVAL;
+    if (m > 0 && (!ti || !tj)) return CGGM_EINVAL;
+    CGGM_TRY(check_sizes(n, p, q));
+    CGGM_TRY(set_device(c));
+    const size_t qq = (size_t)q * q, pq = (size_t)p * q;
+    CGGM_TRY(load_transposed(c, X, CGGM_F64, n, p, c->Xt, nullptr));
+    CGGM_TRY(ensure(c->Sxx, 8 * (size_t)p * p));
+    CGGM_TRY(ensure(c->Xd, 8 * (size_t)p));
+    CGGM_TRY(load_double(c, Sxy, pq, c->Sxy));
+    CGGM_TRY(load_double(c, Sigma, qq, c->Sig));
+    CGGM_TRY(load_double(c, Theta_in, pq, c->Th));
+    CGGM_TRY(load_index(c, ti, m, c->ti));
+    CGGM_TRY(load_index(c, tj, m, c->tj));
+    CGGM_TRY(ensure(c->Sd, 8 * (size_t)q));
+    CGGM_TRY(ensure(c->Rt, 8 * (size_t)q * n));
+    CGGM_TRY(ensure(c->Pt, 8 * (size_t)q * n));
+    CGGM_TRY(ensure(c->W, 8 * pq));
+    const double inv = 1.0 / (double)n;
+    const double *Xt = P<double>(c->Xt);
+    rowsq_kernel<double><<<(unsigned)p, 256, 0, c->st>>>(p, n, Xt, inv, P<double>(c->Xd));
+    diag_to_double<double>(q, P<double>(c->Sig), P<double>(c->Sd), c->st);
+    // W = S_xy + S_xx Theta Sigma
+    gemm<double>(true, false, q, n, p, 1.0, P<double>(c->Th), q, Xt, n, 0.0, P<double>(c->Rt), n, c->st);
+    gemm<double>(false, false, q, n, q, 1.0, P<double>(c->Sig), q, P<double>(c->Rt), n, 0.0,
+                 P<double>(c->Pt), n, c->st);
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->W.p, c->Sxy.p, 8 * pq, cudaMemcpyDeviceToDevice, c->st));
+    gemm<double>(false, true, p, q, n, inv, Xt, n, P<double>(c->Pt), n, 1.0, P<double>(c->W), q, c->st);
+    if (precision == CGGM_FP64) {
+        gemm<double>(false, true, p, p, n, inv, Xt, n, Xt, n, 0.0, P<double>(c->Sxx), p, c->st);
+        CGGM_TRY(ensure(c->dV, 8 * pq));
+        CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, 8 * pq, c->st));
+        CGGM_TRY(theta_sweep<double>(p, q, P<double>(c->Sxx), P<double>(c->Xd), P<double>(c->Sig),
+                                     P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
+                                     P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<double>(c->dV),
+                                     64, c->planT, c->scr, c->st));
+    } else {
+        CGGM_TRY(ensure(c->Xt_f, 4 * (size_t)p * n));
+        CGGM_TRY(ensure(c->Sig_f, 4 * qq));
+        convert_d2f(p * n, Xt, P<float>(c->Xt_f), c->st);
+        gemm<float>(false, true, p, p, n, (float)inv, P<float>(c->Xt_f), n, P<float>(c->Xt_f), n,
+                    0.0f, P<float>(c->Sxx), p, c->st);
+        convert_d2f(q * q, P<double>(c->Sig), P<float>(c->Sig_f), c->st);
+        CGGM_TRY(ensure(c->dV, 4 * pq));
+        CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, 4 * pq, c->st));
+        CGGM_TRY(theta_sweep<float>(p, q, P<float>(c->Sxx), P<double>(c->Xd), P<float>(c->Sig_f),
+                                    P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
+                                    P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<float>(c->dV),
+                                    128, c->planT, c->scr, c->st));
+    }
+    CGGM_TRY(store_double(c, Theta_out, c->Th.p, pq));
+    return sync_err(c);
+}
+
+cggm_status cggm_active_sets(cggm_ctx *c, int64_t p, int64_t q, const double *G_Lambda,
+                             const double *G_Theta, const double *Lambda, const double *Theta,
+                             double lam_L, double lam_T, int penalize_diag, int32_t *li,
+                             int32_t *lj, int64_t *m_lambda, int32_t *ti, int32_t *tj,
+                             int64_t *m_theta) {
+    if (!c || p <= 0 || q <= 0 || !G_Lambda || !G_Theta || !Lambda || !Theta || !li || !lj ||
+        !ti || !tj || !m_lambda || !m_theta)
+        return CGGM_EINVAL;
+    CGGM_TRY(set_device(c));
+    const size_t qq = (size_t)q * q, pq = (size_t)p * q;
+    CGGM_TRY(load_double(c, G_Lambda, qq, c->GL));
+    CGGM_TRY(load_double(c, G_Theta, pq, c->GT));
+    CGGM_TRY(load_double(c, Lambda, qq, c->Lam));
+    CGGM_TRY(load_double(c, Theta, pq, c->Th));
+    CGGM_TRY(ensure(c->li, 4 * (qq / 2 + q + 1)));
+    CGGM_TRY(ensure(c->lj, 4 * (qq / 2 + q + 1)));
+    CGGM_TRY(ensure(c->ti, 4 * pq));
+    CGGM_TRY(ensure(c->tj, 4 * pq));
+    CGGM_TRY(ensure(c->rowcnt, 8 * (size_t)((p > q ? p : q) + 1)));
+    CGGM_TRY(ensure(c->cnt, 32));
+    const double thrd = penalize_diag ? lam_L : -1.0;
+    active_compact(q, q, P<double>(c->GL), P<double>(c->Lam), lam_L, thrd, true,
+                   P<int64_t>(c->rowcnt), P<int32_t>(c->li), P<int32_t>(c->lj), P<int64_t>(c->cnt), c->st);
+    active_compact(p, q, P<double>(c->GT), P<double>(c->Th), lam_T, lam_T, false,
+                   P<int64_t>(c->rowcnt), P<int32_t>(c->ti), P<int32_t>(c->tj),
+                   P<int64_t>(c->cnt) + 1, c->st);
+    int64_t hc[2];
+    CGGM_CUDA_TRY(cudaMemcpyAsync(hc, c->cnt.p, 16, cudaMemcpyDeviceToHost, c->st));
+    CGGM_TRY(sync_err(c));
+    *m_lambda = hc[0];
+    *m_theta = hc[1];
+    CGGM_CUDA_TRY(cudaMemcpyAsync(li, c->li.p, 4 * (size_t)hc[0], cudaMemcpyDefault, c->st));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(lj, c->lj.p, 4 * (size_t)hc[0], cudaMemcpyDefault, c->st));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(ti, c->ti.p, 4 * (size_t)hc[1], cudaMemcpyDefault, c->st));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(tj, c->tj.p, 4 * (size_t)hc[1], cudaMemcpyDefault, c->st));
+    return sync_err(c);
+}
+
+}  // extern "C"

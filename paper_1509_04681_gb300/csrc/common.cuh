@@ -1,0 +1,144 @@
+// Shared device/host helpers of the CGGM CUDA library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/cggm.h"
+
+namespace cggm {
+
+// Device status word codes (written by kernels, read by the host after a launch).
+enum DevErr : int {
+    DEV_OK = 0,
+    DEV_NOTPD = 1,       // Cholesky pivot <= 0 or not finite
+    DEV_TIMEOUT = 2,     // a grid barrier exceeded its deadline
+    DEV_NONFINITE = 3,   // NaN/Inf met in a coordinate step
+    DEV_BADINDEX = 4,    // an index outside its matrix
+};
+
+struct Status {
+    cggm_status code = CGGM_OK;
+    explicit operator bool() const { return code == CGGM_OK; }
+};
+
+#define CGGM_CUDA_TRY(expr)                                                              \
+    do {                                                                                 \
+        cudaError_t _e = (expr);                                                         \
+        if (_e != cudaSuccess) {                                                         \
+            if (getenv("CGGM_DEBUG"))                                                    \
+                fprintf(stderr, "cggm: %s failed at %s:%d: %s\n", #expr, __FILE__,       \
+                        __LINE__, cudaGetErrorString(_e));                               \
+            return _e == cudaErrorMemoryAllocation ? CGGM_ENOMEM : CGGM_ECUDA;           \
+        }                                                                                \
+    } while (0)
+
+#define CGGM_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cggm_status _s = (expr);                                                         \
+        if (_s != CGGM_OK) return _s;                                                    \
+    } while (0)
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Number of SMs of the current device (cached per process; one device per context).
+int sm_count();
+
+// ---------------------------------------------------------------------------------
+// Grid-wide barrier for persistent kernels launched cooperatively (all CTAs resident).
+// Sense/generation based, acquire/release ordered, with a wall-clock deadline: a CTA
+// that waits longer than `deadline_ns` sets the error word to DEV_TIMEOUT; every
+// waiter also leaves as soon as the error word is nonzero.  Returns false on error.
+// ---------------------------------------------------------------------------------
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_acquire_int(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, int *err, unsigned nblocks,
+                                          uint64_t deadline_ns = 2000000000ull) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        const unsigned g = ld_acquire(&bar->gen);
+        __threadfence();
+        const unsigned arrived = atomicAdd(&bar->count, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            bar->count = 0;
+            __threadfence();
+            st_release(&bar->gen, g + 1);
+        } else {
+            const uint64_t t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire(&bar->gen) == g) {
+                if (ld_acquire_int(err) != 0) { ok = 0; break; }
+                if ((++spins & 63u) == 0 && global_ns() - t0 > deadline_ns) {
+                    atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        if (ok && ld_acquire_int(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Warp reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block reduction of a double (blockDim multiple of 32, <= 1024); result valid in all
+// threads.
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double s_part[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) s_part[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    double r = (threadIdx.x < nw) ? s_part[threadIdx.x] : 0.0;
+    if (w == 0) r = warp_sum(r);
+    __shared__ double s_res;
+    if (threadIdx.x == 0) s_res = r;
+    __syncthreads();
+    return s_res;
+}
+
+__device__ __forceinline__ double soft_threshold(double w, double r) {
+    return w > r ? w - r : (w < -r ? w + r : 0.0);
+}
+
+}  // namespace cggm

@@ -1,0 +1,61 @@
+"""The C-ABI library builds, loads without a GPU, and exports every declared symbol."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "cggm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cggm_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1509_04681_gb300 import build
+    return ctypes.CDLL(build.build())
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("cggm_solve", "cggm_objective", "cggm_grad", "cggm_create", "cggm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header():
+    import paper_1509_04681_gb300 as cg
+    assert set(cg.EXPORTED) == set(declared_functions())
+
+
+def test_status_strings_and_defaults(lib):
+    import paper_1509_04681_gb300 as cg
+    o = cg.opts_default()
+    assert o.tol == 0.01 and o.max_iter == 1000 and o.penalize_diag == 1
+    assert o.ls_sigma == 1e-3 and o.ls_beta == 0.5 and o.ls_max_trials == 50
+    lib.cggm_status_string.restype = ctypes.c_char_p
+    assert lib.cggm_status_string(-2) == b"matrix not positive definite"
+
+
+def test_bad_device_is_einval_not_a_crash(lib):
+    h = ctypes.c_void_p()
+    assert lib.cggm_create(ctypes.byref(h), 12345, None) == -1
+
+
+def test_sm103a_only_sources():
+    """The build names one architecture, sm_103a, and the CUDA sources hold no
+    compatibility paths (Triton, other architectures)."""
+    from paper_1509_04681_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    for src in build.sources():
+        s = open(src).read()
+        assert "triton" not in s.lower()
+        assert "__CUDA_ARCH__ <" not in s

@@ -1,0 +1,252 @@
+"""CUDA path against the CPU oracle, step by step and for whole solves (needs a GPU).
+
+Every test calls the library through the C ABI (ctypes binding) on inputs from the
+seeded generators and compares element by element with the oracle on the same inputs.
+Tolerances: double-precision kernels agree with the oracle to rounding (1e-9 relative
+on the step outputs, the sums being reordered); single-precision caches (mixed) to
+1e-4 relative on the steps.  Whole solves are compared by the acceptance bar of the
+method: relative objective gap <= 1e-6, max |dLambda|, |dTheta| <= 1e-4 max|entry|, same
+support above 1e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+cg = pytest.importorskip("paper_1509_04681_gb300")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1509_04681_gb300 import build
+    build.build()
+    c = cg.Context(0)
+    yield c
+    c.close()
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(1e-300, np.max(np.abs(b)))
+
+
+def problem(p, q, n, seed, **kw):
+    kw.setdefault("theta_nnz", 3)
+    return synth.make_problem(p, q, n, seed=seed, **kw)
+
+
+def state_at(pr, iters=2):
+    """An interior iterate of the oracle (nonzero Theta, non-identity Lambda)."""
+    r = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12, max_iter=iters)
+    return r.Lambda, r.Theta
+
+
+# ------------------------------------------------------------------------------------
+# Cholesky, log det, Sigma
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("q", [1, 63, 64, 65, 200, 333])
+def test_cholesky_logdet_sigma(ctx, q):
+    rng = np.random.default_rng(q)
+    A = rng.standard_normal((q, q + 5))
+    Lam = A @ A.T / q + 0.5 * np.eye(q)
+    L, ld, S = ctx.cggm_cholesky(Lam)
+    L_ref = np.linalg.cholesky(Lam)
+    assert rel(L, L_ref) < 1e-12
+    assert abs(ld - 2 * np.log(np.diag(L_ref)).sum()) < 1e-11 * max(1, abs(ld))
+    assert rel(S, np.linalg.inv(Lam)) < 1e-10
+
+
+def test_cholesky_not_pd_is_reported(ctx):
+    Lam = np.diag([1.0, 2.0, -1.0, 3.0])
+    with pytest.raises(cg.CGGMError) as e:
+        ctx.cggm_cholesky(Lam)
+    assert e.value.status == cg.CGGM_ENOTPD
+
+
+# ------------------------------------------------------------------------------------
+# gradients and objective
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("shape", [(30, 20, 25), (130, 70, 90), (7, 1, 12), (1, 5, 9)])
+def test_grad_and_objective(ctx, shape):
+    p, q, n = shape
+    pr = problem(p, q, n, seed=p + q)
+    Lam, Th = state_at(pr)
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    G_L, G_T, _, _ = oracle.gradients(Lam, Th, Sxx, Sxy, Syy)
+    gL, gT = ctx.cggm_grad(pr.X, pr.Y, Lam, Th)
+    assert rel(gL, G_L) < 1e-10
+    assert rel(gT, G_T) < 1e-10
+    for pen in (True, False):
+        f_ref = oracle.objective(Lam, Th, Sxx, Sxy, Syy, 0.1, 0.2, pen)
+        f = ctx.cggm_objective(pr.X, pr.Y, Lam, Th, 0.1, 0.2, pen)
+        assert abs(f - f_ref) < 1e-11 * abs(f_ref)
+
+
+# ------------------------------------------------------------------------------------
+# active sets: integer work, bit-exact
+# ------------------------------------------------------------------------------------
+@pytest.mark.parametrize("pen", [True, False])
+def test_active_sets_bit_exact(ctx, pen):
+    pr = problem(90, 70, 60, seed=5)
+    Lam, Th = state_at(pr)
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    G_L, G_T, _, _ = oracle.gradients(Lam, Th, Sxx, Sxy, Syy)
+    ref = oracle.active_sets(G_L, G_T, Lam, Th, 0.1, 0.1, pen)
+    got = ctx.cggm_active_sets(G_L, G_T, Lam, Th, 0.1, 0.1, pen)
+    for a, b in zip(got, ref):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_active_sets_empty_and_full(ctx):
+    q, p = 5, 4
+    G_L = np.zeros((q, q)); G_T = np.zeros((p, q))
+    li, lj, ti, tj = ctx.cggm_active_sets(G_L, G_T, np.eye(q), np.zeros((p, q)), 1.0, 1.0)
+    assert list(zip(li, lj)) == [(i, i) for i in range(q)] and len(ti) == 0
+    li, lj, ti, tj = ctx.cggm_active_sets(G_L + 5, G_T + 5, np.eye(q), np.zeros((p, q)), 1.0, 1.0)
+    assert len(li) == q * (q + 1) // 2 and len(ti) == p * q
+
+
+# ------------------------------------------------------------------------------------
+# coordinate passes
+# ------------------------------------------------------------------------------------
+def lambda_inputs(p, q, n, seed, lam=0.05):
+    pr = problem(p, q, n, seed=seed)
+    Lam, Th = state_at(pr)
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    G_L, G_T, Sigma, Psi = oracle.gradients(Lam, Th, Sxx, Sxy, Syy)
+    li, lj, ti, tj = oracle.active_sets(G_L, G_T, Lam, Th, lam, lam)
+    return pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi, li, lj, ti, tj
+
+
+@pytest.mark.parametrize("shape", [(40, 37, 30), (120, 150, 80), (60, 1, 40)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-4)])
+def test_lambda_sweep(ctx, shape, prec, tol):
+    pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi, li, lj, _, _ = lambda_inputs(*shape, seed=11)
+    assert len(li) > 128 or shape[1] == 1  # several batches and a ragged tail
+    D_ref = oracle.lambda_sweep(Sigma, Psi, Syy, Lam, li, lj, 0.05)
+    D = ctx.cggm_lambda_sweep(Sigma, Psi, Syy, Lam, li, lj, 0.05, precision=prec)
+    assert rel(D, D_ref) < tol
+    np.testing.assert_array_equal(D, D.T)
+
+
+def test_lambda_sweep_sparse_random_order(ctx):
+    """Scattered active coordinates (not whole rows), and the unpenalised diagonal."""
+    pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi, _, _, _, _ = lambda_inputs(50, 90, 60, seed=3)
+    rng = np.random.default_rng(0)
+    iu, ju = np.triu_indices(90)
+    keep = rng.uniform(size=iu.size) < 0.15
+    keep[iu == ju] = True
+    li, lj = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+    for pen in (True, False):
+        D_ref = oracle.lambda_sweep(Sigma, Psi, Syy, Lam, li, lj, 0.03, pen)
+        D = ctx.cggm_lambda_sweep(Sigma, Psi, Syy, Lam, li, lj, 0.03, pen, precision=0)
+        assert rel(D, D_ref) < 1e-9
+
+
+@pytest.mark.parametrize("shape", [(40, 37, 30), (150, 120, 80), (1, 30, 20), (70, 1, 50)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-4)])
+def test_theta_sweep(ctx, shape, prec, tol):
+    pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi, _, _, ti, tj = lambda_inputs(*shape, seed=17)
+    T_ref = oracle.theta_sweep(Sxx, Sxy, Sigma, Th, ti, tj, 0.05)
+    T = ctx.cggm_theta_sweep(pr.X, Sxy, Sigma, Th, ti, tj, 0.05, precision=prec)
+    assert rel(T, T_ref) < tol
+
+
+def test_sweeps_with_empty_active_set(ctx):
+    pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi, _, _, _, _ = lambda_inputs(20, 10, 15, seed=2)
+    e = np.zeros(0, dtype=np.int32)
+    assert np.all(ctx.cggm_lambda_sweep(Sigma, Psi, Syy, Lam, e, e, 0.1) == 0)
+    np.testing.assert_array_equal(ctx.cggm_theta_sweep(pr.X, Sxy, Sigma, Th, e, e, 0.1), Th)
+
+
+# ------------------------------------------------------------------------------------
+# whole solves
+# ------------------------------------------------------------------------------------
+def check_solution(pr, r_gpu, ref, f_star):
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    f_gpu = oracle.objective(r_gpu.Lambda, r_gpu.Theta, Sxx, Sxy, Syy, pr.lam_L, pr.lam_T)
+    gap = (f_gpu - f_star) / abs(f_star)
+    assert gap <= 1e-6, gap
+    assert rel(r_gpu.Lambda, ref.Lambda) <= 1e-4
+    assert rel(r_gpu.Theta, ref.Theta) <= 1e-4
+    for A, B in ((r_gpu.Lambda, ref.Lambda), (r_gpu.Theta, ref.Theta)):
+        sa, sb = np.abs(A) > 1e-3, np.abs(B) > 1e-3
+        # entries within rounding of the 1e-3 cut may fall either side
+        border = np.abs(np.abs(B) - 1e-3) < 1e-5
+        assert np.all((sa == sb) | border)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_small_chain_matches_oracle(ctx, prec):
+    pr = synth.workload("chain-gauss-p200-q100-n100")
+    ref = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, max_iter=3000)
+    f_star = ref.f
+    o = cg.make_opts(precision=prec, max_iter=3000)
+    r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, opts=o)
+    check_solution(pr, r, ref, f_star)
+
+
+def test_solve_first_iterates_track_oracle(ctx):
+    """FP64 path: the objective after each of the first iterations equals the oracle's."""
+    pr = problem(60, 40, 50, seed=8, lam=0.1)
+    for k in (1, 2, 5):
+        ref = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12, max_iter=k)
+        r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
+                           opts=cg.make_opts(precision=0, max_iter=k))
+        assert rel(r.Lambda, ref.Lambda) < 1e-8
+        assert rel(r.Theta, ref.Theta) < 1e-8
+
+
+def test_solve_warm_start_and_unpenalised_diagonal(ctx):
+    pr = problem(30, 20, 40, seed=4, lam=0.2)
+    ref = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-8, max_iter=2000,
+                       penalize_diag=False)
+    o = cg.make_opts(precision=0, penalize_diag=0, max_iter=2000)
+    r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-8, opts=o)
+    assert rel(r.Lambda, ref.Lambda) < 1e-5
+    # warm start from the answer converges immediately
+    r2 = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-6, opts=o,
+                        warm_Lambda=r.Lambda, warm_Theta=r.Theta)
+    assert r2.info["iterations"] <= 2
+
+
+def test_solve_degenerate_cases(ctx):
+    # huge penalties: Theta stays 0, Lambda diagonal
+    pr = problem(10, 6, 20, seed=9)
+    r = ctx.cggm_solve(pr.X, pr.Y, 100.0, 100.0, tol=1e-8,
+                       opts=cg.make_opts(precision=0, max_iter=500))
+    assert np.all(r.Theta == 0)
+    assert np.all(r.Lambda[~np.eye(6, dtype=bool)] == 0)
+    # p = q = 1
+    x = np.random.default_rng(0).standard_normal((50, 1))
+    y = -0.7 * x + 0.3 * np.random.default_rng(1).standard_normal((50, 1))
+    r = ctx.cggm_solve(x, y, 0.05, 0.1, tol=1e-10, opts=cg.make_opts(precision=0))
+    ref = oracle.solve(x, y, 0.05, 0.1, tol=1e-10, max_iter=1000)
+    assert abs(r.Lambda[0, 0] - ref.Lambda[0, 0]) < 1e-7 * ref.Lambda[0, 0]
+
+
+def test_solve_rejects_bad_input(ctx):
+    pr = problem(10, 6, 20, seed=9)
+    with pytest.raises(cg.CGGMError) as e:
+        ctx.cggm_solve(pr.X, pr.Y, -1.0, 0.1)
+    assert e.value.status == cg.CGGM_EINVAL
+    with pytest.raises(cg.CGGMError) as e:
+        ctx.cggm_solve(pr.X, pr.Y, 0.1, 0.1, warm_Lambda=-np.eye(6))
+    assert e.value.status == cg.CGGM_ENOTPD
+    X = pr.X.copy(); X[3, 4] = np.nan
+    with pytest.raises(cg.CGGMError) as e:
+        ctx.cggm_solve(X, pr.Y, 0.1, 0.1)
+    assert e.value.status == -8
+
+
+def test_device_inputs(ctx):
+    torch = pytest.importorskip("torch")
+    pr = problem(30, 20, 40, seed=12)
+    Xd = torch.tensor(pr.X, device="cuda:0", dtype=torch.float32)
+    Yd = torch.tensor(pr.Y, device="cuda:0", dtype=torch.float32)
+    r1 = ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-6, opts=cg.make_opts(precision=0))
+    r2 = ctx.cggm_solve(pr.X.astype(np.float32), pr.Y.astype(np.float32), pr.lam_L, pr.lam_T,
+                        tol=1e-6, opts=cg.make_opts(precision=0))
+    np.testing.assert_array_equal(r1.Lambda, r2.Lambda)
