@@ -287,18 +287,37 @@ struct Solver {
         rowsq_kernel<double><<<(unsigned)q, 256, 0, st>>>(q, n, P<double>(c->Pt), inv, P<double>(c->Pd));
     }
 
-    // f(Lam, Th) given scal[S_LOGDET] and Rt, Pt current: pieces into scal
-    void objective_pieces() {
-        const int64_t n = z.n, p = z.p, q = z.q;
+    // Theta-only pieces of f at the current Theta: 2 tr(S_xy^T Theta) and ||Theta||_1
+    void theta_pieces() {
+        const int64_t p = z.p, q = z.q;
         double *s = scal();
         double *part = P<double>(c->partial);
-        cudaMemsetAsync(s + S_SYYL, 0, 8 * (S_L1T - S_SYYL + 1), st);
-        dot_d<double>(q * q, P<double>(c->Syy), P<double>(c->Lam), part, s + S_SYYL, st);
+        cudaMemsetAsync(s + S_SXYT, 0, 8, st);
+        cudaMemsetAsync(s + S_L1T, 0, 8, st);
         dot_d<double>(p * q, P<double>(c->Sxy), P<double>(c->Th), part, s + S_SXYT, st);
-        dot_d<double>(q * n, P<double>(c->Rt), P<double>(c->Pt), part, s + S_TRACE, st);
-        l1_d<double>(q * q, P<double>(c->Lam), o.penalize_diag ? 0 : q, part, s + S_L1L, st);
         l1_d<double>(p * q, P<double>(c->Th), 0, part, s + S_L1T, st);
-        (void)n;
+    }
+
+    // f(Lam, Theta) of Eq. 1 with Lch = chol(Lam) and log|Lam| in scal[ld_slot]; the
+    // trace term is tr(Lam^-1 R^T R) / n = ||Lch^-1 R^T||_F^2 / n with R = X Theta (Rt
+    // current).  The start-of-iteration value and every Armijo trial go through this one
+    // function, so that equal arguments give bit-equal values.
+    cggm_status eval_f(Buf &Lam, Buf &Lch, int ld_slot, double *f_out) {
+        const int64_t n = z.n, q = z.q;
+        double *s = scal();
+        double *part = P<double>(c->partial);
+        CGGM_CUDA_TRY(cudaMemcpyAsync(c->Z.p, c->Rt.p, 8 * (size_t)q * n, cudaMemcpyDeviceToDevice, st));
+        trsm_lower_inplace(q, P<double>(Lch), q, P<double>(c->Z), n, n, false, st);
+        CGGM_CUDA_TRY(cudaMemsetAsync(s + S_TRACE_A, 0, 24, st));
+        dot_d<double>(q * n, P<double>(c->Z), P<double>(c->Z), part, s + S_TRACE_A, st);
+        dot_d<double>(q * q, P<double>(c->Syy), P<double>(Lam), part, s + S_SYYL_A, st);
+        l1_d<double>(q * q, P<double>(Lam), o.penalize_diag ? 0 : q, part, s + S_L1L_A, st);
+        double h[S_COUNT];
+        CGGM_CUDA_TRY(cudaMemcpyAsync(h, s, 8 * S_COUNT, cudaMemcpyDeviceToHost, st));
+        CGGM_TRY(sync_err(c));
+        *f_out = -h[ld_slot] + h[S_SYYL_A] + 2.0 * h[S_SXYT] + h[S_TRACE_A] / (double)n +
+                 lamL * h[S_L1L_A] + lamT * h[S_L1T];
+        return CGGM_OK;
     }
 
     double f_from(const double *h) const {
@@ -336,7 +355,7 @@ struct Solver {
         CGGM_TRY(factor(c->Lam, c->Lch, c->logd, S_LOGDET));
         sigma_from_factor();
 
-        const int B = o.sweep_batch > 0 ? o.sweep_batch : (sizeof(T) == 8 ? 64 : 128);
+        const int B = o.sweep_batch > 0 ? o.sweep_batch : (sizeof(T) == 8 ? 128 : 256);
         double h[S_COUNT];
         int64_t hc[2];
         bool converged = false;
@@ -351,7 +370,9 @@ struct Solver {
             // ---- products (R, P, Psi) and the gradients (Eq. 3) ----
             products_R_P();
             product_Psi();
-            objective_pieces();
+            theta_pieces();
+            double f_start = 0.0;
+            CGGM_TRY(eval_f(c->Lam, c->Lch, S_LOGDET, &f_start));
             grad_lambda<T>(q, P<double>(c->Syy), P<double>(c->Sig), (const T *)c->Psi.p,
                            P<double>(c->GL), st);
             // G_Theta = 2 S_xy + (2/n) X^T P
@@ -377,7 +398,7 @@ struct Solver {
             CGGM_CUDA_TRY(cudaMemcpyAsync(h, s, 8 * S_COUNT, cudaMemcpyDeviceToHost, st));
             CGGM_CUDA_TRY(cudaMemcpyAsync(hc, c->cnt.p, 16, cudaMemcpyDeviceToHost, st));
             CGGM_TRY(sync_err(c));
-            f = f_from(h);
+            f = f_start;
             subgrad = h[S_SUBL] + h[S_SUBT];
             nrm = h[S_NRML] + h[S_NRMT];
             {
@@ -412,11 +433,13 @@ struct Solver {
             // delta = tr(G D) + lamL (||Lam + D||_1 - ||Lam||_1)
             double *part = P<double>(c->partial);
             CGGM_CUDA_TRY(cudaMemsetAsync(s + S_GD, 0, 16, st));
+            CGGM_CUDA_TRY(cudaMemsetAsync(s + S_L1L, 0, 8, st));
             dot_d<double>(q * q, P<double>(c->GL), P<double>(c->D), part, s + S_GD, st);
+            l1_d<double>(q * q, P<double>(c->Lam), o.penalize_diag ? 0 : q, part, s + S_L1L, st);
             CGGM_CUDA_TRY(cudaMemcpyAsync(c->Lam_a.p, c->Lam.p, 8 * qq, cudaMemcpyDeviceToDevice, st));
             axpby<double>(qq, 1.0, P<double>(c->D), 1.0, P<double>(c->Lam_a), st);
             l1_d<double>(q * q, P<double>(c->Lam_a), o.penalize_diag ? 0 : q, part, s + S_L1LD, st);
-            CGGM_CUDA_TRY(cudaMemcpyAsync(h + S_GD, s + S_GD, 16, cudaMemcpyDeviceToHost, st));
+            CGGM_CUDA_TRY(cudaMemcpyAsync(h, s, 8 * S_COUNT, cudaMemcpyDeviceToHost, st));
             CGGM_TRY(sync_err(c));
             const double delta = h[S_GD] + lamL * (h[S_L1LD] - h[S_L1L]);
             double alpha = 1.0;
@@ -427,21 +450,8 @@ struct Solver {
                 axpby<double>(qq, alpha, P<double>(c->D), 1.0, P<double>(c->Lam_a), st);
                 cggm_status fs = factor(c->Lam_a, c->Lch_a, c->logd_a, S_LOGDET_A);
                 if (fs == CGGM_OK) {
-                    // tr(Lambda_a^-1 R^T R) / n = ||L_a^-1 R^T||_F^2 / n
-                    CGGM_CUDA_TRY(cudaMemcpyAsync(c->Z.p, c->Rt.p, 8 * (size_t)q * n,
-                                                  cudaMemcpyDeviceToDevice, st));
-                    trsm_lower_inplace(q, P<double>(c->Lch_a), q, P<double>(c->Z), n, n, false, st);
-                    CGGM_CUDA_TRY(cudaMemsetAsync(s + S_TRACE_A, 0, 24, st));
-                    dot_d<double>(q * n, P<double>(c->Z), P<double>(c->Z), part, s + S_TRACE_A, st);
-                    dot_d<double>(q * q, P<double>(c->Syy), P<double>(c->Lam_a), part, s + S_SYYL_A, st);
-                    l1_d<double>(q * q, P<double>(c->Lam_a), o.penalize_diag ? 0 : q, part,
-                                 s + S_L1L_A, st);
-                    CGGM_CUDA_TRY(cudaMemcpyAsync(h + S_LOGDET_A, s + S_LOGDET_A, 32,
-                                                  cudaMemcpyDeviceToHost, st));
-                    CGGM_TRY(sync_err(c));
-                    const double fa = -h[S_LOGDET_A] + h[S_SYYL_A] + 2.0 * h[S_SXYT] +
-                                      h[S_TRACE_A] / (double)n + lamL * h[S_L1L_A] +
-                                      lamT * h[S_L1T];
+                    double fa = 0.0;
+                    CGGM_TRY(eval_f(c->Lam_a, c->Lch_a, S_LOGDET_A, &fa));
                     if (std::isfinite(fa) && fa <= f + o.ls_sigma * alpha * delta) {
                         accepted = true;
                         break;
@@ -456,6 +466,7 @@ struct Solver {
             std::swap(c->Lam, c->Lam_a);
             std::swap(c->Lch, c->Lch_a);
             std::swap(c->logd, c->logd_a);
+            CGGM_CUDA_TRY(cudaMemcpyAsync(s + S_LOGDET, s + S_LOGDET_A, 8, cudaMemcpyDeviceToDevice, st));
             cudaEventRecord(ev[5], st);
             sigma_from_factor();
             // ---- Theta pass (Section 3.2) with the new Sigma ----
@@ -613,7 +624,8 @@ cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, in
     if (tol > 0.0) o.tol = tol;
     if (!(o.tol > 0.0) || o.max_iter < 0 || o.ls_max_trials < 1 || !(o.ls_beta > 0.0 && o.ls_beta < 1.0))
         return CGGM_EINVAL;
-    if (o.sweep_batch != 0 && o.sweep_batch != 32 && o.sweep_batch != 64 && o.sweep_batch != 128)
+    if (o.sweep_batch != 0 && o.sweep_batch != 32 && o.sweep_batch != 64 && o.sweep_batch != 128 &&
+        !(o.sweep_batch == 256 && o.precision == CGGM_MIXED))
         return CGGM_EINVAL;
     if (info) memset(info, 0, sizeof(*info));
     CGGM_TRY(set_device(c));
@@ -786,7 +798,7 @@ cggm_status cggm_lambda_sweep(cggm_ctx *c, int64_t q, const double *Sigma, const
         CGGM_TRY(lambda_sweep<double>(q, P<double>(c->Sig), P<double>(c->work), P<double>(c->Sd),
                                       P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), m,
                                       P<int32_t>(c->li), P<int32_t>(c->lj), lam_L, lamd,
-                                      P<double>(c->D), P<double>(c->U), 64, c->planL, c->scr, c->st));
+                                      P<double>(c->D), P<double>(c->U), 128, c->planL, c->scr, c->st));
     } else {
         CGGM_TRY(ensure(c->U, 4 * qq));
         CGGM_TRY(ensure(c->Sig_f, 4 * qq));
@@ -797,7 +809,7 @@ cggm_status cggm_lambda_sweep(cggm_ctx *c, int64_t q, const double *Sigma, const
         CGGM_TRY(lambda_sweep<float>(q, P<float>(c->Sig_f), P<float>(c->Psi), P<double>(c->Sd),
                                      P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), m,
                                      P<int32_t>(c->li), P<int32_t>(c->lj), lam_L, lamd,
-                                     P<double>(c->D), P<float>(c->U), 128, c->planL, c->scr, c->st));
+                                     P<double>(c->D), P<float>(c->U), 256, c->planL, c->scr, c->st));
     }
     CGGM_TRY(store_double(c, D_out, c->D.p, qq));
     return sync_err(c);
@@ -841,7 +853,7 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
         CGGM_TRY(theta_sweep<double>(p, q, P<double>(c->Sxx), P<double>(c->Xd), P<double>(c->Sig),
                                      P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
                                      P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<double>(c->dV),
-                                     64, c->planT, c->scr, c->st));
+                                     128, c->planT, c->scr, c->st));
     } else {
         CGGM_TRY(ensure(c->Xt_f, 4 * (size_t)p * n));
         CGGM_TRY(ensure(c->Sig_f, 4 * qq));
@@ -854,7 +866,7 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
         CGGM_TRY(theta_sweep<float>(p, q, P<float>(c->Sxx), P<double>(c->Xd), P<float>(c->Sig_f),
                                     P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
                                     P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<float>(c->dV),
-                                    128, c->planT, c->scr, c->st));
+                                    256, c->planT, c->scr, c->st));
     }
     CGGM_TRY(store_double(c, Theta_out, c->Th.p, pq));
     return sync_err(c);

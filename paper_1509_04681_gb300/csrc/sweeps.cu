@@ -26,8 +26,7 @@
 namespace cggm {
 
 namespace {
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
+constexpr int kThreads = 256;
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
@@ -178,12 +177,61 @@ __global__ void theta_plan_kernel(int64_t m, const int32_t *ti, const int32_t *t
 // ---------------------------------------------------------------------------------
 // shared pieces of the sweep kernels
 // ---------------------------------------------------------------------------------
+// Per-coordinate step constants, formed in double in phase A and stored in the cache
+// type T (hi + lo pairs where the value carries the result):
+//   u = c - base/a, r = lam/a, vp = u - r - c, vm = u + r - c, ai = 1/a, mc = -c.
+// With acc = the in-batch correction sum, w = u - acc/a and the step is vp - acc/a
+// (w > r), vm - acc/a (w < -r), -c otherwise (zero curvature: always -c).
+enum { PRE_UH, PRE_UL, PRE_VPH, PRE_VPL, PRE_VMH, PRE_VML, PRE_AI, PRE_R, PRE_MC, PRE_N };
+
+template <typename T>
+__device__ __forceinline__ void split(double v, T *hi, T *lo) {
+    *hi = (T)v;
+    *lo = (T)(v - (double)*hi);
+}
+
+template <typename T>
+__device__ void step_constants(double base, double a, double c, double lam, T *pre, int B, int l) {
+    T *o = pre;
+    if (a > 0.0 && isfinite(a)) {
+        const double ai = 1.0 / a;
+        const double u = c - base * ai, r = lam * ai;
+        split<T>(u, o + PRE_UH * B + l, o + PRE_UL * B + l);
+        split<T>(u - r - c, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
+        split<T>(u + r - c, o + PRE_VMH * B + l, o + PRE_VML * B + l);
+        o[PRE_AI * B + l] = (T)ai;
+        o[PRE_R * B + l] = (T)r;
+    } else {  // zero curvature: w = 0 inside [-1, 1] selects -c
+        o[PRE_UH * B + l] = T(0); o[PRE_UL * B + l] = T(0);
+        split<T>(-c, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
+        split<T>(-c, o + PRE_VMH * B + l, o + PRE_VML * B + l);
+        o[PRE_AI * B + l] = T(0);
+        o[PRE_R * B + l] = T(1);
+    }
+    o[PRE_MC * B + l] = (T)(-c);
+}
+
+__device__ __forceinline__ void decode_pair(int e, int &l, int &l1) {
+    // e = l (l - 1) / 2 + l1, 0 <= l1 < l
+    l = (int)((1.0f + sqrtf(1.0f + 8.0f * (float)e)) * 0.5f);
+    while (l * (l - 1) / 2 > e) l--;
+    while ((l + 1) * l / 2 <= e) l++;
+    l1 = e - l * (l - 1) / 2;
+}
+
+// In-batch coefficients are stored column by column: the entries coef(l2, l) for all
+// later l2 > l are contiguous, at colbase(l) + (l2 - l - 1), so that at step l the lanes
+// of the warp read consecutive words.
+__host__ __device__ __forceinline__ int colbase(int l, int B) { return l * (2 * B - l - 1) / 2; }
+// shared-memory slots for the coefficients (16-byte multiple with copy slack)
+__host__ __device__ __forceinline__ int coef_slots(int B) { return ((B * (B - 1) / 2 + 8) + 3) & ~3; }
+
+constexpr int kRowsC = 16;  // rows of the band staged per round in phase C
+
 struct SmemLayout {
-    // per-warp staging of gathered row segments: kWarps * 3 * K values of T
-    // reduction buffer: kWarps * B * 3 doubles
-    // batch metadata: idx[K], idx2[K], pa[B], pb[B]
-    // phase B: base[B], ainv[B], c[B], lam[B], coef[B*(B-1)/2] doubles
-    size_t stage, red, meta, phb;
+    size_t meta;  // idx[K], idx2[K], pa[B], pb[B], lptr[K+1], lent[K] (ints)
+    size_t work;  // union: phase B coef[B(B-1)/2] (T);
+                  //        phase C mu[B], Sigma rows [kRowsC][K], cache rows [kRowsC][K] (T)
     size_t total;
 };
 
@@ -191,63 +239,73 @@ template <typename T>
 __host__ __device__ inline SmemLayout smem_layout(int B) {
     const int K = 2 * B;
     SmemLayout s;
-    s.stage = 0;
-    size_t off = (size_t)kWarps * 3 * K * sizeof(T);
+    s.meta = 0;
+    size_t off = (size_t)(2 * K + 2 * B + (K + 1) + K) * sizeof(int32_t);
     off = (off + 15) & ~size_t(15);
-    s.red = off;
-    off += (size_t)kWarps * B * 3 * sizeof(double);
-    s.meta = off;
-    off += (size_t)(2 * K + 2 * B) * sizeof(int32_t);
-    off = (off + 15) & ~size_t(15);
-    s.phb = off;
-    off += (size_t)(4 * B + (size_t)B * (B - 1) / 2) * sizeof(double);
-    s.total = off;
+    s.work = off;
+    const size_t phb = ((size_t)coef_slots(B) + PRE_N * B + 8) * sizeof(T);
+    const size_t phc = (size_t)(B + 4) * sizeof(T) + (size_t)kRowsC * (K + 4) * sizeof(T) * 2;
+    s.total = off + (phb > phc ? phb : phc);
     return s;
 }
 
-// Forward substitution of one batch on warp 0.  For l = 0..nb-1:
+// Forward substitution of one batch on warp 0: for l = 0..nb-1,
 //   b_l = base_l + sum_{l' < l} coef(l, l') mu_l',  mu_l = -c_l + S_{lam_l/a_l}(c_l - b_l/a_l)
-// (exact minimiser of (a/2) mu^2 + b mu + lam |c + mu|, Appendix A.1).  ainv_l = 0 marks a
-// coordinate whose curvature is zero (its minimiser is mu = -c).  coef is the strictly
-// lower triangle, row-major packed: coef(l, l') at l (l - 1) / 2 + l'.
-template <int NS>
-__device__ void forward_substitution(int nb, const double *base, const double *ainv,
-                                     const double *cc, const double *lam, const double *coef,
-                                     double *mu_out, int *err) {
+// (exact minimiser of (a/2) mu^2 + b mu + lam |c + mu|, Appendix A.1), written with the
+// step constants above.  coef is the strictly lower triangle, row-major packed, in shared
+// memory (column-packed, see colbase).  Lane k owns coordinates 32 s + k; at step l every lane forms the candidate
+// step of its own coordinate of the current panel and the owner's candidate is broadcast,
+// so the dependent chain per coordinate is a few T operations and one warp shuffle.
+template <typename T, int NS>
+__device__ void forward_substitution(int nb, int B, const T *__restrict__ pre,
+                                     const T *coef, double *mu_out, int *err) {
+    // pre[] holds, for padding coordinates l >= nb, constants that give mu = 0 whatever
+    // the correction sum (ai = 0, u = 0, r = 1, mc = 0), so panels run all 32 steps
+    // without branches.
     const int lane = threadIdx.x & 31;
-    double acc[NS];
+    T acc[NS];
 #pragma unroll
-    for (int s = 0; s < NS; s++) acc[s] = 0.0;
-    for (int l = 0; l < nb; l++) {
-        const int owner = l & 31, slot = l >> 5;
-        double mu = 0.0;
-        if (lane == owner) {
-            double mine = 0.0;
+    for (int s = 0; s < NS; s++) acc[s] = T(0);
+    bool bad = false;
 #pragma unroll
-            for (int s = 0; s < NS; s++)
-                if (s == slot) mine = acc[s];
-            const double c = cc[l], ai = ainv[l];
-            if (ai == 0.0) {
-                mu = -c;
-            } else {
-                const double b = base[l] + mine;
-                mu = -c + soft_threshold(c - b * ai, lam[l] * ai);
-            }
-            if (!isfinite(mu)) {
-                set_err(err, DEV_NONFINITE);
-                mu = 0.0;
-            }
-            mu_out[l] = mu;
+    for (int s = 0; s < NS; s++) {
+        if (s * 32 >= nb) break;
+        const int lo = s * 32 + lane;
+        const T uh = pre[PRE_UH * B + lo], ul = pre[PRE_UL * B + lo];
+        const T vph = pre[PRE_VPH * B + lo], vpl = pre[PRE_VPL * B + lo];
+        const T vmh = pre[PRE_VMH * B + lo], vml = pre[PRE_VML * B + lo];
+        const T ai = pre[PRE_AI * B + lo], r = pre[PRE_R * B + lo], mc = pre[PRE_MC * B + lo];
+        // this panel's own coefficients coef(lo, 32 s + o) for o < lane, in registers
+        T cw[32];
+#pragma unroll
+        for (int o = 0; o < 32; o++) {
+            const int l = s * 32 + o;
+            cw[o] = (lane > o) ? coef[colbase(l, B) + (lo - l - 1)] : T(0);
         }
-        mu = __shfl_sync(0xffffffffu, mu, owner);
-        if (mu != 0.0) {
+        T mymu = T(0);
 #pragma unroll
-            for (int s = 0; s < NS; s++) {
-                const int l2 = s * 32 + lane;
-                if (l2 > l && l2 < nb) acc[s] = fma(coef[(size_t)l2 * (l2 - 1) / 2 + l], mu, acc[s]);
+        for (int o = 0; o < 32; o++) {
+            const int l = s * 32 + o;
+            const T w = fma(-acc[s], ai, uh) + ul;
+            const T mp = fma(-acc[s], ai, vph) + vpl;
+            const T mm = fma(-acc[s], ai, vmh) + vml;
+            const T cand = (w > r) ? mp : ((w < -r) ? mm : mc);
+            const T mu = __shfl_sync(0xffffffffu, cand, o);
+            mymu = (lane == o) ? cand : mymu;
+            acc[s] = fma(cw[o], mu, acc[s]);
+#pragma unroll
+            for (int s2 = s + 1; s2 < NS; s2++) {
+                const int l2 = s2 * 32 + lane;
+                acc[s2] = fma(coef[colbase(l, B) + (l2 - l - 1)], mu, acc[s2]);
             }
+        }
+        if (lo < nb) {
+            double m = (double)mymu;
+            if (!isfinite(m)) { bad = true; m = 0.0; }
+            mu_out[lo] = m;
         }
     }
+    if (bad) set_err(err, DEV_NONFINITE);
 }
 
 // Ticket: returns true in the last CTA to arrive (all CTAs' prior global writes visible).
@@ -267,13 +325,162 @@ __device__ __forceinline__ bool last_cta(unsigned *ticket, unsigned nblocks) {
     return s_last != 0;
 }
 
+// Three dot products of length len over contiguous rows by the whole CTA:
+//   r0 = x0 . y0, r1 = x1 . y0, r2 = x2 . y1   (y rows read through L2); valid in thread 0
 template <typename T>
-__device__ __forceinline__ double ldg_cg(const T *p) {
-    return (double)__ldcg(p);
+__device__ void cta_dot3(int64_t len, const T *x0, const T *x1, const T *x2, const T *y0,
+                         const T *y1, double *r) {
+    T a0 = T(0), a1 = T(0), a2 = T(0);
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
+        const T u0 = __ldcg(y0 + t), u1 = __ldcg(y1 + t);
+        a0 = fma(x0[t], u0, a0);
+        a1 = fma(x1[t], u0, a1);
+        a2 = fma(x2[t], u1, a2);
+    }
+    r[0] = block_sum((double)a0);
+    r[1] = block_sum((double)a1);
+    r[2] = block_sum((double)a2);
+}
+
+template <typename T>
+__device__ double cta_dot1(int64_t len, const T *x0, const T *y0) {
+    T a0 = T(0);
+    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) a0 = fma(x0[t], __ldcg(y0 + t), a0);
+    return block_sum((double)a0);
+}
+
+// Load the batch metadata of batch b into shared memory.
+__device__ void load_meta(const BatchPlan &plan, int64_t b, int B, bool theta, int32_t *sidx,
+                          int32_t *sidx2, int32_t *spa, int32_t *spb, int32_t *slptr,
+                          int32_t *slent) {
+    const int K = 2 * B;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        sidx[k] = plan.idx[b * K + k];
+        if (theta) sidx2[k] = plan.idx2[b * K + k];
+        slent[k] = plan.lent[b * K + k];
+    }
+    for (int k = threadIdx.x; k <= K; k += blockDim.x) slptr[k] = plan.lptr[b * (K + 1) + k];
+    for (int l = threadIdx.x; l < B; l += blockDim.x) {
+        spa[l] = plan.pa[b * B + l];
+        spb[l] = plan.pb[b * B + l];
+    }
+    __syncthreads();
+}
+
+// Copy n elements global -> shared (both 16-byte aligned, n rounded up to 16 bytes; the
+// buffers have that slack) with 16-byte loads, eight in flight per thread.
+template <typename T>
+__device__ void copy_to_smem(const T *g, T *sm, int n) {
+    const int nv = (int)((n * sizeof(T) + 15) / 16);
+    const int4 *gv = reinterpret_cast<const int4 *>(g);
+    int4 *sv = reinterpret_cast<int4 *>(sm);
+    for (int base = threadIdx.x; base < nv; base += 8 * blockDim.x) {
+        int4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = base + u * blockDim.x;
+            if (k < nv) v[u] = __ldcg(gv + k);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int k = base + u * blockDim.x;
+            if (k < nv) sv[k] = v[u];
+        }
+    }
+}
+
+// Phase B body shared by both passes: stage the coefficients and step constants, run
+// the substitution.
+template <typename T, int NS>
+__device__ void phase_b(int nb, int B, const T *gcoef, const T *gpre, T *scoef, T *spre,
+                        double *mu, int *err) {
+    const int ncoef = colbase(nb - 1, B) + 1;  // through column nb - 2 (all entries used)
+    copy_to_smem<T>(gcoef, scoef, ncoef);
+    copy_to_smem<T>(gpre, spre, PRE_N * B);
+    __syncthreads();
+    for (int l = nb + threadIdx.x; l < B; l += blockDim.x) {  // padding: mu = 0
+        for (int k = 0; k < PRE_N; k++) spre[k * B + l] = T(0);
+        spre[PRE_R * B + l] = T(1);
+    }
+    const int nc = colbase(nb - 1, B) + 1, ncb = B * (B - 1) / 2;
+    for (int e = nc + threadIdx.x; e < ncb; e += blockDim.x) scoef[e] = T(0);
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) forward_substitution<T, NS>(nb, B, spre, scoef, mu, err);
+    __syncthreads();
+}
+
+// Phase C body shared by both passes.  For every row t of this CTA's band and every
+// distinct target index k: cache[t][tgt[k]] += sum over the list of k of
+// mu_l Sigma[t][partner[e]].  Rows are processed kRowsC at a time: the Sigma values at
+// the partner columns and the cache values at the target columns are first staged in
+// shared memory by all threads (independent loads), then combined, then written back.
+template <typename T>
+__device__ void phase_c(int nb, int ntgt, const int32_t *tgt, const int32_t *part,
+                        const int32_t *lptr, const int32_t *lent, const T *__restrict__ Sig,
+                        int64_t q, T *cache, int64_t ld, int64_t r0, int64_t r1, T *work,
+                        const double *mu) {
+    const int nent = lptr[ntgt];
+    T *smu = work;
+    T *sS = smu + ((nb + 3) & ~3);
+    for (int l = threadIdx.x; l < nb; l += blockDim.x) smu[l] = (T)__ldcg(mu + l);
+    const int npart = nent;  // one staged Sigma value per entry
+    T *sC = sS + (size_t)kRowsC * ((npart + 3) & ~3);
+    const int lds = (npart + 3) & ~3, ldc = (ntgt + 3) & ~3;
+    for (int64_t t0 = r0; t0 < r1; t0 += kRowsC) {
+        const int nr = (int)((r1 - t0) < kRowsC ? (r1 - t0) : kRowsC);
+        __syncthreads();
+        const int tot_s = nr * npart, tot_c = nr * ntgt;
+        for (int base = threadIdx.x; base < tot_s; base += 8 * blockDim.x) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int x = base + u * blockDim.x;
+                if (x < tot_s) {
+                    const int rr = x / npart, e = x - rr * npart;
+                    v[u] = Sig[(t0 + rr) * q + part[lent[e] & 0xffff]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int x = base + u * blockDim.x;
+                if (x < tot_s) {
+                    const int rr = x / npart, e = x - rr * npart;
+                    sS[(size_t)rr * lds + e] = v[u];
+                }
+            }
+        }
+        for (int base = threadIdx.x; base < tot_c; base += 8 * blockDim.x) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int x = base + u * blockDim.x;
+                if (x < tot_c) {
+                    const int rr = x / ntgt, k = x - rr * ntgt;
+                    v[u] = __ldcg(cache + (t0 + rr) * ld + tgt[k]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int x = base + u * blockDim.x;
+                if (x < tot_c) {
+                    const int rr = x / ntgt, k = x - rr * ntgt;
+                    sC[(size_t)rr * ldc + k] = v[u];
+                }
+            }
+        }
+        __syncthreads();
+        for (int x = threadIdx.x; x < tot_c; x += blockDim.x) {
+            const int rr = x / ntgt, k = x - rr * ntgt;
+            const T *srow = sS + (size_t)rr * lds;
+            T acc = T(0);
+            for (int e = lptr[k]; e < lptr[k + 1]; e++) acc = fma(smu[lent[e] >> 16], srow[e], acc);
+            cache[(t0 + rr) * ld + tgt[k]] = sC[(size_t)rr * ldc + k] + acc;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------------
-// Lambda sweep kernel
+// Lambda sweep kernel.  Cache: Ut = U^T (q x q), Ut[r][t] = U[t][r] = (D Sigma)[t][r].
 // ---------------------------------------------------------------------------------
 template <typename T, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -281,133 +488,96 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                     const double *__restrict__ Sd, const double *__restrict__ Pd,
                     const double *__restrict__ G, const double *__restrict__ Lam, int64_t m,
                     const int32_t *__restrict__ ai, const int32_t *__restrict__ aj,
-                    double lam_off, double lam_diag, double *D, T *U, int B, BatchPlan plan,
+                    double lam_off, double lam_diag, double *D, T *Ut, int B, BatchPlan plan,
                     SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemLayout L = smem_layout<T>(B);
     const int K = 2 * B;
-    T *stage = reinterpret_cast<T *>(smem + L.stage);
-    double *red = reinterpret_cast<double *>(smem + L.red);
     int32_t *sidx = reinterpret_cast<int32_t *>(smem + L.meta);
     int32_t *spa = sidx + 2 * K;
     int32_t *spb = spa + B;
-    double *sbase = reinterpret_cast<double *>(smem + L.phb);
-    double *sainv = sbase + B, *sc = sainv + B, *slam = sc + B, *scoef = slam + B;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *slptr = spb + B;
+    int32_t *slent = slptr + K + 1;
+    unsigned char *work = smem + L.work;
     const unsigned nblk = gridDim.x;
-    T *sub1 = reinterpret_cast<T *>(scr.sub1);  // Sigma[I, I]
-    T *sub2 = reinterpret_cast<T *>(scr.sub2);  // Psi[I, I]
-
-    // rows of U / Sigma / Psi owned by this CTA in phase A
+    T *pre = reinterpret_cast<T *>(scr.sub1);   // [PRE_N][B]
+    T *gcoef = reinterpret_cast<T *>(scr.sub2); // [B(B-1)/2]
     const int64_t rows_per = (q + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)nblk * blockDim.x;
 
     for (int64_t b = 0; b < plan.nbatch; b++) {
         const int64_t s = b * B;
         const int nb = (int)((m - s) < B ? (m - s) : B);
         const int nidx = plan.nidx[b];
-        for (int k = threadIdx.x; k < K; k += blockDim.x) sidx[k] = plan.idx[b * K + k];
-        for (int l = threadIdx.x; l < B; l += blockDim.x) {
-            spa[l] = plan.pa[b * B + l];
-            spb[l] = plan.pb[b * B + l];
-        }
-        __syncthreads();
+        load_meta(plan, b, B, false, sidx, nullptr, spa, spb, slptr, slent);
 
-        // ---------------- phase A: partial dots over this CTA's rows ----------------
-        double p1[NS], p2[NS], p3[NS];
-#pragma unroll
-        for (int s2 = 0; s2 < NS; s2++) p1[s2] = p2[s2] = p3[s2] = 0.0;
-        T *sU = stage + (size_t)warp * 3 * K;
-        T *sP = sU + K;
-        T *sS = sP + K;
-        for (int64_t t = r0 + warp; t < r1; t += kWarps) {
-            const T *Ur = U + t * q, *Pr = Psi + t * q, *Sr = Sig + t * q;
-            for (int k = lane; k < nidx; k += 32) {
-                const int64_t c = sidx[k];
-                sU[k] = __ldcg(Ur + c);
-                sP[k] = Pr[c];
-                sS[k] = Sr[c];
-            }
-            __syncwarp();
-#pragma unroll
-            for (int s2 = 0; s2 < NS; s2++) {
-                const int l = s2 * 32 + lane;
-                if (l < nb) {
-                    const int pa = spa[l], pb = spb[l];
-                    const double ub = (double)sU[pb];
-                    p1[s2] = fma((double)sS[pa], ub, p1[s2]);  // Sigma_{t a} U_{t b}
-                    p2[s2] = fma((double)sP[pa], ub, p2[s2]);  // Psi_{t a} U_{t b}
-                    p3[s2] = fma((double)sP[pb], (double)sU[pa], p3[s2]);  // Psi_{t b} U_{t a}
+        // ---- phase A: dots and step constants (two coordinates per CTA in one pass) ----
+        for (int l = blockIdx.x; l < nb; l += 2 * nblk) {
+            const int lb = l + (int)nblk;
+            const bool two = lb < nb;
+            const int64_t i0 = ai[s + l], j0 = aj[s + l];
+            const int64_t i1 = two ? ai[s + lb] : i0, j1 = two ? aj[s + lb] : j0;
+            // (Sigma D Sigma)_ij = Sigma_i . U_{:,j}, (Psi D Sigma)_ij = Psi_i . U_{:,j},
+            // (Psi D Sigma)_ji = Psi_j . U_{:,i}
+            const T *x0 = Sig + i0 * q, *x1 = Psi + i0 * q, *x2 = Psi + j0 * q;
+            const T *y0 = Ut + j0 * q, *y1 = Ut + i0 * q;
+            const T *z0 = Sig + i1 * q, *z1 = Psi + i1 * q, *z2 = Psi + j1 * q;
+            const T *w0 = Ut + j1 * q, *w1 = Ut + i1 * q;
+            T a0 = T(0), a1 = T(0), a2 = T(0), b0 = T(0), b1 = T(0), b2 = T(0);
+            for (int64_t t = threadIdx.x; t < q; t += blockDim.x) {
+                const T u0 = __ldcg(y0 + t), u1 = __ldcg(y1 + t);
+                a0 = fma(x0[t], u0, a0);
+                a1 = fma(x1[t], u0, a1);
+                a2 = fma(x2[t], u1, a2);
+                if (two) {
+                    const T v0 = __ldcg(w0 + t), v1 = __ldcg(w1 + t);
+                    b0 = fma(z0[t], v0, b0);
+                    b1 = fma(z1[t], v0, b1);
+                    b2 = fma(z2[t], v1, b2);
                 }
             }
-            __syncwarp();
-        }
-        // gathered submatrices Sigma[I, I], Psi[I, I] (rows split over CTAs)
-        for (int k = blockIdx.x; k < nidx; k += nblk) {
-            const int64_t r = sidx[k];
-            for (int k2 = threadIdx.x; k2 < nidx; k2 += blockDim.x) {
-                sub1[(size_t)k * K + k2] = Sig[r * q + sidx[k2]];
-                sub2[(size_t)k * K + k2] = Psi[r * q + sidx[k2]];
-            }
-        }
-        // CTA reduction of the per-warp partials (fixed order)
-#pragma unroll
-        for (int s2 = 0; s2 < NS; s2++) {
-            const int l = s2 * 32 + lane;
-            if (l < B) {
-                red[((size_t)warp * B + l) * 3 + 0] = p1[s2];
-                red[((size_t)warp * B + l) * 3 + 1] = p2[s2];
-                red[((size_t)warp * B + l) * 3 + 2] = p3[s2];
-            }
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < nb * 3; e += blockDim.x) {
-            double acc = 0.0;
-            for (int w = 0; w < kWarps; w++) acc += red[(size_t)w * B * 3 + e];
-            scr.partial[(size_t)blockIdx.x * B * 3 + e] = acc;
-        }
-
-        // ---------------- phase B: last CTA ----------------
-        if (last_cta(scr.ticket, nblk)) {
-            for (int e = threadIdx.x; e < nb * 3; e += blockDim.x) {
-                double acc = 0.0;
-                for (unsigned c = 0; c < nblk; c++) acc += __ldcg(scr.partial + (size_t)c * B * 3 + e);
-                red[e] = acc;  // reuse: red[l*3 + k]
-            }
-            __syncthreads();
-            for (int l = threadIdx.x; l < nb; l += blockDim.x) {
-                const int64_t i = ai[s + l], j = aj[s + l];
-                const double s1 = red[l * 3 + 0], s2v = red[l * 3 + 1], s3 = red[l * 3 + 2];
-                double a, bb;
+            double d[6];
+            d[0] = block_sum((double)a0);
+            d[1] = block_sum((double)a1);
+            d[2] = block_sum((double)a2);
+            d[3] = block_sum((double)b0);
+            d[4] = block_sum((double)b1);
+            d[5] = block_sum((double)b2);
+            const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
+            if (which >= 0) {
+                const int lw = which ? lb : l;
+                const int64_t i = which ? i1 : i0, j = which ? j1 : j0;
+                const double *dd = d + 3 * which;
+                double a, bb, lam;
                 if (i != j) {
-                    const double sij = ldg_cg(Sig + i * q + j), pij = ldg_cg(Psi + i * q + j);
+                    const double sij = (double)Sig[i * q + j], pij = (double)Psi[i * q + j];
                     a = sij * sij + Sd[i] * Sd[j] + Sd[i] * Pd[j] + Sd[j] * Pd[i] + 2.0 * sij * pij;
-                    bb = G[i * q + j] + s1 + s2v + s3;
-                    slam[l] = lam_off;
+                    bb = G[i * q + j] + dd[0] + dd[1] + dd[2];
+                    lam = lam_off;
                 } else {
                     a = Sd[i] * Sd[i] + 2.0 * Sd[i] * Pd[i];
-                    bb = G[i * q + i] + s1 + 2.0 * s2v;
-                    slam[l] = lam_diag;
+                    bb = G[i * q + i] + dd[0] + 2.0 * dd[1];
+                    lam = lam_diag;
                 }
-                sbase[l] = bb;
-                sainv[l] = (a > 0.0) ? 1.0 / a : 0.0;
-                sc[l] = Lam[i * q + j];
+                step_constants<T>(bb, a, Lam[i * q + j], lam, pre, B, lw);
             }
-            // coefficients of the in-batch corrections (packed strict lower triangle)
-            const size_t ncoef = (size_t)nb * (nb - 1) / 2;
-            for (size_t e = threadIdx.x; e < ncoef; e += blockDim.x) {
-                // invert e = l (l - 1) / 2 + l'
-                int l = (int)((1.0 + sqrt(1.0 + 8.0 * (double)e)) * 0.5);
-                while ((size_t)l * (l - 1) / 2 > e) l--;
-                while ((size_t)(l + 1) * l / 2 <= e) l++;
-                const int l1 = (int)(e - (size_t)l * (l - 1) / 2);
-                const int pi = spa[l], pj = spb[l];   // coordinate l = (i, j)
-                const int pa = spa[l1], pb = spb[l1]; // earlier coordinate l1 = (a, b)
-                auto S = [&](int x, int y) { return ldg_cg(sub1 + (size_t)x * K + y); };
-                auto P = [&](int x, int y) { return ldg_cg(sub2 + (size_t)x * K + y); };
-                double c1, c2, c3;
+        }
+        {
+            // coefficient of the correction of coordinate l = (i, j) by the earlier step of
+            // l1 = (a, b):  (Sigma dD Sigma)_ij + (Psi dD Sigma)_ij + (Psi dD Sigma)_ji per unit
+            // step, dD = E_ab + E_ba (one term when a == b); doubled middle term on the diagonal
+            const int ncoef = nb * (nb - 1) / 2;
+            for (int64_t e = gtid; e < ncoef; e += gthreads) {
+                int l, l1;
+                decode_pair((int)e, l, l1);
+                const int64_t pi = sidx[spa[l]], pj = sidx[spb[l]];
+                const int64_t pa = sidx[spa[l1]], pb = sidx[spb[l1]];
+                auto S = [&](int64_t x, int64_t y) -> T { return Sig[x * q + y]; };
+                auto P = [&](int64_t x, int64_t y) -> T { return Psi[x * q + y]; };
+                T c1, c2, c3;
                 if (pa != pb) {
                     c1 = S(pi, pa) * S(pb, pj) + S(pi, pb) * S(pa, pj);
                     c2 = P(pi, pa) * S(pb, pj) + P(pi, pb) * S(pa, pj);
@@ -417,12 +587,14 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                     c2 = P(pi, pa) * S(pa, pj);
                     c3 = P(pj, pa) * S(pa, pi);
                 }
-                scoef[e] = (pi != pj) ? (c1 + c2 + c3) : (c1 + 2.0 * c2);
+                gcoef[colbase(l1, B) + (l - l1 - 1)] = (pi != pj) ? (c1 + c2 + c3) : (c1 + T(2) * c2);
             }
-            __syncthreads();
-            if (warp == 0)
-                forward_substitution<NS>(nb, sbase, sainv, sc, slam, scoef, scr.mu, scr.err);
-            __syncthreads();
+        }
+
+        // ---- phase B: last CTA runs the coordinate steps in order ----
+        if (last_cta(scr.ticket, nblk)) {
+            phase_b<T, NS>(nb, B, gcoef, pre, reinterpret_cast<T *>(work),
+                           reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
             for (int l = threadIdx.x; l < nb; l += blockDim.x) {
                 const int64_t i = ai[s + l], j = aj[s + l];
                 const double mu = scr.mu[l];
@@ -432,33 +604,15 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
-        // ---------------- phase C: U rows += mu Sigma rows ----------------
-        {
-            const int32_t *lptr = plan.lptr + b * (K + 1);
-            const int32_t *lent = plan.lent + b * K;
-            const int64_t nchunk = (q + 31) / 32;
-            const int64_t items = (int64_t)nidx * nchunk;
-            for (int64_t it = (int64_t)blockIdx.x * kWarps + warp; it < items;
-                 it += (int64_t)nblk * kWarps) {
-                const int k = (int)(it / nchunk);
-                const int64_t t = (it % nchunk) * 32 + lane;
-                if (t >= q) continue;
-                const int64_t u = sidx[k];
-                double acc = 0.0;
-                for (int e = lptr[k]; e < lptr[k + 1]; e++) {
-                    const int ent = lent[e];
-                    const int l = ent >> 16, pp = ent & 0xffff;
-                    acc = fma(__ldcg(scr.mu + l), (double)Sig[(int64_t)sidx[pp] * q + t], acc);
-                }
-                U[u * q + t] = (T)((double)__ldcg(U + u * q + t) + acc);
-            }
-        }
+        // ---- phase C: Ut[t][u] += sum mu Sigma[t][partner] over this CTA's rows t ----
+        phase_c<T>(nb, nidx, sidx, sidx, slptr, slent, Sig, q, Ut, q, r0, r1,
+                   reinterpret_cast<T *>(work), scr.mu);
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
     }
 }
 
 // ---------------------------------------------------------------------------------
-// Theta sweep kernel
+// Theta sweep kernel.  Cache: dVt = (Delta V)^T (q x p), dVt[j][t] = (Delta Theta Sigma)[t][j].
 // ---------------------------------------------------------------------------------
 template <typename T, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -466,142 +620,85 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                    const T *__restrict__ Sig, const double *__restrict__ Sd,
                    const double *__restrict__ W, double *Theta, int64_t m,
                    const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam,
-                   T *dV, int B, BatchPlan plan, SweepScratch scr) {
+                   T *dVt, int B, BatchPlan plan, SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
     const SmemLayout L = smem_layout<T>(B);
     const int K = 2 * B;
-    T *stage = reinterpret_cast<T *>(smem + L.stage);
-    double *red = reinterpret_cast<double *>(smem + L.red);
     int32_t *sI = reinterpret_cast<int32_t *>(smem + L.meta);
     int32_t *sJ = sI + K;
     int32_t *spa = sJ + K;
     int32_t *spb = spa + B;
-    double *sbase = reinterpret_cast<double *>(smem + L.phb);
-    double *sainv = sbase + B, *sc = sainv + B, *slam = sc + B, *scoef = slam + B;
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *slptr = spb + B;
+    int32_t *slent = slptr + K + 1;
+    unsigned char *work = smem + L.work;
     const unsigned nblk = gridDim.x;
-    T *sub1 = reinterpret_cast<T *>(scr.sub1);  // Sxx[I, I]
-    T *sub2 = reinterpret_cast<T *>(scr.sub2);  // Sigma[J, J]
+    T *pre = reinterpret_cast<T *>(scr.sub1);
+    T *gcoef = reinterpret_cast<T *>(scr.sub2);
+    const int64_t rows_per = (q + nblk - 1) / nblk;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t gthreads = (int64_t)nblk * blockDim.x;
 
     for (int64_t b = 0; b < plan.nbatch; b++) {
         const int64_t s = b * B;
         const int nb = (int)((m - s) < B ? (m - s) : B);
-        const int nI = plan.nidx[b], nJ = plan.nidx2[b];
-        for (int k = threadIdx.x; k < K; k += blockDim.x) {
-            sI[k] = plan.idx[b * K + k];
-            sJ[k] = plan.idx2[b * K + k];
-        }
-        for (int l = threadIdx.x; l < B; l += blockDim.x) {
-            spa[l] = plan.pa[b * B + l];
-            spb[l] = plan.pb[b * B + l];
-        }
-        __syncthreads();
-        // rows of dV that can be nonzero: those at or before the batch's first row
+        const int nI = plan.nidx[b];
+        load_meta(plan, b, B, true, sI, sJ, spa, spb, slptr, slent);
+        // rows of Delta V that can be nonzero: those at or before the batch's first row
         const int64_t tmax = (int64_t)ti[s] + 1;
-        const int64_t rows_per = (tmax + nblk - 1) / nblk;
-        const int64_t r0 = (int64_t)blockIdx.x * rows_per;
-        const int64_t r1 = (r0 + rows_per) < tmax ? (r0 + rows_per) : tmax;
 
-        // ---------------- phase A ----------------
-        double p1[NS];
-#pragma unroll
-        for (int s2 = 0; s2 < NS; s2++) p1[s2] = 0.0;
-        T *sV = stage + (size_t)warp * 3 * K;
-        T *sX = sV + K;
-        for (int64_t t = r0 + warp; t < r1; t += kWarps) {
-            const T *Vr = dV + t * q, *Xr = Sxx + t * p;
-            for (int k = lane; k < nJ; k += 32) sV[k] = __ldcg(Vr + sJ[k]);
-            for (int k = lane; k < nI; k += 32) sX[k] = Xr[sI[k]];
-            __syncwarp();
-#pragma unroll
-            for (int s2 = 0; s2 < NS; s2++) {
-                const int l = s2 * 32 + lane;
-                if (l < nb) p1[s2] = fma((double)sX[spa[l]], (double)sV[spb[l]], p1[s2]);
+        // ---- phase A (two coordinates per CTA in one pass) ----
+        for (int l = blockIdx.x; l < nb; l += 2 * nblk) {
+            const int lb = l + (int)nblk;
+            const bool two = lb < nb;
+            const int64_t i0 = ti[s + l], j0 = tj[s + l];
+            const int64_t i1 = two ? ti[s + lb] : i0, j1 = two ? tj[s + lb] : j0;
+            // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
+            const T *x0 = Sxx + i0 * p, *y0 = dVt + j0 * p, *x1 = Sxx + i1 * p, *y1 = dVt + j1 * p;
+            T a0 = T(0), a1 = T(0);
+            for (int64_t t = threadIdx.x; t < tmax; t += blockDim.x) {
+                a0 = fma(x0[t], __ldcg(y0 + t), a0);
+                if (two) a1 = fma(x1[t], __ldcg(y1 + t), a1);
             }
-            __syncwarp();
-        }
-        for (int k = blockIdx.x; k < nI; k += nblk) {
-            const int64_t r = sI[k];
-            for (int k2 = threadIdx.x; k2 < nI; k2 += blockDim.x)
-                sub1[(size_t)k * K + k2] = Sxx[r * p + sI[k2]];
-        }
-        for (int k = blockIdx.x; k < nJ; k += nblk) {
-            const int64_t r = sJ[k];
-            for (int k2 = threadIdx.x; k2 < nJ; k2 += blockDim.x)
-                sub2[(size_t)k * K + k2] = Sig[r * q + sJ[k2]];
-        }
-#pragma unroll
-        for (int s2 = 0; s2 < NS; s2++) {
-            const int l = s2 * 32 + lane;
-            if (l < B) red[(size_t)warp * B + l] = p1[s2];
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < nb; e += blockDim.x) {
-            double acc = 0.0;
-            for (int w = 0; w < kWarps; w++) acc += red[(size_t)w * B + e];
-            scr.partial[(size_t)blockIdx.x * B + e] = acc;
-        }
-
-        // ---------------- phase B ----------------
-        if (last_cta(scr.ticket, nblk)) {
-            for (int e = threadIdx.x; e < nb; e += blockDim.x) {
-                double acc = 0.0;
-                for (unsigned c = 0; c < nblk; c++) acc += __ldcg(scr.partial + (size_t)c * B + e);
-                red[e] = acc;
-            }
-            __syncthreads();
-            for (int l = threadIdx.x; l < nb; l += blockDim.x) {
-                const int64_t i = ti[s + l], j = tj[s + l];
+            const double d0 = block_sum((double)a0);
+            const double d1 = block_sum((double)a1);
+            const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
+            if (which >= 0) {
+                const int lw = which ? lb : l;
+                const int64_t i = which ? i1 : i0, j = which ? j1 : j0;
                 const double xii = Xd[i];
-                const double a = 2.0 * Sd[j] * xii;
-                sbase[l] = 2.0 * W[i * q + j] + 2.0 * red[l];
-                sainv[l] = (xii != 0.0 && a > 0.0) ? 1.0 / a : 0.0;
-                sc[l] = __ldcg(Theta + i * q + j);
-                slam[l] = lam;
+                const double a = (xii != 0.0) ? 2.0 * Sd[j] * xii : 0.0;
+                step_constants<T>(2.0 * W[i * q + j] + 2.0 * (which ? d1 : d0), a,
+                                  __ldcg(Theta + i * q + j), lam, pre, B, lw);
             }
-            const size_t ncoef = (size_t)nb * (nb - 1) / 2;
-            for (size_t e = threadIdx.x; e < ncoef; e += blockDim.x) {
-                int l = (int)((1.0 + sqrt(1.0 + 8.0 * (double)e)) * 0.5);
-                while ((size_t)l * (l - 1) / 2 > e) l--;
-                while ((size_t)(l + 1) * l / 2 <= e) l++;
-                const int l1 = (int)(e - (size_t)l * (l - 1) / 2);
-                // 2 (S_xx)_{i a} Sigma_{b j}: coordinate l = (i, j), earlier l1 = (a, b)
-                scoef[e] = 2.0 * ldg_cg(sub1 + (size_t)spa[l] * K + spa[l1]) *
-                           ldg_cg(sub2 + (size_t)spb[l1] * K + spb[l]);
+        }
+        {
+            // 2 (S_xx)_{i a} Sigma_{b j}: coordinate l = (i, j), earlier l1 = (a, b)
+            const int ncoef = nb * (nb - 1) / 2;
+            for (int64_t e = gtid; e < ncoef; e += gthreads) {
+                int l, l1;
+                decode_pair((int)e, l, l1);
+                const int64_t i = sI[spa[l]], j = sJ[spb[l]];
+                const int64_t a = sI[spa[l1]], bq = sJ[spb[l1]];
+                gcoef[colbase(l1, B) + (l - l1 - 1)] = T(2) * Sxx[i * p + a] * Sig[bq * q + j];
             }
-            __syncthreads();
-            if (warp == 0)
-                forward_substitution<NS>(nb, sbase, sainv, sc, slam, scoef, scr.mu, scr.err);
-            __syncthreads();
+        }
+
+        // ---- phase B ----
+        if (last_cta(scr.ticket, nblk)) {
+            phase_b<T, NS>(nb, B, gcoef, pre, reinterpret_cast<T *>(work),
+                           reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
             for (int l = threadIdx.x; l < nb; l += blockDim.x) {
                 const int64_t i = ti[s + l], j = tj[s + l];
-                Theta[i * q + j] = sc[l] + scr.mu[l];
+                Theta[i * q + j] = __ldcg(Theta + i * q + j) + scr.mu[l];
             }
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
-        // ---------------- phase C: dV rows += mu Sigma rows ----------------
-        {
-            const int32_t *lptr = plan.lptr + b * (K + 1);
-            const int32_t *lent = plan.lent + b * K;
-            const int64_t nchunk = (q + 31) / 32;
-            const int64_t items = (int64_t)nI * nchunk;
-            for (int64_t it = (int64_t)blockIdx.x * kWarps + warp; it < items;
-                 it += (int64_t)nblk * kWarps) {
-                const int k = (int)(it / nchunk);
-                const int64_t t = (it % nchunk) * 32 + lane;
-                if (t >= q) continue;
-                const int64_t u = sI[k];
-                double acc = 0.0;
-                for (int e = lptr[k]; e < lptr[k + 1]; e++) {
-                    const int ent = lent[e];
-                    const int l = ent >> 16, pp = ent & 0xffff;
-                    acc = fma(__ldcg(scr.mu + l), (double)Sig[(int64_t)sJ[pp] * q + t], acc);
-                }
-                dV[u * q + t] = (T)((double)__ldcg(dV + u * q + t) + acc);
-            }
-        }
+        // ---- phase C: dVt[t][i] += sum mu Sigma[t][j] over this CTA's rows t ----
+        phase_c<T>(nb, nI, sI, sJ, slptr, slent, Sig, q, dVt, p, r0, r1,
+                   reinterpret_cast<T *>(work), scr.mu);
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
     }
 }
@@ -659,7 +756,7 @@ void plan_free(BatchPlan &plan) {
 
 cggm_status scratch_reserve(SweepScratch &scr, int B, int grid) {
     if (scr.partial) return CGGM_OK;
-    const int Bmax = 128, K = 2 * Bmax;
+    const int Bmax = 256, K = 2 * Bmax;
     (void)B;
     CGGM_CUDA_TRY(cudaMalloc(&scr.partial, sizeof(double) * (size_t)grid * Bmax * 3));
     CGGM_CUDA_TRY(cudaMalloc(&scr.mu, sizeof(double) * Bmax));
@@ -687,7 +784,7 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
                          double *D, T *U, int B, BatchPlan &plan, SweepScratch &scr,
                          cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
-    if (B < 32 || B > 128 || (B & (B - 1))) return CGGM_EINVAL;
+    if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
     const int64_t nbatch = (m + B - 1) / B;
     CGGM_TRY(plan_reserve(plan, B, nbatch, false));
     CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
@@ -709,6 +806,7 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
         case 32: fn = (const void *)lambda_sweep_kernel<T, 1>; break;
         case 64: fn = (const void *)lambda_sweep_kernel<T, 2>; break;
         case 128: fn = (const void *)lambda_sweep_kernel<T, 4>; break;
+        case 256: fn = (const void *)lambda_sweep_kernel<T, 8>; break;
         default: return CGGM_EINVAL;
     }
     CGGM_TRY(launch_coop<T>(fn, args, smem, st));
@@ -721,7 +819,7 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
                         const int32_t *ti, const int32_t *tj, double lam, T *dV, int B,
                         BatchPlan &plan, SweepScratch &scr, cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
-    if (B < 32 || B > 128 || (B & (B - 1))) return CGGM_EINVAL;
+    if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
     const int64_t nbatch = (m + B - 1) / B;
     CGGM_TRY(plan_reserve(plan, B, nbatch, true));
     CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
@@ -743,6 +841,7 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
         case 32: fn = (const void *)theta_sweep_kernel<T, 1>; break;
         case 64: fn = (const void *)theta_sweep_kernel<T, 2>; break;
         case 128: fn = (const void *)theta_sweep_kernel<T, 4>; break;
+        case 256: fn = (const void *)theta_sweep_kernel<T, 8>; break;
         default: return CGGM_EINVAL;
     }
     CGGM_TRY(launch_coop<T>(fn, args, smem, st));
