@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 CGGM solver (alternating Newton coordinate descent).
+
+One step is one Newton iteration of Algorithm 1 (every per-iteration step of the hot
+path: products R, P, Psi, gradients, stopping quantity, active sets, the Lambda
+coordinate pass, the Armijo search and the Theta coordinate pass) on the genotype chain
+workload p = q = 5000, n = 1000, lambda = 0.05, in the mixed-precision path.  W warm-up
+iterations start from Lambda = I, Theta = 0; the K timed iterations continue from there
+(inputs resident on the device, warm start passed in device memory).
+
+Printed (rank 0, one JSON line): Newton iterations per second over all ranks, the
+roofline of the dominant kernel (the coordinate pass with the larger share of the timed
+region), the oracle's CPU rate on a bounded sample, the same iterations end to end
+through the C ABI from host buffers, and the time to a 1e-6 relative objective gap of
+the mixed and the FP64 paths on the small chain workload (p=200, q=100, n=100), where a
+whole solve fits in seconds.  With --gpus N (torchrun) every rank solves an independent
+replica (another seed): the solve does not shard.
+
+--impl reference times the CPU oracle (the plain double-precision restatement of the
+method) on a bounded sample of the same workload and prints the same kind of line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "chain-geno-p5000-q5000-n1000"
+SMALL = "chain-gauss-p200-q100-n100"
+METRIC = "time to 1e-6 rel obj gap, mixed vs FP64 GPU; λ-path solves/s, p50/p99"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                    "sw_power_cap"), f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_rate(pr, budget_s=25.0):
+    """Oracle Newton iterations per second on a bounded sample of the workload: the dense
+    steps of one iteration (covariances amortised out, Sigma, Psi, gradients, active sets)
+    once, and the two coordinate passes over the leading coordinates of their active
+    sets until the time budget is spent; per-coordinate costs are scaled to the full
+    active sets."""
+    import numpy as np
+    import oracle
+    t0 = time.perf_counter()
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    q = Syy.shape[0]
+    p = Sxy.shape[0]
+    Lam, Th = np.eye(q), np.zeros((p, q))
+    t1 = time.perf_counter()
+    G_L, G_T, Sigma, Psi = oracle.gradients(Lam, Th, Sxx, Sxy, Syy)
+    li, lj, ti, tj = oracle.active_sets(G_L, G_T, Lam, Th, pr.lam_L, pr.lam_T)
+    f0 = oracle.objective(Lam, Th, Sxx, Sxy, Syy, pr.lam_L, pr.lam_T)
+    t_dense = time.perf_counter() - t1
+    # coordinate passes on growing prefixes until the budget is used
+    per = {}
+    for name, (ii, jj) in (("lambda", (li, lj)), ("theta", (ti, tj))):
+        k = 256
+        spent = 0.0
+        while True:
+            ts = time.perf_counter()
+            if name == "lambda":
+                oracle.lambda_sweep(Sigma, Psi, Syy, Lam, ii[:k], jj[:k], pr.lam_L)
+            else:
+                oracle.theta_sweep(Sxx, Sxy, Sigma, Th, ii[:k], jj[:k], pr.lam_T)
+            dt = time.perf_counter() - ts
+            spent += dt
+            per[name] = (dt, k)
+            # next prefix is 4x longer; stop before it would overrun this pass's share
+            if spent + 4 * dt > budget_s / 3 or k >= len(ii):
+                break
+            k = min(len(ii), k * 4)
+    t_iter = t_dense * 2 + per["lambda"][0] / per["lambda"][1] * len(li) + \
+        per["theta"][0] / per["theta"][1] * len(ti)
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    return {"value": 1.0 / t_iter, "unit": "Newton iterations/s", "cores": cores,
+            "kind": "oracle",
+            "sample": (f"{WORKLOAD} iteration 0: dense steps (Sigma, Psi, gradients, "
+                       f"objective, active sets) timed once and counted twice (the Armijo "
+                       f"objective), Lambda pass over the first {per['lambda'][1]} of "
+                       f"{len(li)} coordinates, Theta pass over the first {per['theta'][1]} "
+                       f"of {len(ti)}, scaled to the full active sets; coordinate passes "
+                       f"single-threaded C, dense steps numpy BLAS"),
+            "seconds_measured": round(time.perf_counter() - t0, 2)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import synth
+    pr = synth.workload(WORKLOAD)
+    rates = []
+    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    for k in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(pr, budget_s=budget)
+        if k >= args.warmup:
+            rates.append(r)
+    v = statistics.median([r["value"] for r in rates])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Newton iterations/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "p": 5000, "q": 5000, "n": 1000, "lambda": 0.05,
+                       "x": "genotype Binomial(2, MAF~U(0.05,0.5)) standardised",
+                       "network": "chain (1.0 / 0.4)", "theta_nnz_per_col": 10, "seed": 0},
+            "cpu_baseline": {"kind": "oracle", "cores": rates[0]["cores"],
+                             "sample": rates[0]["sample"], "value": v,
+                             "unit": "Newton iterations/s"},
+            "e2e": {"value": v, "unit": "Newton iterations/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def time_to_gap(ctx, cg, pr, torch):
+    """Seconds (device time of the solve) to reach (f - f*)/|f*| <= 1e-6, f* from the
+    double-precision path run until progress stops."""
+    ref = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
+                         opts=cg.make_opts(precision=cg.CGGM_FP64, max_iter=4000))
+    fstar = ctx.cggm_objective(pr.X, pr.Y, ref.Lambda, ref.Theta, pr.lam_L, pr.lam_T)
+    target = fstar + 1e-6 * abs(fstar)
+    out = {"workload": SMALL, "f_star": fstar}
+    for name, prec in (("mixed", cg.CGGM_MIXED), ("fp64", cg.CGGM_FP64)):
+        r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
+                           opts=cg.make_opts(precision=prec, max_iter=4000, target_f=target))
+        f = ctx.cggm_objective(pr.X, pr.Y, r.Lambda, r.Theta, pr.lam_L, pr.lam_T)
+        out[name] = {"seconds": r.info["seconds"], "iterations": r.info["iterations"],
+                     "reached": bool((f - fstar) / abs(fstar) <= 1e-6),
+                     "rel_gap": (f - fstar) / abs(fstar)}
+    return out
+
+
+def run_cuda(args):
+    import numpy as np
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    import synth
+
+    pr = synth.workload(WORKLOAD, seed=rank)  # independent replica per rank
+    n, p = pr.X.shape
+    q = pr.Y.shape[1]
+    Xd = torch.tensor(pr.X, device=dev, dtype=torch.float64)
+    Yd = torch.tensor(pr.Y, device=dev, dtype=torch.float64)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cg.Context(local, stream=stream.cuda_stream)
+    prec = cg.CGGM_MIXED if args.precision == "mixed" else cg.CGGM_FP64
+    L0 = torch.empty((q, q), device=dev, dtype=torch.float64)
+    T0 = torch.empty((p, q), device=dev, dtype=torch.float64)
+    L1 = torch.empty_like(L0)
+    T1 = torch.empty_like(T0)
+
+    # warm-up: W Newton iterations from Lambda = I, Theta = 0
+    ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
+                   opts=cg.make_opts(precision=prec, max_iter=args.warmup),
+                   Lambda_out=L0, Theta_out=T0)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        res = ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=L0,
+                             warm_Theta=T0,
+                             opts=cg.make_opts(precision=prec, max_iter=args.steps),
+                             Lambda_out=L1, Theta_out=T1)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    sec = ev0.elapsed_time(ev1) / 1e3
+    sec_max = max_over_ranks(sec, world)
+    info = res.info
+    iters = info["iterations"]
+    value = world * iters / sec_max
+    clocks = clk.summary()
+
+    # roofline of the dominant kernel: the coordinate pass with the larger time
+    esz = 4 if prec == cg.CGGM_MIXED else 8
+    lam_bytes = info["coords_lambda"] * 10 * q * esz
+    th_bytes = info["coords_theta"] * (2 * p + 3 * q) * esz
+    hbm, src = peaks()
+    if info["sec_sweep_lambda"] >= info["sec_sweep_theta"]:
+        kname, kbytes, ksec = "lambda_sweep_kernel", lam_bytes, info["sec_sweep_lambda"]
+        per_unit = f"10 q x {esz} B per Lambda coordinate"
+    else:
+        kname, kbytes, ksec = "theta_sweep_kernel", th_bytes, info["sec_sweep_theta"]
+        per_unit = f"(2 p + 3 q) x {esz} B per Theta coordinate"
+    achieved = kbytes / ksec / 1e9 if ksec > 0 else 0.0
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "peak_source": src, "algorithmic_bytes": per_unit,
+            "launch_seconds": ksec / max(1, iters), "share_of_step": ksec / sec}
+
+    line = {"metric": METRIC, "value": value, "unit": "Newton iterations/s",
+            "n_gpus": world, "steps": iters, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sec_max / max(1, iters), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 caches + f64 scalars" if prec == cg.CGGM_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "p": p, "q": q, "n": n, "lambda": pr.lam_L,
+                       "precision": args.precision, "parallelism": "replicas",
+                       "x": "genotype Binomial(2, MAF~U(0.05,0.5)) standardised",
+                       "network": "chain (1.0 / 0.4)", "theta_nnz_per_col": 10,
+                       "seed": 0, "l2": "working set (Sigma, Psi, U, S_xx, Delta V: "
+                       "~100 MB each) larger than L2; no flush"},
+            "roofline": roof, "clocks": clocks, "gpu_launches": info["launches"],
+            "per_iteration": {"active_lambda_last": info["m_lambda"],
+                              "active_theta_last": info["m_theta"],
+                              "sec_products": info["sec_products"] / max(1, iters),
+                              "sec_sweep_lambda": info["sec_sweep_lambda"] / max(1, iters),
+                              "sec_linesearch": info["sec_linesearch"] / max(1, iters),
+                              "sec_sweep_theta": info["sec_sweep_theta"] / max(1, iters),
+                              "coords_per_s": (info["coords_lambda"] + info["coords_theta"]) /
+                              max(1e-9, info["sec_sweep_lambda"] + info["sec_sweep_theta"])},
+            "reported_as": "Newton iterations/s on the 5000 x 5000 workload; time-to-gap on "
+                           "the 200 x 100 workload (time_to_gap)"}
+
+    # end to end through the C ABI from host buffers (copies inside the timed region)
+    if not args.no_e2e:
+        Lh, Th_ = L0.cpu().numpy(), T0.cpu().numpy()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        r2 = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=Lh,
+                            warm_Theta=Th_,
+                            opts=cg.make_opts(precision=prec, max_iter=args.steps))
+        torch.cuda.synchronize()
+        e2e_sec = max_over_ranks(time.perf_counter() - t0, world)
+        it2 = r2.info["iterations"]
+        line["e2e"] = {"value": world * it2 / e2e_sec, "unit": "Newton iterations/s",
+                       "h2d_bytes_per_step": int((pr.X.nbytes + pr.Y.nbytes + Lh.nbytes +
+                                                  Th_.nbytes) / max(1, it2)),
+                       "d2h_bytes_per_step": int((q * q + p * q) * 8 / max(1, it2))}
+
+    if rank == 0 and world == 1 and not args.no_ttg:
+        small = synth.workload(SMALL)
+        line["time_to_gap"] = time_to_gap(ctx, cg, small, torch)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate(pr)
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["cuda", "reference"], default="cuda")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ttg", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -85,6 +85,9 @@ typedef struct {
     double sec_sweep_lambda;
     double sec_linesearch;
     double sec_sweep_theta;
+    int64_t launches;       /* CUDA kernels this library launched during the call        */
+    int64_t coords_lambda;  /* coordinate steps taken by all Lambda passes of the call   */
+    int64_t coords_theta;   /* coordinate steps taken by all Theta passes of the call    */
 } cggm_info;
 
 typedef struct cggm_ctx cggm_ctx;

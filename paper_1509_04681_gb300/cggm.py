@@ -46,7 +46,9 @@ class cggm_info(ctypes.Structure):
                 ("ls_trials", ctypes.c_int), ("seconds", ctypes.c_double),
                 ("sec_products", ctypes.c_double), ("sec_factor", ctypes.c_double),
                 ("sec_active", ctypes.c_double), ("sec_sweep_lambda", ctypes.c_double),
-                ("sec_linesearch", ctypes.c_double), ("sec_sweep_theta", ctypes.c_double)]
+                ("sec_linesearch", ctypes.c_double), ("sec_sweep_theta", ctypes.c_double),
+                ("launches", ctypes.c_int64), ("coords_lambda", ctypes.c_int64),
+                ("coords_theta", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

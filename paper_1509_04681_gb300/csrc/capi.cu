@@ -233,6 +233,7 @@ struct Solver {
             gemm<float>(false, true, p, p, n, (float)inv, P<float>(c->Xt_f), n, P<float>(c->Xt_f), n,
                         0.0f, (float *)c->Sxx.p, p, st);
         }
+        note_launch();
         rowsq_kernel<double><<<(unsigned)p, 256, 0, st>>>(p, n, Xt, inv, P<double>(c->Xd));
         CGGM_CUDA_TRY(cudaGetLastError());
         return CGGM_OK;
@@ -284,6 +285,7 @@ struct Solver {
             convert_d2f(q * n, P<double>(c->Pt), Ptf, st);
             gemm<float>(false, true, q, q, n, (float)inv, Ptf, n, Ptf, n, 0.0f, (float *)c->Psi.p, q, st);
         }
+        note_launch();
         rowsq_kernel<double><<<(unsigned)q, 256, 0, st>>>(q, n, P<double>(c->Pt), inv, P<double>(c->Pd));
     }
 
@@ -335,6 +337,7 @@ struct Solver {
         if (warmL) {
             CGGM_TRY(load_double(c, warmL, qq, c->Lam));
         } else {
+            note_launch();
             set_identity<<<gcap(q * q), 256, 0, st>>>(q, P<double>(c->Lam));
         }
         if (warmT) {
@@ -343,9 +346,13 @@ struct Solver {
             CGGM_CUDA_TRY(cudaMemsetAsync(c->Th.p, 0, 8 * pq, st));
         }
         CGGM_CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), st));
+        note_launch();
         finite_check_kernel<<<gcap(n * p), 256, 0, st>>>(n * p, P<double>(c->Xt), P<int>(c->err));
+        note_launch();
         finite_check_kernel<<<gcap(n * q), 256, 0, st>>>(n * q, P<double>(c->Yt), P<int>(c->err));
+        note_launch();
         finite_check_kernel<<<gcap(q * q), 256, 0, st>>>(q * q, P<double>(c->Lam), P<int>(c->err));
+        note_launch();
         finite_check_kernel<<<gcap(p * q), 256, 0, st>>>(p * q, P<double>(c->Th), P<int>(c->err));
         {
             int h = 0;
@@ -362,6 +369,7 @@ struct Solver {
         int it = 0;
         double f = 0.0, subgrad = 0.0, nrm = 0.0;
         int ls_total = 0;
+        int64_t coords_l = 0, coords_t = 0;
         cudaEvent_t *ev = c->ev;
         double t_prod = 0, t_fac = 0, t_act = 0, t_swl = 0, t_ls = 0, t_swt = 0;
         cudaEventRecord(ev[7], st);
@@ -421,6 +429,8 @@ struct Solver {
                 break;
             }
             // ---- Lambda direction (Section 3.1) ----
+            coords_l += hc[0];
+            coords_t += hc[1];
             cudaEventRecord(ev[3], st);
             CGGM_CUDA_TRY(cudaMemsetAsync(c->D.p, 0, 8 * qq, st));
             CGGM_CUDA_TRY(cudaMemsetAsync(c->U.p, 0, sizeof(T) * qq, st));
@@ -511,6 +521,8 @@ struct Solver {
             info->sec_sweep_lambda = t_swl;
             info->sec_linesearch = t_ls;
             info->sec_sweep_theta = t_swt;
+            info->coords_lambda = coords_l;
+            info->coords_theta = coords_t;
         }
         *iters_out = it;
         *conv_out = converged;
@@ -628,6 +640,7 @@ cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, in
         !(o.sweep_batch == 256 && o.precision == CGGM_MIXED))
         return CGGM_EINVAL;
     if (info) memset(info, 0, sizeof(*info));
+    const int64_t launches0 = launch_counter();
     CGGM_TRY(set_device(c));
     CGGM_TRY(ensure(c->err, sizeof(int)));
     CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
@@ -649,6 +662,7 @@ cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, in
     if (Lambda_out) CGGM_TRY(store_double(c, Lambda_out, c->Lam.p, (size_t)q * q));
     if (Theta_out) CGGM_TRY(store_double(c, Theta_out, c->Th.p, (size_t)p * q));
     CGGM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    if (info) info->launches = launch_counter() - launches0;
     return conv ? CGGM_OK : CGGM_EMAXITER;
 }
 
@@ -838,6 +852,7 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
     CGGM_TRY(ensure(c->W, 8 * pq));
     const double inv = 1.0 / (double)n;
     const double *Xt = P<double>(c->Xt);
+    note_launch();
     rowsq_kernel<double><<<(unsigned)p, 256, 0, c->st>>>(p, n, Xt, inv, P<double>(c->Xd));
     diag_to_double<double>(q, P<double>(c->Sig), P<double>(c->Sd), c->st);
     // W = S_xy + S_xx Theta Sigma

@@ -144,19 +144,23 @@ void cholesky_inplace(int64_t n, double *A, int64_t lda, double *logd, int *err,
                       cudaStream_t st) {
     for (int64_t k0 = 0; k0 < n; k0 += NB) {
         const int nb = (int)((n - k0) < NB ? (n - k0) : NB);
+        note_launch();
         potrf_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, nb, logd, err);
         const int64_t k1 = k0 + nb;
         if (k1 < n) {
+            note_launch();
             trsm_panel_kernel<<<ceil_div(n - k1, 128), 128, 0, st>>>(n, A, lda, k0, nb, k1);
             // trailing lower update A[k1:, k1:] -= P P^T with P = A[k1:, k0:k1]
             gemm<double>(false, true, n - k1, n - k1, nb, -1.0, A + k1 * lda + k0, lda,
                          A + k1 * lda + k0, lda, 1.0, A + k1 * lda + k1, lda, st, /*tri=*/1);
         }
     }
+    note_launch();
     zero_upper_kernel<<<grid_cap(n * n), 256, 0, st>>>(n, A, lda);
 }
 
 void logdet_from_logd(int64_t n, const double *logd, double *out, cudaStream_t st) {
+    note_launch();
     sum_kernel<<<1, 1024, 0, st>>>(n, logd, 2.0, out);
 }
 
@@ -170,12 +174,14 @@ void trsm_lower_inplace(int64_t n, const double *L, int64_t ldl, double *B, int6
         if (i0 > 0)
             gemm<double>(false, false, rb, nc, i0, -1.0, L + i0 * ldl, ldl, B, ldb, 1.0,
                          B + i0 * ldb, ldb, st);
+        note_launch();
         trsv_block_kernel<<<ceil_div(nc, 128), 128, 0, st>>>(L, ldl, i0, rb, B, ldb, nc);
     }
 }
 
 void inverse_from_cholesky(int64_t n, const double *L, double *Sigma, double *work,
                            cudaStream_t st) {
+    note_launch();
     set_identity_kernel<<<grid_cap(n * n), 256, 0, st>>>(n, work, n);
     trsm_lower_inplace(n, L, n, work, n, n, true, st);  // work = L^-1 (lower)
     // Sigma = W^T W, lower triangle, then mirror

@@ -45,6 +45,11 @@ inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) /
 // Number of SMs of the current device (cached per process; one device per context).
 int sm_count();
 
+// Host-side count of kernel launches issued by this library (all contexts, process-wide);
+// reported per call in cggm_info.launches.
+int64_t &launch_counter();
+inline void note_launch() { __atomic_add_fetch(&launch_counter(), 1, __ATOMIC_RELAXED); }
+
 // ---------------------------------------------------------------------------------
 // Grid-wide barrier for persistent kernels launched cooperatively (all CTAs resident).
 // Sense/generation based, acquire/release ordered, with a wall-clock deadline: a CTA

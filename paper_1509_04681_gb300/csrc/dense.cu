@@ -3,6 +3,11 @@
 
 namespace cggm {
 
+int64_t &launch_counter() {
+    static int64_t n = 0;
+    return n;
+}
+
 int sm_count() {
     static int n = 0;
     if (n == 0) {
@@ -100,6 +105,7 @@ void gemm(bool transA, bool transB, int64_t M, int64_t N, int64_t K, T alpha, co
     if (M <= 0 || N <= 0) return;
     dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
     dim3 block(256);
+    note_launch();
     if (!transA && !transB)
         gemm_kernel<T, false, false><<<grid, block, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, tri, kdiag);
     else if (!transA && transB)
@@ -172,22 +178,32 @@ inline unsigned grid_for(int64_t len) {
 
 template <typename T>
 void axpby(int64_t len, T a, const T *x, T b, T *y, cudaStream_t st) {
-    if (len > 0) axpby_kernel<<<grid_for(len), 256, 0, st>>>(len, a, x, b, y);
+    if (len > 0) {
+        note_launch();
+        axpby_kernel<<<grid_for(len), 256, 0, st>>>(len, a, x, b, y);
+    }
 }
 template void axpby<double>(int64_t, double, const double *, double, double *, cudaStream_t);
 template void axpby<float>(int64_t, float, const float *, float, float *, cudaStream_t);
 
 void convert_d2f(int64_t len, const double *x, float *y, cudaStream_t st) {
-    if (len > 0) d2f_kernel<<<grid_for(len), 256, 0, st>>>(len, x, y);
+    if (len > 0) {
+        note_launch();
+        d2f_kernel<<<grid_for(len), 256, 0, st>>>(len, x, y);
+    }
 }
 void convert_f2d(int64_t len, const float *x, double *y, cudaStream_t st) {
-    if (len > 0) f2d_kernel<<<grid_for(len), 256, 0, st>>>(len, x, y);
+    if (len > 0) {
+        note_launch();
+        f2d_kernel<<<grid_for(len), 256, 0, st>>>(len, x, y);
+    }
 }
 
 template <typename Tin, typename Tout>
 void transpose(int64_t rows, int64_t cols, const Tin *in, Tout *out, cudaStream_t st) {
     if (rows <= 0 || cols <= 0) return;
     dim3 grid(ceil_div(cols, 32), ceil_div(rows, 32)), block(32, 8);
+    note_launch();
     transpose_kernel<Tin, Tout><<<grid, block, 0, st>>>(rows, cols, in, out);
 }
 template void transpose<double, double>(int64_t, int64_t, const double *, double *, cudaStream_t);
@@ -197,14 +213,20 @@ template void transpose<float, double>(int64_t, int64_t, const float *, double *
 
 template <typename T>
 void symmetrize_lower(int64_t n, T *A, cudaStream_t st) {
-    if (n > 0) symmetrize_kernel<<<grid_for(n * n), 256, 0, st>>>(n, A);
+    if (n > 0) {
+        note_launch();
+        symmetrize_kernel<<<grid_for(n * n), 256, 0, st>>>(n, A);
+    }
 }
 template void symmetrize_lower<double>(int64_t, double *, cudaStream_t);
 template void symmetrize_lower<float>(int64_t, float *, cudaStream_t);
 
 template <typename T>
 void diag_to_double(int64_t n, const T *A, double *d, cudaStream_t st) {
-    if (n > 0) diag_kernel<<<grid_for(n), 256, 0, st>>>(n, A, d);
+    if (n > 0) {
+        note_launch();
+        diag_kernel<<<grid_for(n), 256, 0, st>>>(n, A, d);
+    }
 }
 template void diag_to_double<double>(int64_t, const double *, double *, cudaStream_t);
 template void diag_to_double<float>(int64_t, const float *, double *, cudaStream_t);
@@ -246,7 +268,9 @@ __global__ void finish_sum_kernel(int nparts, const double *partial, double *out
 
 template <typename T>
 void dot_d(int64_t len, const T *x, const T *y, double *partial, double *out, cudaStream_t st) {
+    note_launch();
     dot_partial_kernel<<<RED_BLOCKS, 256, 0, st>>>(len, x, y, partial);
+    note_launch();
     finish_sum_kernel<<<1, 512, 0, st>>>(RED_BLOCKS, partial, out);
 }
 template void dot_d<double>(int64_t, const double *, const double *, double *, double *, cudaStream_t);
@@ -254,7 +278,9 @@ template void dot_d<float>(int64_t, const float *, const float *, double *, doub
 
 template <typename T>
 void l1_d(int64_t len, const T *x, int64_t nd, double *partial, double *out, cudaStream_t st) {
+    note_launch();
     l1_partial_kernel<<<RED_BLOCKS, 256, 0, st>>>(len, x, nd, partial);
+    note_launch();
     finish_sum_kernel<<<1, 512, 0, st>>>(RED_BLOCKS, partial, out);
 }
 template void l1_d<double>(int64_t, const double *, int64_t, double *, double *, cudaStream_t);

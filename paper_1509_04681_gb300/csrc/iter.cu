@@ -144,6 +144,7 @@ inline unsigned grid_cap(int64_t len) {
 template <typename TP>
 void grad_lambda(int64_t q, const double *Syy, const double *Sigma, const TP *Psi, double *G,
                  cudaStream_t st) {
+    note_launch();
     grad_lambda_kernel<<<grid_cap(q * q), 256, 0, st>>>(q * q, Syy, Sigma, Psi, G);
 }
 template void grad_lambda<double>(int64_t, const double *, const double *, const double *,
@@ -153,7 +154,9 @@ template void grad_lambda<float>(int64_t, const double *, const double *, const 
 
 void subgrad_sums(int64_t r, int64_t c, const double *G, const double *P, double lam,
                   double diag_lam, double *partial, double *out, cudaStream_t st) {
+    note_launch();
     subgrad_partial_kernel<<<RED_BLOCKS, 256, 0, st>>>(r, c, G, P, lam, diag_lam, partial);
+    note_launch();
     subgrad_finish_kernel<<<1, 512, 0, st>>>(RED_BLOCKS, partial, out);
 }
 
@@ -161,8 +164,11 @@ void active_compact(int64_t r, int64_t c, const double *G, const double *P, doub
                     double thr_diag, bool upper, int64_t *rowcnt, int32_t *ii, int32_t *jj,
                     int64_t *count, cudaStream_t st) {
     if (r <= 0) return;
+    note_launch();
     active_count_kernel<<<(unsigned)r, 256, 0, st>>>(c, G, P, thr, thr_diag, upper, rowcnt);
+    note_launch();
     scan_rows_kernel<<<1, 1024, 0, st>>>(r, rowcnt, count);
+    note_launch();
     active_write_kernel<<<(unsigned)r, 256, 0, st>>>(c, G, P, thr, thr_diag, upper, rowcnt, ii,
                                                      jj);
 }

@@ -708,6 +708,7 @@ cggm_status launch_coop(const void *fn, void **args, size_t smem, cudaStream_t s
     CGGM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     const int grid = sweep_grid();
+    note_launch();
     CGGM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, st));
     return CGGM_OK;
 }
@@ -790,6 +791,7 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
     CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
     plan.nbatch = nbatch;
     const int K = 2 * B;
+    note_launch();
     lambda_plan_kernel<<<(unsigned)nbatch, 256, (size_t)(3 * K + 1) * sizeof(int), st>>>(
         m, ai, aj, B, plan);
     CGGM_CUDA_TRY(cudaGetLastError());
@@ -825,6 +827,7 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
     CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
     plan.nbatch = nbatch;
     const int K = 2 * B;
+    note_launch();
     theta_plan_kernel<<<(unsigned)nbatch, 256, (size_t)(4 * K + 1) * sizeof(int), st>>>(
         m, ti, tj, B, plan);
     CGGM_CUDA_TRY(cudaGetLastError());
