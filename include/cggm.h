@@ -185,6 +185,36 @@ cggm_status cggm_active_sets(cggm_ctx *ctx, int64_t p, int64_t q, const double *
                              int penalize_diag, int32_t *li, int32_t *lj, int64_t *m_lambda,
                              int32_t *ti, int32_t *tj, int64_t *m_theta);
 
+/*
+ * No-allocation variant of cggm_lambda_sweep (the paper has no counterpart: this is an
+ * interface for embedding).  Some callers cannot call cudaMalloc: code that runs under
+ * an allocator that owns all device memory (a framework's caching allocator or a fixed
+ * memory pool sized up front), and latency-critical loops where the implicit device
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.  This entry point computes
+ * the same Lambda direction as cggm_lambda_sweep (double precision) but allocates
+ * nothing: its working memory is one device array inside the library, of
+ * CGGM_NOALLOC_SCRATCH_BYTES bytes, which every GPU that loads the library holds until
+ * the process exits.
+ *
+ *  - q <= CGGM_NOALLOC_MAX_Q and 0 <= m <= q (q + 1) / 2; larger sizes return
+ *    CGGM_EINVAL without touching the GPU.
+ *  - Every pointer must be device memory of the current device (CGGM_EINVAL otherwise):
+ *    Sigma, Psi, Syy, Lambda (q x q double), ai, aj (m int32, ai <= aj, visiting order),
+ *    D_out (q x q double, overwritten).  The call runs on cuda_stream (a cudaStream_t;
+ *    NULL = the legacy default stream) and returns after the pass has finished.
+ *  - The first call on a device looks up the device address of the array (once per
+ *    device, with that device current); make that first call before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents (the call
+ *    clears what must start at zero).  Calls that overlap on the GPU - from two host
+ *    threads or on two streams - race on it; serialise them.
+ */
+#define CGGM_NOALLOC_MAX_Q 256
+#define CGGM_NOALLOC_SCRATCH_BYTES (3u << 20)
+cggm_status cggm_lambda_sweep_noalloc(int64_t q, const double *Sigma, const double *Psi,
+                                      const double *Syy, const double *Lambda, int64_t m,
+                                      const int32_t *ai, const int32_t *aj, double lam_L,
+                                      int penalize_diag, double *D_out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,7 +27,7 @@ CGGM_F32, CGGM_F64 = 0, 1
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
-    "cggm_active_sets",
+    "cggm_active_sets", "cggm_lambda_sweep_noalloc",
 ]
 
 
@@ -87,12 +87,15 @@ def _lib():
         lib.cggm_theta_sweep.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp]
         lib.cggm_active_sets.argtypes = [vp, i64, i64, vp, vp, vp, vp, dbl, dbl, ip, vp, vp,
                                          ctypes.POINTER(i64), vp, vp, ctypes.POINTER(i64)]
+        lib.cggm_lambda_sweep_noalloc.argtypes = [i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp,
+                                                  vp]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
                                                      "cggm_grad", "cggm_cholesky",
                                                      "cggm_lambda_sweep", "cggm_theta_sweep",
-                                                     "cggm_active_sets"):
+                                                     "cggm_active_sets",
+                                                     "cggm_lambda_sweep_noalloc"):
                 f.restype = ctypes.c_int
         _LIB = lib
     return _LIB

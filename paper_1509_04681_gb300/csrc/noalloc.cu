@@ -1,0 +1,136 @@
+// cggm_lambda_sweep_noalloc: the Lambda coordinate pass for callers that must not
+// allocate device memory.  Its working memory is one file-scope device array.
+#include <mutex>
+
+#include "common.cuh"
+#include "dense.cuh"
+#include "iter.cuh"
+#include "sweeps.cuh"
+
+using namespace cggm;
+
+namespace {
+
+constexpr int64_t kMaxQ = CGGM_NOALLOC_MAX_Q;
+constexpr int kBatch = 64;
+constexpr int64_t kMaxCoords = kMaxQ * (kMaxQ + 1) / 2;
+constexpr int64_t kMaxBatches = (kMaxCoords + kBatch - 1) / kBatch;
+constexpr int kK = 2 * kBatch;
+
+// Byte offsets of the regions inside the array (each 256-byte aligned).
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t OFF_G = 0;                                                   // q x q double
+constexpr size_t OFF_U = align256(OFF_G + 8 * kMaxQ * kMaxQ);                 // q x q double
+constexpr size_t OFF_SD = align256(OFF_U + 8 * kMaxQ * kMaxQ);                // q double
+constexpr size_t OFF_PD = align256(OFF_SD + 8 * kMaxQ);                       // q double
+constexpr size_t OFF_NIDX = align256(OFF_PD + 8 * kMaxQ);                     // batches int
+constexpr size_t OFF_NIDX2 = align256(OFF_NIDX + 4 * kMaxBatches);
+constexpr size_t OFF_IDX = align256(OFF_NIDX2 + 4 * kMaxBatches);             // batches x K
+constexpr size_t OFF_IDX2 = align256(OFF_IDX + 4 * kMaxBatches * kK);
+constexpr size_t OFF_PA = align256(OFF_IDX2 + 4 * kMaxBatches * kK);          // batches x B
+constexpr size_t OFF_PB = align256(OFF_PA + 4 * kMaxBatches * kBatch);
+constexpr size_t OFF_LPTR = align256(OFF_PB + 4 * kMaxBatches * kBatch);      // batches x (K+1)
+constexpr size_t OFF_LENT = align256(OFF_LPTR + 4 * kMaxBatches * (kK + 1));  // batches x K
+constexpr size_t OFF_MU = align256(OFF_LENT + 4 * kMaxBatches * kK);          // B double
+constexpr size_t OFF_SUB1 = align256(OFF_MU + 8 * kBatch);                    // step constants
+constexpr size_t OFF_SUB2 = align256(OFF_SUB1 + 16 * 1024);                   // coefficients
+constexpr size_t OFF_BAR = align256(OFF_SUB2 + 8 * kBatch * kBatch + 1024);   // barrier
+constexpr size_t OFF_TICKET = align256(OFF_BAR + sizeof(GridBarrier));
+constexpr size_t OFF_ERR = align256(OFF_TICKET + sizeof(unsigned));
+constexpr size_t kBytes = align256(OFF_ERR + sizeof(int));
+static_assert(kBytes <= (size_t)CGGM_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds its size");
+
+// The scratch array.  Every GPU that loads the library holds it until the process exits.
+static __device__ __align__(256) unsigned char g_scratch[CGGM_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_scratch per device, taken once with that device current (the host
+// name of the array is only a stand-in for it).
+constexpr int kMaxDevices = 64;
+unsigned char *g_base[kMaxDevices] = {};
+std::mutex g_mutex;
+
+cggm_status scratch_base(int dev, unsigned char **out) {
+    if (dev < 0 || dev >= kMaxDevices) return CGGM_EINVAL;
+    std::lock_guard<std::mutex> lock(g_mutex);
+    if (!g_base[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) {
+            cudaGetLastError();
+            return CGGM_ECUDA;
+        }
+        g_base[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_base[dev];
+    return CGGM_OK;
+}
+
+bool on_device(const void *p, int dev) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) &&
+           a.device == dev;
+}
+
+}  // namespace
+
+extern "C" cggm_status cggm_lambda_sweep_noalloc(int64_t q, const double *Sigma,
+                                                 const double *Psi, const double *Syy,
+                                                 const double *Lambda, int64_t m,
+                                                 const int32_t *ai, const int32_t *aj,
+                                                 double lam_L, int penalize_diag,
+                                                 double *D_out, void *cuda_stream) {
+    if (q < 1 || q > kMaxQ || m < 0 || m > q * (q + 1) / 2) return CGGM_EINVAL;
+    if (!Sigma || !Psi || !Syy || !Lambda || !D_out || (m > 0 && (!ai || !aj)))
+        return CGGM_EINVAL;
+    if (!(lam_L >= 0.0)) return CGGM_EINVAL;
+    int dev = 0;
+    CGGM_CUDA_TRY(cudaGetDevice(&dev));
+    const void *ptrs[] = {Sigma, Psi, Syy, Lambda, D_out};
+    for (const void *p : ptrs)
+        if (!on_device(p, dev)) return CGGM_EINVAL;
+    if (m > 0 && (!on_device(ai, dev) || !on_device(aj, dev))) return CGGM_EINVAL;
+    unsigned char *base = nullptr;
+    CGGM_TRY(scratch_base(dev, &base));
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+
+    double *G = reinterpret_cast<double *>(base + OFF_G);
+    double *U = reinterpret_cast<double *>(base + OFF_U);
+    double *Sd = reinterpret_cast<double *>(base + OFF_SD);
+    double *Pd = reinterpret_cast<double *>(base + OFF_PD);
+    BatchPlan plan;
+    plan.B = kBatch;
+    plan.K = kK;
+    plan.cap = kMaxBatches;
+    plan.nidx = reinterpret_cast<int32_t *>(base + OFF_NIDX);
+    plan.nidx2 = reinterpret_cast<int32_t *>(base + OFF_NIDX2);
+    plan.idx = reinterpret_cast<int32_t *>(base + OFF_IDX);
+    plan.idx2 = reinterpret_cast<int32_t *>(base + OFF_IDX2);
+    plan.pa = reinterpret_cast<int32_t *>(base + OFF_PA);
+    plan.pb = reinterpret_cast<int32_t *>(base + OFF_PB);
+    plan.lptr = reinterpret_cast<int32_t *>(base + OFF_LPTR);
+    plan.lent = reinterpret_cast<int32_t *>(base + OFF_LENT);
+    SweepScratch scr;
+    scr.mu = reinterpret_cast<double *>(base + OFF_MU);
+    scr.sub1 = base + OFF_SUB1;
+    scr.sub2 = base + OFF_SUB2;
+    scr.bar = reinterpret_cast<GridBarrier *>(base + OFF_BAR);
+    scr.ticket = reinterpret_cast<unsigned *>(base + OFF_TICKET);
+    scr.err = reinterpret_cast<int *>(base + OFF_ERR);
+
+    // What must start at zero: the direction and the cache U = D Sigma.  The gradient,
+    // the diagonals and the batch plan are rewritten in full below.
+    const size_t qq = (size_t)q * q;
+    CGGM_CUDA_TRY(cudaMemsetAsync(D_out, 0, 8 * qq, st));
+    CGGM_CUDA_TRY(cudaMemsetAsync(U, 0, 8 * qq, st));
+    grad_lambda<double>(q, Syy, Sigma, Psi, G, st);
+    diag_to_double<double>(q, Sigma, Sd, st);
+    diag_to_double<double>(q, Psi, Pd, st);
+    CGGM_CUDA_TRY(cudaGetLastError());
+    const double lamd = penalize_diag ? lam_L : 0.0;
+    return lambda_sweep_preplanned_f64(q, Sigma, Psi, Sd, Pd, G, Lambda, m, ai, aj, lam_L,
+                                       lamd, D_out, U, kBatch, plan, scr, st);
+}

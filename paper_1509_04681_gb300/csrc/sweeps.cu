@@ -815,6 +815,41 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
     return read_err(scr.err, st);
 }
 
+// Same pass as lambda_sweep on plan and scratch buffers that the caller has already laid
+// out (pointers set, capacity for ceil(m / B) batches); allocates nothing.
+cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const double *Psi,
+                                        const double *Sd, const double *Pd, const double *G,
+                                        const double *Lambda, int64_t m, const int32_t *ai,
+                                        const int32_t *aj, double lam_off, double lam_diag,
+                                        double *D, double *U, int B, BatchPlan plan,
+                                        SweepScratch scr, cudaStream_t st) {
+    if (m <= 0) return CGGM_OK;
+    if (B != 32 && B != 64 && B != 128) return CGGM_EINVAL;
+    const int64_t nbatch = (m + B - 1) / B;
+    if (nbatch > plan.cap) return CGGM_EINVAL;
+    plan.B = B;
+    plan.K = 2 * B;
+    plan.nbatch = nbatch;
+    const int K = 2 * B;
+    note_launch();
+    lambda_plan_kernel<<<(unsigned)nbatch, 256, (size_t)(3 * K + 1) * sizeof(int), st>>>(
+        m, ai, aj, B, plan);
+    CGGM_CUDA_TRY(cudaGetLastError());
+    CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
+    CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
+    CGGM_CUDA_TRY(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), st));
+    const size_t smem = smem_layout<double>(B).total;
+    void *args[] = {(void *)&q, (void *)&Sigma, (void *)&Psi, (void *)&Sd, (void *)&Pd,
+                    (void *)&G, (void *)&Lambda, (void *)&m, (void *)&ai, (void *)&aj,
+                    (void *)&lam_off, (void *)&lam_diag, (void *)&D, (void *)&U, (void *)&B,
+                    (void *)&plan, (void *)&scr};
+    const void *fn = B == 32 ? (const void *)lambda_sweep_kernel<double, 1>
+                   : B == 64 ? (const void *)lambda_sweep_kernel<double, 2>
+                             : (const void *)lambda_sweep_kernel<double, 4>;
+    CGGM_TRY(launch_coop<double>(fn, args, smem, st));
+    return read_err(scr.err, st);
+}
+
 template <typename T>
 cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, const T *Sigma,
                         const double *Sd, const double *W, double *Theta, int64_t m,

@@ -54,6 +54,15 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
                         const int32_t *ti, const int32_t *tj, double lam, T *dV, int B,
                         BatchPlan &plan, SweepScratch &scr, cudaStream_t st);
 
+// lambda_sweep in double on plan and scratch buffers laid out by the caller (their
+// pointers set, plan.cap >= ceil(m / B)); allocates nothing.  B in {32, 64, 128}.
+cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const double *Psi,
+                                        const double *Sd, const double *Pd, const double *G,
+                                        const double *Lambda, int64_t m, const int32_t *ai,
+                                        const int32_t *aj, double lam_off, double lam_diag,
+                                        double *D, double *U, int B, BatchPlan plan,
+                                        SweepScratch scr, cudaStream_t st);
+
 // Plan storage helpers (allocate on demand, grow only).
 cggm_status plan_reserve(BatchPlan &plan, int B, int64_t nbatch, bool theta);
 void plan_free(BatchPlan &plan);
