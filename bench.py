@@ -233,6 +233,34 @@ def time_to_gap(ctx, cg, pr, torch):
     return out
 
 
+def run_profile_sweep(args):
+    """A bounded Lambda coordinate pass at q = 5000 (Sigma, Psi and the cache, 100 MB each,
+    exceed L2): rows 0..39 of a dense active set, ~2e5 coordinates, run twice through
+    cggm_lambda_sweep.  Used for ncu captures of the sweep kernel."""
+    import numpy as np
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    q = 5000
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((q, q + 8)) / np.sqrt(q)
+    Sig = A @ A.T + np.eye(q)
+    Bm = rng.standard_normal((q, 64)) / 8
+    Psi = Bm @ Bm.T
+    Syy = Sig + 0.1 * np.eye(q)
+    Lam = np.linalg.inv(Sig)
+    iu, ju = np.triu_indices(q)
+    keep = iu < 40
+    li, lj = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+    prec = cg.CGGM_MIXED if args.precision == "mixed" else cg.CGGM_FP64
+    with cg.Context(0) as ctx:
+        for _ in range(2):
+            D = ctx.cggm_lambda_sweep(Sig, Psi, Syy, Lam, li, lj, 0.01, precision=prec)
+    print(json.dumps({"profile_sweep": {"q": q, "coordinates": int(len(li)),
+                                        "precision": args.precision,
+                                        "d_abs_sum": float(np.abs(D).sum())}}))
+
+
 def run_cuda(args):
     import numpy as np
     import torch
@@ -364,8 +392,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile-sweep", action="store_true",
+                    help="run only a bounded Lambda pass at q=5000 (for ncu captures)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_sweep:
+        run_profile_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_cuda(args)
