@@ -31,150 +31,6 @@ constexpr int kThreads = 256;
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
 // ---------------------------------------------------------------------------------
-// batch plans
-// ---------------------------------------------------------------------------------
-// Bitonic sort of K (power of two) ints in shared memory, ascending.
-__device__ void bitonic_sort(int *key, int K) {
-    for (int size = 2; size <= K; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            __syncthreads();
-            for (int t = threadIdx.x; t < K / 2; t += blockDim.x) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = ((lo & size) == 0);
-                const int a = key[lo], b = key[hi];
-                if ((a > b) == up) { key[lo] = b; key[hi] = a; }
-            }
-        }
-    }
-    __syncthreads();
-}
-
-// Sort, deduplicate; returns count, writes the distinct values to out[0..count).
-__device__ int sort_unique(int *key, int K, int32_t *out, int *s_cnt) {
-    bitonic_sort(key, K);
-    if (threadIdx.x == 0) {
-        int c = 0;
-        for (int k = 0; k < K; k++) {
-            const int v = key[k];
-            if (v == INT_MAX) break;
-            if (c == 0 || out[c - 1] != v) out[c++] = v;
-        }
-        *s_cnt = c;
-    }
-    __syncthreads();
-    return *s_cnt;
-}
-
-__device__ int lower_bound(const int32_t *a, int n, int v) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < v) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Lambda plan: one index set (both coordinates of (a, b) index q); lists per distinct
-// index u: every coordinate with a == u (partner b) and with b == u != a (partner a).
-__global__ void lambda_plan_kernel(int64_t m, const int32_t *ai, const int32_t *aj, int B,
-                                   BatchPlan plan) {
-    extern __shared__ int smem_i[];
-    const int K = 2 * B;
-    int *key = smem_i;              // K
-    int32_t *sidx = key + K;        // K
-    int *cnt = sidx + K;            // K + 1
-    __shared__ int s_cnt;
-    const int64_t b = blockIdx.x;
-    const int64_t s = b * B;
-    const int nb = (int)((m - s) < B ? (m - s) : B);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        const int l = k >> 1;
-        key[k] = (l < nb) ? ((k & 1) ? aj[s + l] : ai[s + l]) : INT_MAX;
-    }
-    const int nidx = sort_unique(key, K, sidx, &s_cnt);
-    int32_t *idx = plan.idx + b * K;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) idx[k] = (k < nidx) ? sidx[k] : 0;
-    for (int l = threadIdx.x; l < B; l += blockDim.x) {
-        int pa = 0, pb = 0;
-        if (l < nb) {
-            pa = lower_bound(sidx, nidx, ai[s + l]);
-            pb = lower_bound(sidx, nidx, aj[s + l]);
-        }
-        plan.pa[b * B + l] = pa;
-        plan.pb[b * B + l] = pb;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        plan.nidx[b] = nidx;
-        for (int k = 0; k <= K; k++) cnt[k] = 0;
-        for (int l = 0; l < nb; l++) {
-            const int pa = plan.pa[b * B + l], pb = plan.pb[b * B + l];
-            cnt[pa + 1]++;
-            if (pa != pb) cnt[pb + 1]++;
-        }
-        for (int k = 0; k < K; k++) cnt[k + 1] += cnt[k];
-        int32_t *lptr = plan.lptr + b * (K + 1);
-        for (int k = 0; k <= K; k++) lptr[k] = cnt[k];
-        int32_t *lent = plan.lent + b * K;
-        for (int l = 0; l < nb; l++) {
-            const int pa = plan.pa[b * B + l], pb = plan.pb[b * B + l];
-            lent[cnt[pa]++] = (l << 16) | pb;
-            if (pa != pb) lent[cnt[pb]++] = (l << 16) | pa;
-        }
-    }
-}
-
-// Theta plan: distinct i (idx) and distinct j (idx2); lists per distinct i: every
-// coordinate of that row (partner = position of its j in idx2).
-__global__ void theta_plan_kernel(int64_t m, const int32_t *ti, const int32_t *tj, int B,
-                                  BatchPlan plan) {
-    extern __shared__ int smem_i[];
-    const int K = 2 * B;
-    int *key = smem_i;            // K
-    int32_t *sI = key + K;        // K
-    int32_t *sJ = sI + K;         // K
-    int *cnt = sJ + K;            // K + 1
-    __shared__ int s_cnt;
-    const int64_t b = blockIdx.x;
-    const int64_t s = b * B;
-    const int nb = (int)((m - s) < B ? (m - s) : B);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) key[k] = (k < nb) ? ti[s + k] : INT_MAX;
-    const int nI = sort_unique(key, K, sI, &s_cnt);
-    __syncthreads();
-    for (int k = threadIdx.x; k < K; k += blockDim.x) key[k] = (k < nb) ? tj[s + k] : INT_MAX;
-    const int nJ = sort_unique(key, K, sJ, &s_cnt);
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        plan.idx[b * K + k] = (k < nI) ? sI[k] : 0;
-        plan.idx2[b * K + k] = (k < nJ) ? sJ[k] : 0;
-    }
-    for (int l = threadIdx.x; l < B; l += blockDim.x) {
-        int pa = 0, pb = 0;
-        if (l < nb) {
-            pa = lower_bound(sI, nI, ti[s + l]);
-            pb = lower_bound(sJ, nJ, tj[s + l]);
-        }
-        plan.pa[b * B + l] = pa;
-        plan.pb[b * B + l] = pb;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        plan.nidx[b] = nI;
-        plan.nidx2[b] = nJ;
-        for (int k = 0; k <= K; k++) cnt[k] = 0;
-        for (int l = 0; l < nb; l++) cnt[plan.pa[b * B + l] + 1]++;
-        for (int k = 0; k < K; k++) cnt[k + 1] += cnt[k];
-        int32_t *lptr = plan.lptr + b * (K + 1);
-        for (int k = 0; k <= K; k++) lptr[k] = cnt[k];
-        int32_t *lent = plan.lent + b * K;
-        for (int l = 0; l < nb; l++) {
-            const int pa = plan.pa[b * B + l], pb = plan.pb[b * B + l];
-            lent[cnt[pa]++] = (l << 16) | pb;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------
 // shared pieces of the sweep kernels
 // ---------------------------------------------------------------------------------
 // Per-coordinate step constants, formed in double in phase A and stored in the cache
@@ -226,25 +82,23 @@ __host__ __device__ __forceinline__ int colbase(int l, int B) { return l * (2 * 
 // shared-memory slots for the coefficients (16-byte multiple with copy slack)
 __host__ __device__ __forceinline__ int coef_slots(int B) { return ((B * (B - 1) / 2 + 8) + 3) & ~3; }
 
-constexpr int kRowsC = 16;  // rows of the band staged per round in phase C
 
 struct SmemLayout {
-    size_t meta;  // idx[K], idx2[K], pa[B], pb[B], lptr[K+1], lent[K] (ints)
-    size_t work;  // union: phase B coef[B(B-1)/2] (T);
-                  //        phase C mu[B], Sigma rows [kRowsC][K], cache rows [kRowsC][K] (T)
+    size_t meta;  // sa[B], sb[B] (batch coordinates), sseg[B + 1] (segment starts), nseg (ints)
+    size_t work;  // union: phase B coef[coef_slots(B)] + step constants [PRE_N][B] (T);
+                  //        phase C mu[B] (T)
     size_t total;
 };
 
 template <typename T>
 __host__ __device__ inline SmemLayout smem_layout(int B) {
-    const int K = 2 * B;
     SmemLayout s;
     s.meta = 0;
-    size_t off = (size_t)(2 * K + 2 * B + (K + 1) + K) * sizeof(int32_t);
+    size_t off = (size_t)(2 * B + (B + 1) + 1) * sizeof(int32_t);
     off = (off + 15) & ~size_t(15);
     s.work = off;
     const size_t phb = ((size_t)coef_slots(B) + PRE_N * B + 8) * sizeof(T);
-    const size_t phc = (size_t)(B + 4) * sizeof(T) + (size_t)kRowsC * (K + 4) * sizeof(T) * 2;
+    const size_t phc = (size_t)(B + 4) * sizeof(T);
     s.total = off + (phb > phc ? phb : phc);
     return s;
 }
@@ -325,48 +179,6 @@ __device__ __forceinline__ bool last_cta(unsigned *ticket, unsigned nblocks) {
     return s_last != 0;
 }
 
-// Three dot products of length len over contiguous rows by the whole CTA:
-//   r0 = x0 . y0, r1 = x1 . y0, r2 = x2 . y1   (y rows read through L2); valid in thread 0
-template <typename T>
-__device__ void cta_dot3(int64_t len, const T *x0, const T *x1, const T *x2, const T *y0,
-                         const T *y1, double *r) {
-    T a0 = T(0), a1 = T(0), a2 = T(0);
-    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) {
-        const T u0 = __ldcg(y0 + t), u1 = __ldcg(y1 + t);
-        a0 = fma(x0[t], u0, a0);
-        a1 = fma(x1[t], u0, a1);
-        a2 = fma(x2[t], u1, a2);
-    }
-    r[0] = block_sum((double)a0);
-    r[1] = block_sum((double)a1);
-    r[2] = block_sum((double)a2);
-}
-
-template <typename T>
-__device__ double cta_dot1(int64_t len, const T *x0, const T *y0) {
-    T a0 = T(0);
-    for (int64_t t = threadIdx.x; t < len; t += blockDim.x) a0 = fma(x0[t], __ldcg(y0 + t), a0);
-    return block_sum((double)a0);
-}
-
-// Load the batch metadata of batch b into shared memory.
-__device__ void load_meta(const BatchPlan &plan, int64_t b, int B, bool theta, int32_t *sidx,
-                          int32_t *sidx2, int32_t *spa, int32_t *spb, int32_t *slptr,
-                          int32_t *slent) {
-    const int K = 2 * B;
-    for (int k = threadIdx.x; k < K; k += blockDim.x) {
-        sidx[k] = plan.idx[b * K + k];
-        if (theta) sidx2[k] = plan.idx2[b * K + k];
-        slent[k] = plan.lent[b * K + k];
-    }
-    for (int k = threadIdx.x; k <= K; k += blockDim.x) slptr[k] = plan.lptr[b * (K + 1) + k];
-    for (int l = threadIdx.x; l < B; l += blockDim.x) {
-        spa[l] = plan.pa[b * B + l];
-        spb[l] = plan.pb[b * B + l];
-    }
-    __syncthreads();
-}
-
 // Copy n elements global -> shared (both 16-byte aligned, n rounded up to 16 bytes; the
 // buffers have that slack) with 16-byte loads, eight in flight per thread.
 template <typename T>
@@ -409,74 +221,62 @@ __device__ void phase_b(int nb, int B, const T *gcoef, const T *gpre, T *scoef, 
     __syncthreads();
 }
 
-// Phase C body shared by both passes.  For every row t of this CTA's band and every
-// distinct target index k: cache[t][tgt[k]] += sum over the list of k of
-// mu_l Sigma[t][partner[e]].  Rows are processed kRowsC at a time: the Sigma values at
-// the partner columns and the cache values at the target columns are first staged in
-// shared memory by all threads (independent loads), then combined, then written back.
-template <typename T>
-__device__ void phase_c(int nb, int ntgt, const int32_t *tgt, const int32_t *part,
-                        const int32_t *lptr, const int32_t *lent, const T *__restrict__ Sig,
-                        int64_t q, T *cache, int64_t ld, int64_t r0, int64_t r1, T *work,
-                        const double *mu) {
-    const int nent = lptr[ntgt];
-    T *smu = work;
-    T *sS = smu + ((nb + 3) & ~3);
-    for (int l = threadIdx.x; l < nb; l += blockDim.x) smu[l] = (T)__ldcg(mu + l);
-    const int npart = nent;  // one staged Sigma value per entry
-    T *sC = sS + (size_t)kRowsC * ((npart + 3) & ~3);
-    const int lds = (npart + 3) & ~3, ldc = (ntgt + 3) & ~3;
-    for (int64_t t0 = r0; t0 < r1; t0 += kRowsC) {
-        const int nr = (int)((r1 - t0) < kRowsC ? (r1 - t0) : kRowsC);
-        __syncthreads();
-        const int tot_s = nr * npart, tot_c = nr * ntgt;
-        for (int base = threadIdx.x; base < tot_s; base += 8 * blockDim.x) {
-            T v[8];
+// 16-byte vector of the cache type
+template <typename T> struct V16;
+template <> struct V16<float> { using type = float4; static const int n = 4; };
+template <> struct V16<double> { using type = double2; static const int n = 2; };
+
+__device__ __forceinline__ float vget(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
+__device__ __forceinline__ double vget(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
+
+// Sum of NV per-thread values over the CTA, in double, in a fixed order; results in r[]
+// (valid in every thread).  red: shared scratch of kThreads / 32 * NV doubles.
+template <int NV>
+__device__ void cta_sums(double *v, double *red, double *r) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int x = base + u * blockDim.x;
-                if (x < tot_s) {
-                    const int rr = x / npart, e = x - rr * npart;
-                    v[u] = Sig[(t0 + rr) * q + part[lent[e] & 0xffff]];
-                }
-            }
+    for (int k = 0; k < NV; k++) v[k] = warp_sum(v[k]);
+    __syncthreads();
+    if (lane == 0)
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int x = base + u * blockDim.x;
-                if (x < tot_s) {
-                    const int rr = x / npart, e = x - rr * npart;
-                    sS[(size_t)rr * lds + e] = v[u];
-                }
-            }
+        for (int k = 0; k < NV; k++) red[warp * NV + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double s = 0.0;
+        for (int w = 0; w < nw; w++) s += red[w * NV + k];
+        r[k] = s;
+    }
+    __syncthreads();
+}
+
+// Load the coordinates of the batch [s, s + nb) into shared memory and find its segments
+// (maximal runs of coordinates with the same first index; the lists are row-major, so a
+// segment is the part of one row of the active set that falls in the batch).
+__device__ void load_batch(const int32_t *__restrict__ ai, const int32_t *__restrict__ aj,
+                           int64_t s, int nb, int32_t *sa, int32_t *sb, int32_t *sseg,
+                           int32_t *snseg) {
+    for (int l = threadIdx.x; l < nb; l += blockDim.x) {
+        sa[l] = ai[s + l];
+        sb[l] = aj[s + l];
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        int base = 0;
+        for (int l0 = 0; l0 < nb; l0 += 32) {
+            const int l = l0 + lane;
+            const bool f = l < nb && (l == 0 || sa[l] != sa[l - 1]);
+            const unsigned m = __ballot_sync(0xffffffffu, f);
+            if (f) sseg[base + __popc(m & ((1u << lane) - 1u))] = l;
+            base += __popc(m);
         }
-        for (int base = threadIdx.x; base < tot_c; base += 8 * blockDim.x) {
-            T v[8];
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int x = base + u * blockDim.x;
-                if (x < tot_c) {
-                    const int rr = x / ntgt, k = x - rr * ntgt;
-                    v[u] = __ldcg(cache + (t0 + rr) * ld + tgt[k]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int x = base + u * blockDim.x;
-                if (x < tot_c) {
-                    const int rr = x / ntgt, k = x - rr * ntgt;
-                    sC[(size_t)rr * ldc + k] = v[u];
-                }
-            }
-        }
-        __syncthreads();
-        for (int x = threadIdx.x; x < tot_c; x += blockDim.x) {
-            const int rr = x / ntgt, k = x - rr * ntgt;
-            const T *srow = sS + (size_t)rr * lds;
-            T acc = T(0);
-            for (int e = lptr[k]; e < lptr[k + 1]; e++) acc = fma(smu[lent[e] >> 16], srow[e], acc);
-            cache[(t0 + rr) * ld + tgt[k]] = sC[(size_t)rr * ldc + k] + acc;
+        if (lane == 0) {
+            sseg[base] = nb;
+            *snseg = base;
         }
     }
+    __syncthreads();
 }
 
 // ---------------------------------------------------------------------------------
@@ -488,38 +288,39 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                     const double *__restrict__ Sd, const double *__restrict__ Pd,
                     const double *__restrict__ G, const double *__restrict__ Lam, int64_t m,
                     const int32_t *__restrict__ ai, const int32_t *__restrict__ aj,
-                    double lam_off, double lam_diag, double *D, T *Ut, int B, BatchPlan plan,
+                    double lam_off, double lam_diag, double *D, T *Ut, int B,
                     SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[(kThreads / 32) * 6];
     const SmemLayout L = smem_layout<T>(B);
-    const int K = 2 * B;
-    int32_t *sidx = reinterpret_cast<int32_t *>(smem + L.meta);
-    int32_t *spa = sidx + 2 * K;
-    int32_t *spb = spa + B;
-    int32_t *slptr = spb + B;
-    int32_t *slent = slptr + K + 1;
+    int32_t *sa = reinterpret_cast<int32_t *>(smem + L.meta);
+    int32_t *sb = sa + B;
+    int32_t *sseg = sb + B;
+    int32_t *snseg = sseg + B + 1;
     unsigned char *work = smem + L.work;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned nblk = gridDim.x;
-    T *pre = reinterpret_cast<T *>(scr.sub1);   // [PRE_N][B]
-    T *gcoef = reinterpret_cast<T *>(scr.sub2); // [B(B-1)/2]
+    T *pre = reinterpret_cast<T *>(scr.sub1);    // [PRE_N][B]
+    T *gcoef = reinterpret_cast<T *>(scr.sub2);  // column-packed coefficients
     const int64_t rows_per = (q + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)nblk * blockDim.x;
+    using VT = typename V16<T>::type;
+    constexpr int VN = V16<T>::n;
+    const bool vec = (q % VN) == 0;
 
-    for (int64_t b = 0; b < plan.nbatch; b++) {
-        const int64_t s = b * B;
+    for (int64_t s = 0; s < m; s += B) {
         const int nb = (int)((m - s) < B ? (m - s) : B);
-        const int nidx = plan.nidx[b];
-        load_meta(plan, b, B, false, sidx, nullptr, spa, spb, slptr, slent);
+        load_batch(ai, aj, s, nb, sa, sb, sseg, snseg);
 
-        // ---- phase A: dots and step constants (two coordinates per CTA in one pass) ----
+        // ---- phase A: dot products and step constants, two coordinates per CTA ----
         for (int l = blockIdx.x; l < nb; l += 2 * nblk) {
             const int lb = l + (int)nblk;
             const bool two = lb < nb;
-            const int64_t i0 = ai[s + l], j0 = aj[s + l];
-            const int64_t i1 = two ? ai[s + lb] : i0, j1 = two ? aj[s + lb] : j0;
+            const int64_t i0 = sa[l], j0 = sb[l];
+            const int64_t i1 = two ? sa[lb] : i0, j1 = two ? sb[lb] : j0;
             // (Sigma D Sigma)_ij = Sigma_i . U_{:,j}, (Psi D Sigma)_ij = Psi_i . U_{:,j},
             // (Psi D Sigma)_ji = Psi_j . U_{:,i}
             const T *x0 = Sig + i0 * q, *x1 = Psi + i0 * q, *x2 = Psi + j0 * q;
@@ -527,39 +328,67 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             const T *z0 = Sig + i1 * q, *z1 = Psi + i1 * q, *z2 = Psi + j1 * q;
             const T *w0 = Ut + j1 * q, *w1 = Ut + i1 * q;
             T a0 = T(0), a1 = T(0), a2 = T(0), b0 = T(0), b1 = T(0), b2 = T(0);
-            for (int64_t t = threadIdx.x; t < q; t += blockDim.x) {
-                const T u0 = __ldcg(y0 + t), u1 = __ldcg(y1 + t);
-                a0 = fma(x0[t], u0, a0);
-                a1 = fma(x1[t], u0, a1);
-                a2 = fma(x2[t], u1, a2);
-                if (two) {
-                    const T v0 = __ldcg(w0 + t), v1 = __ldcg(w1 + t);
-                    b0 = fma(z0[t], v0, b0);
-                    b1 = fma(z1[t], v0, b1);
-                    b2 = fma(z2[t], v1, b2);
+            if (vec) {
+                const int64_t nv = q / VN;
+#pragma unroll 4
+                for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+                    const VT X0 = reinterpret_cast<const VT *>(x0)[v];
+                    const VT X1 = reinterpret_cast<const VT *>(x1)[v];
+                    const VT X2 = reinterpret_cast<const VT *>(x2)[v];
+                    const VT Y0 = __ldcg(reinterpret_cast<const VT *>(y0) + v);
+                    const VT Y1 = __ldcg(reinterpret_cast<const VT *>(y1) + v);
+#pragma unroll
+                    for (int k = 0; k < VN; k++) {
+                        a0 = fma(vget(X0, k), vget(Y0, k), a0);
+                        a1 = fma(vget(X1, k), vget(Y0, k), a1);
+                        a2 = fma(vget(X2, k), vget(Y1, k), a2);
+                    }
+                    if (two) {
+                        const VT Z0 = reinterpret_cast<const VT *>(z0)[v];
+                        const VT Z1 = reinterpret_cast<const VT *>(z1)[v];
+                        const VT Z2 = reinterpret_cast<const VT *>(z2)[v];
+                        const VT W0 = __ldcg(reinterpret_cast<const VT *>(w0) + v);
+                        const VT W1 = __ldcg(reinterpret_cast<const VT *>(w1) + v);
+#pragma unroll
+                        for (int k = 0; k < VN; k++) {
+                            b0 = fma(vget(Z0, k), vget(W0, k), b0);
+                            b1 = fma(vget(Z1, k), vget(W0, k), b1);
+                            b2 = fma(vget(Z2, k), vget(W1, k), b2);
+                        }
+                    }
+                }
+            } else {
+                for (int64_t t = threadIdx.x; t < q; t += blockDim.x) {
+                    const T u0 = __ldcg(y0 + t), u1 = __ldcg(y1 + t);
+                    a0 = fma(x0[t], u0, a0);
+                    a1 = fma(x1[t], u0, a1);
+                    a2 = fma(x2[t], u1, a2);
+                    if (two) {
+                        const T v0 = __ldcg(w0 + t), v1 = __ldcg(w1 + t);
+                        b0 = fma(z0[t], v0, b0);
+                        b1 = fma(z1[t], v0, b1);
+                        b2 = fma(z2[t], v1, b2);
+                    }
                 }
             }
+            double v6[6] = {(double)a0, (double)a1, (double)a2, (double)b0, (double)b1, (double)b2};
             double d[6];
-            d[0] = block_sum((double)a0);
-            d[1] = block_sum((double)a1);
-            d[2] = block_sum((double)a2);
-            d[3] = block_sum((double)b0);
-            d[4] = block_sum((double)b1);
-            d[5] = block_sum((double)b2);
+            cta_sums<6>(v6, s_red, d);
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             if (which >= 0) {
                 const int lw = which ? lb : l;
                 const int64_t i = which ? i1 : i0, j = which ? j1 : j0;
-                const double *dd = d + 3 * which;
+                const double d0 = which ? d[3] : d[0], d1 = which ? d[4] : d[1],
+                             d2 = which ? d[5] : d[2];
                 double a, bb, lam;
                 if (i != j) {
                     const double sij = (double)Sig[i * q + j], pij = (double)Psi[i * q + j];
                     a = sij * sij + Sd[i] * Sd[j] + Sd[i] * Pd[j] + Sd[j] * Pd[i] + 2.0 * sij * pij;
-                    bb = G[i * q + j] + dd[0] + dd[1] + dd[2];
+                    bb = G[i * q + j] + d0 + d1 + d2;
                     lam = lam_off;
                 } else {
                     a = Sd[i] * Sd[i] + 2.0 * Sd[i] * Pd[i];
-                    bb = G[i * q + i] + dd[0] + 2.0 * dd[1];
+                    bb = G[i * q + i] + d0 + 2.0 * d1;
                     lam = lam_diag;
                 }
                 step_constants<T>(bb, a, Lam[i * q + j], lam, pre, B, lw);
@@ -573,8 +402,8 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             for (int64_t e = gtid; e < ncoef; e += gthreads) {
                 int l, l1;
                 decode_pair((int)e, l, l1);
-                const int64_t pi = sidx[spa[l]], pj = sidx[spb[l]];
-                const int64_t pa = sidx[spa[l1]], pb = sidx[spb[l1]];
+                const int64_t pi = sa[l], pj = sb[l];
+                const int64_t pa = sa[l1], pb = sb[l1];
                 auto S = [&](int64_t x, int64_t y) -> T { return Sig[x * q + y]; };
                 auto P = [&](int64_t x, int64_t y) -> T { return Psi[x * q + y]; };
                 T c1, c2, c3;
@@ -596,7 +425,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             phase_b<T, NS>(nb, B, gcoef, pre, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
             for (int l = threadIdx.x; l < nb; l += blockDim.x) {
-                const int64_t i = ai[s + l], j = aj[s + l];
+                const int64_t i = sa[l], j = sb[l];
                 const double mu = scr.mu[l];
                 D[i * q + j] = mu;
                 if (i != j) D[j * q + i] = mu;
@@ -604,9 +433,50 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
-        // ---- phase C: Ut[t][u] += sum mu Sigma[t][partner] over this CTA's rows t ----
-        phase_c<T>(nb, nidx, sidx, sidx, slptr, slent, Sig, q, Ut, q, r0, r1,
-                   reinterpret_cast<T *>(work), scr.mu);
+        // ---- phase C: rows t of this CTA's band, segment by segment ----
+        // coordinate (a, b) of a segment with row a: U_a += mu Sigma_b, U_b += mu Sigma_a
+        // (b != a); transposed: Ut[t][a] += sum mu Sigma[t][b], Ut[t][b] += mu Sigma[t][a]
+        {
+            T *smu = reinterpret_cast<T *>(work);
+            for (int l = threadIdx.x; l < nb; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
+            __syncthreads();
+            const int nseg = *snseg;
+            for (int64_t t = r0 + warp; t < r1; t += (kThreads / 32)) {
+                const T *Sr = Sig + t * q;
+                T *Ur = Ut + t * q;
+                for (int g = 0; g < nseg; g++) {
+                    const int l0 = sseg[g], l1 = sseg[g + 1];
+                    const int64_t a = sa[l0];
+                    // issue every load of this lane first (up to NS coordinates per lane)
+                    T sv[NS], uv[NS], mv[NS];
+                    int64_t bv[NS];
+                    const T sta = Sr[a];
+#pragma unroll
+                    for (int k = 0; k < NS; k++) {
+                        const int l = l0 + lane + 32 * k;
+                        bv[k] = -1;
+                        if (l < l1) {
+                            bv[k] = sb[l];
+                            mv[k] = smu[l];
+                            sv[k] = Sr[bv[k]];
+                            uv[k] = (bv[k] != a) ? __ldcg(Ur + bv[k]) : T(0);
+                        }
+                    }
+                    T dot = T(0);
+#pragma unroll
+                    for (int k = 0; k < NS; k++) {
+                        if (bv[k] >= 0) {
+                            dot = fma(mv[k], sv[k], dot);
+                            if (bv[k] != a) Ur[bv[k]] = uv[k] + mv[k] * sta;
+                        }
+                    }
+                    dot = warp_sum(dot);
+                    __syncwarp();
+                    if (lane == 0) Ur[a] = __ldcg(Ur + a) + dot;
+                    __syncwarp();
+                }
+            }
+        }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
     }
 }
@@ -620,17 +490,16 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                    const T *__restrict__ Sig, const double *__restrict__ Sd,
                    const double *__restrict__ W, double *Theta, int64_t m,
                    const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam,
-                   T *dVt, int B, BatchPlan plan, SweepScratch scr) {
+                   T *dVt, int B, SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[(kThreads / 32) * 2];
     const SmemLayout L = smem_layout<T>(B);
-    const int K = 2 * B;
-    int32_t *sI = reinterpret_cast<int32_t *>(smem + L.meta);
-    int32_t *sJ = sI + K;
-    int32_t *spa = sJ + K;
-    int32_t *spb = spa + B;
-    int32_t *slptr = spb + B;
-    int32_t *slent = slptr + K + 1;
+    int32_t *sa = reinterpret_cast<int32_t *>(smem + L.meta);
+    int32_t *sb = sa + B;
+    int32_t *sseg = sb + B;
+    int32_t *snseg = sseg + B + 1;
     unsigned char *work = smem + L.work;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned nblk = gridDim.x;
     T *pre = reinterpret_cast<T *>(scr.sub1);
     T *gcoef = reinterpret_cast<T *>(scr.sub2);
@@ -639,37 +508,56 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t gthreads = (int64_t)nblk * blockDim.x;
+    using VT = typename V16<T>::type;
+    constexpr int VN = V16<T>::n;
 
-    for (int64_t b = 0; b < plan.nbatch; b++) {
-        const int64_t s = b * B;
+    for (int64_t s = 0; s < m; s += B) {
         const int nb = (int)((m - s) < B ? (m - s) : B);
-        const int nI = plan.nidx[b];
-        load_meta(plan, b, B, true, sI, sJ, spa, spb, slptr, slent);
+        load_batch(ti, tj, s, nb, sa, sb, sseg, snseg);
         // rows of Delta V that can be nonzero: those at or before the batch's first row
-        const int64_t tmax = (int64_t)ti[s] + 1;
+        const int64_t tmax = (int64_t)sa[0] + 1;
 
         // ---- phase A (two coordinates per CTA in one pass) ----
         for (int l = blockIdx.x; l < nb; l += 2 * nblk) {
             const int lb = l + (int)nblk;
             const bool two = lb < nb;
-            const int64_t i0 = ti[s + l], j0 = tj[s + l];
-            const int64_t i1 = two ? ti[s + lb] : i0, j1 = two ? tj[s + lb] : j0;
+            const int64_t i0 = sa[l], j0 = sb[l];
+            const int64_t i1 = two ? sa[lb] : i0, j1 = two ? sb[lb] : j0;
             // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
             const T *x0 = Sxx + i0 * p, *y0 = dVt + j0 * p, *x1 = Sxx + i1 * p, *y1 = dVt + j1 * p;
             T a0 = T(0), a1 = T(0);
-            for (int64_t t = threadIdx.x; t < tmax; t += blockDim.x) {
+            int64_t tv = 0;
+            if ((p % VN) == 0) {
+                const int64_t nv = tmax / VN;
+#pragma unroll 4
+                for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
+                    const VT X0 = reinterpret_cast<const VT *>(x0)[v];
+                    const VT Y0 = __ldcg(reinterpret_cast<const VT *>(y0) + v);
+#pragma unroll
+                    for (int k = 0; k < VN; k++) a0 = fma(vget(X0, k), vget(Y0, k), a0);
+                    if (two) {
+                        const VT X1 = reinterpret_cast<const VT *>(x1)[v];
+                        const VT Y1 = __ldcg(reinterpret_cast<const VT *>(y1) + v);
+#pragma unroll
+                        for (int k = 0; k < VN; k++) a1 = fma(vget(X1, k), vget(Y1, k), a1);
+                    }
+                }
+                tv = nv * VN;
+            }
+            for (int64_t t = tv + threadIdx.x; t < tmax; t += blockDim.x) {
                 a0 = fma(x0[t], __ldcg(y0 + t), a0);
                 if (two) a1 = fma(x1[t], __ldcg(y1 + t), a1);
             }
-            const double d0 = block_sum((double)a0);
-            const double d1 = block_sum((double)a1);
+            double v2[2] = {(double)a0, (double)a1};
+            double d[2];
+            cta_sums<2>(v2, s_red, d);
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             if (which >= 0) {
                 const int lw = which ? lb : l;
                 const int64_t i = which ? i1 : i0, j = which ? j1 : j0;
                 const double xii = Xd[i];
                 const double a = (xii != 0.0) ? 2.0 * Sd[j] * xii : 0.0;
-                step_constants<T>(2.0 * W[i * q + j] + 2.0 * (which ? d1 : d0), a,
+                step_constants<T>(2.0 * W[i * q + j] + 2.0 * d[which], a,
                                   __ldcg(Theta + i * q + j), lam, pre, B, lw);
             }
         }
@@ -679,8 +567,8 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
             for (int64_t e = gtid; e < ncoef; e += gthreads) {
                 int l, l1;
                 decode_pair((int)e, l, l1);
-                const int64_t i = sI[spa[l]], j = sJ[spb[l]];
-                const int64_t a = sI[spa[l1]], bq = sJ[spb[l1]];
+                const int64_t i = sa[l], j = sb[l];
+                const int64_t a = sa[l1], bq = sb[l1];
                 gcoef[colbase(l1, B) + (l - l1 - 1)] = T(2) * Sxx[i * p + a] * Sig[bq * q + j];
             }
         }
@@ -690,15 +578,45 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
             phase_b<T, NS>(nb, B, gcoef, pre, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
             for (int l = threadIdx.x; l < nb; l += blockDim.x) {
-                const int64_t i = ti[s + l], j = tj[s + l];
+                const int64_t i = sa[l], j = sb[l];
                 Theta[i * q + j] = __ldcg(Theta + i * q + j) + scr.mu[l];
             }
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
-        // ---- phase C: dVt[t][i] += sum mu Sigma[t][j] over this CTA's rows t ----
-        phase_c<T>(nb, nI, sI, sJ, slptr, slent, Sig, q, dVt, p, r0, r1,
-                   reinterpret_cast<T *>(work), scr.mu);
+        // ---- phase C: dVt[t][i] += sum over the segment of row i of mu Sigma[t][j] ----
+        {
+            T *smu = reinterpret_cast<T *>(work);
+            for (int l = threadIdx.x; l < nb; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
+            __syncthreads();
+            const int nseg = *snseg;
+            for (int64_t t = r0 + warp; t < r1; t += (kThreads / 32)) {
+                const T *Sr = Sig + t * q;
+                T *Vr = dVt + t * p;
+                for (int g = 0; g < nseg; g++) {
+                    const int l0 = sseg[g], l1 = sseg[g + 1];
+                    T sv[NS], mv[NS];
+#pragma unroll
+                    for (int k = 0; k < NS; k++) {
+                        const int l = l0 + lane + 32 * k;
+                        sv[k] = T(0);
+                        mv[k] = T(0);
+                        if (l < l1) {
+                            mv[k] = smu[l];
+                            sv[k] = Sr[sb[l]];
+                        }
+                    }
+                    T dot = T(0);
+#pragma unroll
+                    for (int k = 0; k < NS; k++) dot = fma(mv[k], sv[k], dot);
+                    dot = warp_sum(dot);
+                    if (lane == 0) {
+                        const int64_t i = sa[l0];
+                        Vr[i] = __ldcg(Vr + i) + dot;
+                    }
+                }
+            }
+        }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
     }
 }
@@ -786,15 +704,8 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
                          cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
     if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
-    const int64_t nbatch = (m + B - 1) / B;
-    CGGM_TRY(plan_reserve(plan, B, nbatch, false));
+    (void)plan;
     CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
-    plan.nbatch = nbatch;
-    const int K = 2 * B;
-    note_launch();
-    lambda_plan_kernel<<<(unsigned)nbatch, 256, (size_t)(3 * K + 1) * sizeof(int), st>>>(
-        m, ai, aj, B, plan);
-    CGGM_CUDA_TRY(cudaGetLastError());
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), st));
@@ -802,7 +713,7 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
     void *args[] = {(void *)&q, (void *)&Sigma, (void *)&Psi, (void *)&Sd, (void *)&Pd,
                     (void *)&G, (void *)&Lambda, (void *)&m, (void *)&ai, (void *)&aj,
                     (void *)&lam_off, (void *)&lam_diag, (void *)&D, (void *)&U, (void *)&B,
-                    (void *)&plan, (void *)&scr};
+                    (void *)&scr};
     const void *fn;
     switch (B) {
         case 32: fn = (const void *)lambda_sweep_kernel<T, 1>; break;
@@ -825,16 +736,7 @@ cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const do
                                         SweepScratch scr, cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
     if (B != 32 && B != 64 && B != 128) return CGGM_EINVAL;
-    const int64_t nbatch = (m + B - 1) / B;
-    if (nbatch > plan.cap) return CGGM_EINVAL;
-    plan.B = B;
-    plan.K = 2 * B;
-    plan.nbatch = nbatch;
-    const int K = 2 * B;
-    note_launch();
-    lambda_plan_kernel<<<(unsigned)nbatch, 256, (size_t)(3 * K + 1) * sizeof(int), st>>>(
-        m, ai, aj, B, plan);
-    CGGM_CUDA_TRY(cudaGetLastError());
+    (void)plan;
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), st));
@@ -842,7 +744,7 @@ cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const do
     void *args[] = {(void *)&q, (void *)&Sigma, (void *)&Psi, (void *)&Sd, (void *)&Pd,
                     (void *)&G, (void *)&Lambda, (void *)&m, (void *)&ai, (void *)&aj,
                     (void *)&lam_off, (void *)&lam_diag, (void *)&D, (void *)&U, (void *)&B,
-                    (void *)&plan, (void *)&scr};
+                    (void *)&scr};
     const void *fn = B == 32 ? (const void *)lambda_sweep_kernel<double, 1>
                    : B == 64 ? (const void *)lambda_sweep_kernel<double, 2>
                              : (const void *)lambda_sweep_kernel<double, 4>;
@@ -857,23 +759,15 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
                         BatchPlan &plan, SweepScratch &scr, cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
     if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
-    const int64_t nbatch = (m + B - 1) / B;
-    CGGM_TRY(plan_reserve(plan, B, nbatch, true));
+    (void)plan;
     CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
-    plan.nbatch = nbatch;
-    const int K = 2 * B;
-    note_launch();
-    theta_plan_kernel<<<(unsigned)nbatch, 256, (size_t)(4 * K + 1) * sizeof(int), st>>>(
-        m, ti, tj, B, plan);
-    CGGM_CUDA_TRY(cudaGetLastError());
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), st));
     const size_t smem = smem_layout<T>(B).total;
     void *args[] = {(void *)&p, (void *)&q, (void *)&Sxx, (void *)&Xd, (void *)&Sigma,
                     (void *)&Sd, (void *)&W, (void *)&Theta, (void *)&m, (void *)&ti,
-                    (void *)&tj, (void *)&lam, (void *)&dV, (void *)&B, (void *)&plan,
-                    (void *)&scr};
+                    (void *)&tj, (void *)&lam, (void *)&dV, (void *)&B, (void *)&scr};
     const void *fn;
     switch (B) {
         case 32: fn = (const void *)theta_sweep_kernel<T, 1>; break;
