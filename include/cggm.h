@@ -185,6 +185,17 @@ cggm_status cggm_active_sets(cggm_ctx *ctx, int64_t p, int64_t q, const double *
                              int penalize_diag, int32_t *li, int32_t *lj, int64_t *m_lambda,
                              int32_t *ti, int32_t *tj, int64_t *m_theta);
 
+/* Dense contraction on the tensor cores, the form every product from X takes in the mixed
+ * path (R = X Theta, P = R Sigma, Psi = P^T P / n, X^T (Y + P); Section 2.3 lists them):
+ *     C = alpha A B^T + beta C,
+ * A M x K, B N x K, C M x N, row-major float in device memory; lda, ldb, ldc in elements,
+ * lda and ldb multiples of 4 with 16-byte aligned bases (CGGM_EINVAL otherwise).
+ * mode 0: one TF32 product (10-bit mantissa operands, FP32 accumulation); mode 1: three
+ * TF32 products on a high/low split of both operands (close to FP32 accuracy). */
+cggm_status cggm_contract(cggm_ctx *ctx, int64_t M, int64_t N, int64_t K, float alpha,
+                          const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+                          float *C, int64_t ldc, int mode);
+
 /*
  * No-allocation variant of cggm_lambda_sweep (the paper has no counterpart: this is an
  * interface for embedding).  Some callers cannot call cudaMalloc: code that runs under

@@ -27,7 +27,7 @@ CGGM_F32, CGGM_F64 = 0, 1
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
-    "cggm_active_sets", "cggm_lambda_sweep_noalloc",
+    "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract",
 ]
 
 
@@ -87,6 +87,8 @@ def _lib():
         lib.cggm_theta_sweep.argtypes = [vp, i64, i64, i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp]
         lib.cggm_active_sets.argtypes = [vp, i64, i64, vp, vp, vp, vp, dbl, dbl, ip, vp, vp,
                                          ctypes.POINTER(i64), vp, vp, ctypes.POINTER(i64)]
+        lib.cggm_contract.argtypes = [vp, i64, i64, i64, ctypes.c_float, vp, i64, vp, i64,
+                                      ctypes.c_float, vp, i64, ip]
         lib.cggm_lambda_sweep_noalloc.argtypes = [i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp,
                                                   vp]
         for name in EXPORTED:
@@ -95,7 +97,8 @@ def _lib():
                                                      "cggm_grad", "cggm_cholesky",
                                                      "cggm_lambda_sweep", "cggm_theta_sweep",
                                                      "cggm_active_sets",
-                                                     "cggm_lambda_sweep_noalloc"):
+                                                     "cggm_lambda_sweep_noalloc",
+                                                     "cggm_contract"):
                 f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -264,6 +267,18 @@ class Context:
                                        float(lam_T), int(precision), out.ctypes.data),
                "cggm_theta_sweep")
         return out
+
+    def cggm_contract(self, A, B, C=None, alpha=1.0, beta=0.0, mode=1):
+        """C = alpha A B^T + beta C on the tensor cores; A, B, C float32 CUDA tensors."""
+        import torch
+        M, K = A.shape
+        N = B.shape[0]
+        if C is None:
+            C = torch.zeros((M, N), device=A.device, dtype=torch.float32)
+        _check(_lib().cggm_contract(self._h, M, N, K, float(alpha), A.data_ptr(), A.stride(0),
+                                    B.data_ptr(), B.stride(0), float(beta), C.data_ptr(),
+                                    C.stride(0), int(mode)), "cggm_contract")
+        return C
 
     def cggm_active_sets(self, G_L, G_T, Lam, Th, lam_L, lam_T, penalize_diag=True):
         q = Lam.shape[0]

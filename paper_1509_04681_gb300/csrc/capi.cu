@@ -9,6 +9,7 @@
 #include "chol.cuh"
 #include "common.cuh"
 #include "dense.cuh"
+#include "gemm_tc.cuh"
 #include "iter.cuh"
 #include "sweeps.cuh"
 
@@ -66,6 +67,7 @@ struct cggm_ctx {
     Buf D, U, dV, li, lj, ti, tj, rowcnt;
     // scalars
     Buf scal, cnt, err;
+    Buf tcA_hi, tcA_lo, tcB_hi, tcB_lo;  // split operands of the tensor-core contraction
     Buf partial;
     BatchPlan planL, planT;
     SweepScratch scr;
@@ -612,7 +614,8 @@ void cggm_destroy(cggm_ctx *c) {
                    &c->Lam, &c->Th, &c->Lch, &c->logd, &c->Sig, &c->Sig_f, &c->Sd, &c->Lam_a,
                    &c->Lch_a, &c->logd_a, &c->work, &c->Rt, &c->Pt, &c->Z, &c->Psi, &c->Pd,
                    &c->GL, &c->GT, &c->W, &c->D, &c->U, &c->dV, &c->li, &c->lj, &c->ti,
-                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial};
+                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial,
+                   &c->tcA_hi, &c->tcA_lo, &c->tcB_hi, &c->tcB_lo};
     for (Buf *b : bufs) if (b->p) cudaFree(b->p);
     plan_free(c->planL);
     plan_free(c->planT);
@@ -923,6 +926,36 @@ cggm_status cggm_active_sets(cggm_ctx *c, int64_t p, int64_t q, const double *G_
     CGGM_CUDA_TRY(cudaMemcpyAsync(ti, c->ti.p, 4 * (size_t)hc[1], cudaMemcpyDefault, c->st));
     CGGM_CUDA_TRY(cudaMemcpyAsync(tj, c->tj.p, 4 * (size_t)hc[1], cudaMemcpyDefault, c->st));
     return sync_err(c);
+}
+
+cggm_status cggm_contract(cggm_ctx *c, int64_t M, int64_t N, int64_t K, float alpha,
+                          const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
+                          float *C, int64_t ldc, int mode) {
+    if (!c || !A || !B || !C || M < 0 || N < 0 || K <= 0 || ldc < N) return CGGM_EINVAL;
+    if ((mode != 0 && mode != 1) || lda < K || ldb < K) return CGGM_EINVAL;
+    if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) return CGGM_EINVAL;
+    CGGM_TRY(set_device(c));
+    CGGM_TRY(ensure(c->err, sizeof(int)));
+    CGGM_CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), c->st));
+    if (mode == 0) {
+        CGGM_TRY(gemm_tc_nt(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, false, nullptr, nullptr,
+                            P<int>(c->err), c->st));
+    } else {
+        CGGM_TRY(ensure(c->tcA_hi, 4 * (size_t)M * lda));
+        CGGM_TRY(ensure(c->tcA_lo, 4 * (size_t)M * lda));
+        CGGM_TRY(ensure(c->tcB_hi, 4 * (size_t)N * ldb));
+        CGGM_TRY(ensure(c->tcB_lo, 4 * (size_t)N * ldb));
+        split_tf32(M, K, lda, A, P<float>(c->tcA_hi), P<float>(c->tcA_lo), c->st);
+        split_tf32(N, K, ldb, B, P<float>(c->tcB_hi), P<float>(c->tcB_lo), c->st);
+        CGGM_TRY(gemm_tc_nt(M, N, K, alpha, P<float>(c->tcA_hi), lda, P<float>(c->tcB_hi), ldb,
+                            beta, C, ldc, true, P<float>(c->tcA_lo), P<float>(c->tcB_lo),
+                            P<int>(c->err), c->st));
+    }
+    int h = 0;
+    CGGM_TRY(read_dev_err(c, &h));
+    if (h == DEV_TIMEOUT) return CGGM_ETIMEDOUT;
+    if (h != 0) return CGGM_ECUDA;
+    return CGGM_OK;
 }
 
 }  // extern "C"
