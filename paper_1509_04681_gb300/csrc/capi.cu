@@ -68,6 +68,8 @@ struct cggm_ctx {
     // scalars
     Buf scal, cnt, err;
     Buf tcA_hi, tcA_lo, tcB_hi, tcB_lo;  // split operands of the tensor-core contraction
+    // mixed path: float operands of the tensor-core products and their TF32 hi/lo splits
+    Buf Xt_hi, Xt_lo, Sig_hi, Sig_lo, R_f, R_hi, R_lo, Pt_f, Pt_hi, Pt_lo, Zf, tcerr;
     Buf partial;
     BatchPlan planL, planT;
     SweepScratch scr;
@@ -220,6 +222,54 @@ struct Solver {
         return CGGM_OK;
     }
 
+    // The mixed path runs the products from X on the tensor cores (3xTF32) when every
+    // contracted dimension gives 16-byte rows (multiples of 4 floats).
+    bool tc() const { return sizeof(T) == 4 && z.n % 4 == 0 && z.p % 4 == 0 && z.q % 4 == 0; }
+
+    cggm_status tc_alloc() {
+        const int64_t n = z.n, p = z.p, q = z.q;
+        Buf *pn[] = {&c->Xt_hi, &c->Xt_lo};
+        for (Buf *b : pn) CGGM_TRY(ensure(*b, 4 * (size_t)p * n));
+        Buf *qq[] = {&c->Sig_hi, &c->Sig_lo};
+        for (Buf *b : qq) CGGM_TRY(ensure(*b, 4 * (size_t)q * q));
+        Buf *nq[] = {&c->R_f, &c->R_hi, &c->R_lo, &c->Pt_f, &c->Pt_hi, &c->Pt_lo};
+        for (Buf *b : nq) CGGM_TRY(ensure(*b, 4 * (size_t)n * q));
+        CGGM_TRY(ensure(c->Zf, 4 * (size_t)p * q));
+        CGGM_TRY(ensure(c->tcerr, sizeof(int)));
+        return CGGM_OK;
+    }
+
+    // Pt_f = Sigma R^T (q x n) on the tensor cores from the current splits of Sigma and R,
+    // then its own split.
+    cggm_status tc_P() {
+        const int64_t n = z.n, q = z.q;
+        CGGM_TRY(gemm_tc_nt(q, n, q, 1.0f, P<float>(c->Sig_hi), q, P<float>(c->R_hi), q, 0.0f,
+                            P<float>(c->Pt_f), n, true, P<float>(c->Sig_lo), P<float>(c->R_lo),
+                            P<int>(c->tcerr), st));
+        split_tf32(q, n, n, P<float>(c->Pt_f), P<float>(c->Pt_hi), P<float>(c->Pt_lo), st);
+        return CGGM_OK;
+    }
+
+    // out = a S_xy + scale X^T P_f^T... : Zf = scale Xt Pt_f^T (p x q), out = a S_xy + Zf
+    cggm_status tc_XtP(double scale, double a, double *out) {
+        const int64_t n = z.n, p = z.p, q = z.q;
+        CGGM_TRY(gemm_tc_nt(p, q, n, (float)scale, P<float>(c->Xt_hi), n, P<float>(c->Pt_hi), n,
+                            0.0f, P<float>(c->Zf), q, true, P<float>(c->Xt_lo), P<float>(c->Pt_lo),
+                            P<int>(c->tcerr), st));
+        axpy_f2d(p * q, a, P<double>(c->Sxy), P<float>(c->Zf), out, st);
+        return CGGM_OK;
+    }
+
+    cggm_status tc_check() {
+        if (!tc()) return CGGM_OK;
+        int h = 0;
+        CGGM_CUDA_TRY(cudaMemcpyAsync(&h, c->tcerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CGGM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (h == DEV_TIMEOUT) return CGGM_ETIMEDOUT;
+        if (h != 0) return CGGM_ECUDA;
+        return CGGM_OK;
+    }
+
     // S_yy, S_xy, S_xx (Section 2.1) from Xt (p x n) and Yt (q x n), double
     cggm_status covariances() {
         const int64_t n = z.n, p = z.p, q = z.q;
@@ -232,8 +282,17 @@ struct Solver {
         } else {
             CGGM_TRY(ensure(c->Xt_f, 4 * (size_t)p * n));
             convert_d2f(p * n, Xt, P<float>(c->Xt_f), st);
-            gemm<float>(false, true, p, p, n, (float)inv, P<float>(c->Xt_f), n, P<float>(c->Xt_f), n,
-                        0.0f, (float *)c->Sxx.p, p, st);
+            if (tc()) {
+                CGGM_TRY(tc_alloc());
+                CGGM_CUDA_TRY(cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), st));
+                split_tf32(p, n, n, P<float>(c->Xt_f), P<float>(c->Xt_hi), P<float>(c->Xt_lo), st);
+                CGGM_TRY(gemm_tc_nt(p, p, n, (float)inv, P<float>(c->Xt_hi), n, P<float>(c->Xt_hi),
+                                    n, 0.0f, (float *)c->Sxx.p, p, true, P<float>(c->Xt_lo),
+                                    P<float>(c->Xt_lo), P<int>(c->tcerr), st));
+            } else {
+                gemm<float>(false, true, p, p, n, (float)inv, P<float>(c->Xt_f), n,
+                            P<float>(c->Xt_f), n, 0.0f, (float *)c->Sxx.p, p, st);
+            }
         }
         note_launch();
         rowsq_kernel<double><<<(unsigned)p, 256, 0, st>>>(p, n, Xt, inv, P<double>(c->Xd));
@@ -260,25 +319,43 @@ struct Solver {
         const int64_t q = z.q;
         inverse_from_cholesky(q, P<double>(c->Lch), P<double>(c->Sig), P<double>(c->work), st);
         if (sizeof(T) == 4) convert_d2f(q * q, P<double>(c->Sig), (float *)c->Sig_f.p, st);
+        if (tc()) split_tf32(q, q, q, (const float *)c->Sig_f.p, P<float>(c->Sig_hi),
+                             P<float>(c->Sig_lo), st);
         diag_to_double<double>(q, P<double>(c->Sig), P<double>(c->Sd), st);
     }
     const T *SigT() {
         return sizeof(T) == 8 ? (const T *)c->Sig.p : (const T *)c->Sig_f.p;
     }
 
-    // Rt = Theta^T X^T (q x n) in double; Pt = Sigma Rt (double)
-    void products_R_P() {
+    // Rt = Theta^T X^T (q x n) in double (it enters the double-precision objective);
+    // Pt = Sigma Rt: double, or float on the tensor cores in the mixed path
+    cggm_status products_R_P() {
         const int64_t n = z.n, p = z.p, q = z.q;
         gemm<double>(true, false, q, n, p, 1.0, P<double>(c->Th), q, P<double>(c->Xt), n, 0.0,
                      P<double>(c->Rt), n, st);
+        if (tc()) {
+            transpose<double, float>(q, n, P<double>(c->Rt), P<float>(c->R_f), st);
+            split_tf32(n, q, q, P<float>(c->R_f), P<float>(c->R_hi), P<float>(c->R_lo), st);
+            return tc_P();
+        }
         gemm<double>(false, false, q, n, q, 1.0, P<double>(c->Sig), q, P<double>(c->Rt), n, 0.0,
                      P<double>(c->Pt), n, st);
+        return CGGM_OK;
     }
 
     // Psi = Pt Pt^T / n (T), its double diagonal
-    void product_Psi() {
+    cggm_status product_Psi() {
         const int64_t n = z.n, q = z.q;
         const double inv = 1.0 / (double)n;
+        if (tc()) {
+            CGGM_TRY(gemm_tc_nt(q, q, n, (float)inv, P<float>(c->Pt_hi), n, P<float>(c->Pt_hi), n,
+                                0.0f, (float *)c->Psi.p, q, true, P<float>(c->Pt_lo),
+                                P<float>(c->Pt_lo), P<int>(c->tcerr), st));
+            note_launch();
+            rowsq_kernel<float><<<(unsigned)q, 256, 0, st>>>(q, n, P<float>(c->Pt_f), inv,
+                                                              P<double>(c->Pd));
+            return CGGM_OK;
+        }
         if (sizeof(T) == 8) {
             gemm<double>(false, true, q, q, n, inv, P<double>(c->Pt), n, P<double>(c->Pt), n, 0.0,
                          (double *)c->Psi.p, q, st);
@@ -289,6 +366,7 @@ struct Solver {
         }
         note_launch();
         rowsq_kernel<double><<<(unsigned)q, 256, 0, st>>>(q, n, P<double>(c->Pt), inv, P<double>(c->Pd));
+        return CGGM_OK;
     }
 
     // Theta-only pieces of f at the current Theta: 2 tr(S_xy^T Theta) and ||Theta||_1
@@ -378,17 +456,21 @@ struct Solver {
         for (it = 0; it < o.max_iter; it++) {
             cudaEventRecord(ev[0], st);
             // ---- products (R, P, Psi) and the gradients (Eq. 3) ----
-            products_R_P();
-            product_Psi();
+            CGGM_TRY(products_R_P());
+            CGGM_TRY(product_Psi());
             theta_pieces();
             double f_start = 0.0;
             CGGM_TRY(eval_f(c->Lam, c->Lch, S_LOGDET, &f_start));
             grad_lambda<T>(q, P<double>(c->Syy), P<double>(c->Sig), (const T *)c->Psi.p,
                            P<double>(c->GL), st);
             // G_Theta = 2 S_xy + (2/n) X^T P
-            axpby<double>(pq, 2.0, P<double>(c->Sxy), 0.0, P<double>(c->GT), st);
-            gemm<double>(false, true, p, q, n, 2.0 / (double)n, P<double>(c->Xt), n,
-                         P<double>(c->Pt), n, 1.0, P<double>(c->GT), q, st);
+            if (tc()) {
+                CGGM_TRY(tc_XtP(2.0 / (double)n, 2.0, P<double>(c->GT)));
+            } else {
+                axpby<double>(pq, 2.0, P<double>(c->Sxy), 0.0, P<double>(c->GT), st);
+                gemm<double>(false, true, p, q, n, 2.0 / (double)n, P<double>(c->Xt), n,
+                             P<double>(c->Pt), n, 1.0, P<double>(c->GT), q, st);
+            }
             cudaEventRecord(ev[1], st);
             // ---- stopping quantity (Section 5.1) and active sets (Section 2.2) ----
             double *s = scal();
@@ -483,11 +565,16 @@ struct Solver {
             sigma_from_factor();
             // ---- Theta pass (Section 3.2) with the new Sigma ----
             // W = S_xy + S_xx Theta Sigma = S_xy + (1/n) X^T (X Theta Sigma)
-            gemm<double>(false, false, q, n, q, 1.0, P<double>(c->Sig), q, P<double>(c->Rt), n,
-                         0.0, P<double>(c->Pt), n, st);
-            CGGM_CUDA_TRY(cudaMemcpyAsync(c->W.p, c->Sxy.p, 8 * pq, cudaMemcpyDeviceToDevice, st));
-            gemm<double>(false, true, p, q, n, 1.0 / (double)n, P<double>(c->Xt), n,
-                         P<double>(c->Pt), n, 1.0, P<double>(c->W), q, st);
+            if (tc()) {
+                CGGM_TRY(tc_P());
+                CGGM_TRY(tc_XtP(1.0 / (double)n, 1.0, P<double>(c->W)));
+            } else {
+                gemm<double>(false, false, q, n, q, 1.0, P<double>(c->Sig), q, P<double>(c->Rt), n,
+                             0.0, P<double>(c->Pt), n, st);
+                CGGM_CUDA_TRY(cudaMemcpyAsync(c->W.p, c->Sxy.p, 8 * pq, cudaMemcpyDeviceToDevice, st));
+                gemm<double>(false, true, p, q, n, 1.0 / (double)n, P<double>(c->Xt), n,
+                             P<double>(c->Pt), n, 1.0, P<double>(c->W), q, st);
+            }
             CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, sizeof(T) * pq, st));
             CGGM_TRY(theta_sweep<T>(p, q, (const T *)c->Sxx.p, P<double>(c->Xd), SigT(),
                                     P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), hc[1],
@@ -495,6 +582,7 @@ struct Solver {
                                     c->planT, c->scr, st));
             cudaEventRecord(ev[6], st);
             CGGM_TRY(sync_err(c));
+            CGGM_TRY(tc_check());
             {
                 float a, b, d2;
                 cudaEventElapsedTime(&a, ev[3], ev[4]);
@@ -615,7 +703,9 @@ void cggm_destroy(cggm_ctx *c) {
                    &c->Lch_a, &c->logd_a, &c->work, &c->Rt, &c->Pt, &c->Z, &c->Psi, &c->Pd,
                    &c->GL, &c->GT, &c->W, &c->D, &c->U, &c->dV, &c->li, &c->lj, &c->ti,
                    &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial,
-                   &c->tcA_hi, &c->tcA_lo, &c->tcB_hi, &c->tcB_lo};
+                   &c->tcA_hi, &c->tcA_lo, &c->tcB_hi, &c->tcB_lo, &c->Xt_hi, &c->Xt_lo,
+                   &c->Sig_hi, &c->Sig_lo, &c->R_f, &c->R_hi, &c->R_lo, &c->Pt_f, &c->Pt_hi,
+                   &c->Pt_lo, &c->Zf, &c->tcerr};
     for (Buf *b : bufs) if (b->p) cudaFree(b->p);
     plan_free(c->planL);
     plan_free(c->planT);
@@ -734,8 +824,8 @@ cggm_status cggm_grad(cggm_ctx *c, const void *X, int xdtype, const void *Y, int
     CGGM_TRY(load_double(c, Theta, pq, c->Th));
     CGGM_TRY(S.factor(c->Lam, c->Lch, c->logd, S_LOGDET));
     S.sigma_from_factor();
-    S.products_R_P();
-    S.product_Psi();
+    CGGM_TRY(S.products_R_P());
+    CGGM_TRY(S.product_Psi());
     grad_lambda<double>(q, P<double>(c->Syy), P<double>(c->Sig), P<double>(c->Psi),
                         P<double>(c->GL), c->st);
     axpby<double>(pq, 2.0, P<double>(c->Sxy), 0.0, P<double>(c->GT), c->st);

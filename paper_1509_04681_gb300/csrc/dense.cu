@@ -130,6 +130,12 @@ __global__ void axpby_kernel(int64_t len, T a, const T *x, T b, T *y) {
          i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a * x[i] + b * y[i];
 }
+__global__ void axpy_f2d_kernel(int64_t len, double a, const double *x, const float *z,
+                                double *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + (double)z[i];
+}
 __global__ void d2f_kernel(int64_t len, const double *x, float *y) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -185,6 +191,14 @@ void axpby(int64_t len, T a, const T *x, T b, T *y, cudaStream_t st) {
 }
 template void axpby<double>(int64_t, double, const double *, double, double *, cudaStream_t);
 template void axpby<float>(int64_t, float, const float *, float, float *, cudaStream_t);
+
+void axpy_f2d(int64_t len, double a, const double *x, const float *z, double *out,
+              cudaStream_t st) {
+    if (len > 0) {
+        note_launch();
+        axpy_f2d_kernel<<<grid_for(len), 256, 0, st>>>(len, a, x, z, out);
+    }
+}
 
 void convert_d2f(int64_t len, const double *x, float *y, cudaStream_t st) {
     if (len > 0) {

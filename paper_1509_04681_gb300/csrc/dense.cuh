@@ -22,6 +22,8 @@ template <typename T>
 void axpby(int64_t len, T a, const T *x, T b, T *y, cudaStream_t st);
 
 void convert_d2f(int64_t len, const double *x, float *y, cudaStream_t st);
+// out = a x + z  (x, out double; z float)
+void axpy_f2d(int64_t len, double a, const double *x, const float *z, double *out, cudaStream_t st);
 void convert_f2d(int64_t len, const float *x, double *y, cudaStream_t st);
 
 // out (cols x rows) = in^T (rows x cols), element type converted
