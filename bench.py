@@ -261,6 +261,51 @@ def run_profile_sweep(args):
                                         "d_abs_sum": float(np.abs(D).sum())}}))
 
 
+def run_serve(args):
+    """Served regularisation paths: requests of uneven size arriving as a Poisson process
+    (20 per second), each an 8-point lambda grid from 0.5 down to 0.02 solved with warm
+    starts, admitted by device-memory footprint into `slots` concurrent workers.  Prints
+    lambda-path solves per second over the makespan and p50 / p99 latency (arrival to the
+    last lambda point)."""
+    import numpy as np
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    import synth
+    scale = args.serve_scale
+    reqs = synth.serving_requests(n_req=args.serve_requests, rate_per_s=20.0, seed=0,
+                                  p_range=(int(500 / scale), int(8000 / scale)),
+                                  q_range=(int(200 / scale), int(4000 / scale)),
+                                  n_range=(int(200 / scale), int(1000 / scale)))
+    probs = [(r, r.problem()) for r in reqs]
+    with cg.Server(0, slots=args.serve_slots) as srv:
+        t0 = time.perf_counter()
+        ids = []
+        for r, pr in probs:
+            wait = r.arrival_s - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(srv.submit(pr.X.astype(np.float32), pr.Y.astype(np.float32), r.lambdas,
+                                  tol=0.01, max_iter=args.serve_max_iter,
+                                  precision=cg.CGGM_MIXED, want_outputs=False))
+        res = [srv.poll(i, wait=True) for i in ids]
+        makespan = time.perf_counter() - t0
+    lat = sorted(r["finish_s"] - r["arrival_s"] for r in res)
+    pts = sum(len(r.lambdas) for r, _ in probs)
+    line = {"metric": METRIC, "serving": {
+        "value": pts / makespan, "unit": "lambda-point solves/s",
+        "requests": len(res), "lambda_points": pts, "makespan_s": makespan,
+        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+        "slots": args.serve_slots, "statuses": sorted(set(r["status"] for r in res)),
+        "iterations": sum(r["iterations"] for r in res),
+        "workload": (f"{len(res)} requests, sizes log-uniform p in [{int(500/scale)}, "
+                     f"{int(8000/scale)}], q in [{int(200/scale)}, {int(4000/scale)}], n in "
+                     f"[{int(200/scale)}, {int(1000/scale)}]; 8-point grid 0.5 -> 0.02; Poisson "
+                     f"arrivals 20/s; tol 0.01, at most {args.serve_max_iter} iterations per point; "
+                     f"mixed precision")}}
+    print(json.dumps(line), flush=True)
+
+
 def run_cuda(args):
     import numpy as np
     import torch
@@ -392,11 +437,20 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="served lambda paths (Poisson arrivals) instead of the default line")
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-scale", type=float, default=4.0,
+                    help="divide the request size ranges by this factor")
+    ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-max-iter", type=int, default=100)
     ap.add_argument("--profile-sweep", action="store_true",
                     help="run only a bounded Lambda pass at q=5000 (for ncu captures)")
     args = ap.parse_args()
     if args.profile_sweep:
         run_profile_sweep(args)
+    elif args.serve:
+        run_serve(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

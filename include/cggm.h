@@ -185,6 +185,60 @@ cggm_status cggm_active_sets(cggm_ctx *ctx, int64_t p, int64_t q, const double *
                              int penalize_diag, int32_t *li, int32_t *lj, int64_t *m_lambda,
                              int32_t *ti, int32_t *tj, int64_t *m_theta);
 
+/*
+ * Regularisation-path server (not in the paper: a serving layer over Algorithm 1).
+ * Requests arrive at any time through cggm_server_submit; each carries X (n x p), Y (n x q)
+ * in host or device memory (kept alive by the caller until the request is done) and a grid
+ * of lambda values solved in order with lam_Lambda = lam_Theta = lambdas[k], every solve
+ * warm-started from the previous one with Lambda and Theta kept in device memory.  A request
+ * is admitted when one of `slots` worker contexts is free and its device footprint
+ * (cggm_footprint) fits the budget (the oldest request that fits goes first; a request larger
+ * than the whole budget runs alone).  Admitted requests run concurrently, each on its own
+ * stream, so their kernels overlap on the GPU; the results of a request do not depend on the
+ * others (every kernel reduces in a fixed order).  Times are seconds on the server's clock
+ * (steady clock from cggm_server_create).
+ */
+typedef struct cggm_server cggm_server;
+
+typedef struct {
+    const void *X;        /* n x p, row-major, host or device                            */
+    int xdtype;           /* cggm_dtype                                                  */
+    const void *Y;        /* n x q                                                       */
+    int ydtype;
+    int64_t n, p, q;
+    int n_lambda;         /* points of the path (> 0)                                    */
+    const double *lambdas;/* host, n_lambda values >= 0, copied at submission           */
+    double tol;           /* stopping ratio of Section 5.1 for every point               */
+    int max_iter;         /* per point; <= 0: default                                    */
+    int precision;        /* cggm_precision                                              */
+    double *Lambda_out;   /* host or device, n_lambda x q x q, or NULL                   */
+    double *Theta_out;    /* host or device, n_lambda x p x q, or NULL                   */
+} cggm_request;
+
+typedef struct {
+    int done;             /* 1 once the request has finished (or was cancelled)          */
+    int status;           /* CGGM_OK, or the first error of the path                     */
+    double arrival_s;     /* submission time                                             */
+    double start_s;       /* admission time                                              */
+    double finish_s;      /* completion time                                             */
+    int iterations;       /* Newton iterations summed over the path                      */
+    double f_last;        /* objective at the last point                                 */
+    int64_t footprint;    /* device bytes accounted to the request                       */
+} cggm_result;
+
+/* Start `slots` worker threads on `device`; hbm_budget_bytes <= 0 means 80 % of the free
+ * device memory at creation. */
+cggm_status cggm_server_create(cggm_server **srv, int device, int slots, int64_t hbm_budget_bytes);
+/* Queue a request; *id identifies it for cggm_server_poll. */
+cggm_status cggm_server_submit(cggm_server *srv, const cggm_request *req, uint64_t *id);
+/* Copy the request's state into *out; with wait != 0 block until it is done. */
+cggm_status cggm_server_poll(cggm_server *srv, uint64_t id, int wait, cggm_result *out);
+/* Cancel requests not yet admitted, wait for the running ones, release everything. */
+void cggm_server_destroy(cggm_server *srv);
+/* Device bytes a request of this size is accounted for (workspace of cggm_solve plus the
+ * request's own device copies); -1 for invalid sizes. */
+int64_t cggm_footprint(int64_t n, int64_t p, int64_t q, int precision);
+
 /* Dense contraction on the tensor cores, the form every product from X takes in the mixed
  * path (R = X Theta, P = R Sigma, Psi = P^T P / n, X^T (Y + P); Section 2.3 lists them):
  *     C = alpha A B^T + beta C,

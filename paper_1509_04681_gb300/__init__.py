@@ -5,6 +5,8 @@ The compute path is the CUDA library ``libcggm.so`` (C ABI in include/cggm.h); t
 package is its Python binding.  Build it with ``paper_1509_04681_gb300.build.build()``.
 """
 from .cggm import (  # noqa: F401
+    Server,
+    footprint,
     Context,
     CGGMError,
     cggm_opts,

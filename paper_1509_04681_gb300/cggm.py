@@ -27,7 +27,8 @@ CGGM_F32, CGGM_F64 = 0, 1
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
-    "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract",
+    "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
+    "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
 ]
 
 
@@ -49,6 +50,25 @@ class cggm_info(ctypes.Structure):
                 ("sec_linesearch", ctypes.c_double), ("sec_sweep_theta", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("coords_lambda", ctypes.c_int64),
                 ("coords_theta", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cggm_request(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("xdtype", ctypes.c_int), ("Y", ctypes.c_void_p),
+                ("ydtype", ctypes.c_int), ("n", ctypes.c_int64), ("p", ctypes.c_int64),
+                ("q", ctypes.c_int64), ("n_lambda", ctypes.c_int),
+                ("lambdas", ctypes.POINTER(ctypes.c_double)), ("tol", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("Lambda_out", ctypes.c_void_p), ("Theta_out", ctypes.c_void_p)]
+
+
+class cggm_result(ctypes.Structure):
+    _fields_ = [("done", ctypes.c_int), ("status", ctypes.c_int), ("arrival_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double),
+                ("iterations", ctypes.c_int), ("f_last", ctypes.c_double),
+                ("footprint", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -89,6 +109,14 @@ def _lib():
                                          ctypes.POINTER(i64), vp, vp, ctypes.POINTER(i64)]
         lib.cggm_contract.argtypes = [vp, i64, i64, i64, ctypes.c_float, vp, i64, vp, i64,
                                       ctypes.c_float, vp, i64, ip]
+        lib.cggm_server_create.argtypes = [ctypes.POINTER(vp), ip, ip, i64]
+        lib.cggm_server_submit.argtypes = [vp, ctypes.POINTER(cggm_request),
+                                           ctypes.POINTER(ctypes.c_uint64)]
+        lib.cggm_server_poll.argtypes = [vp, ctypes.c_uint64, ip, ctypes.POINTER(cggm_result)]
+        lib.cggm_server_destroy.argtypes = [vp]
+        lib.cggm_server_destroy.restype = None
+        lib.cggm_footprint.argtypes = [i64, i64, i64, ip]
+        lib.cggm_footprint.restype = i64
         lib.cggm_lambda_sweep_noalloc.argtypes = [i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp,
                                                   vp]
         for name in EXPORTED:
@@ -98,7 +126,8 @@ def _lib():
                                                      "cggm_lambda_sweep", "cggm_theta_sweep",
                                                      "cggm_active_sets",
                                                      "cggm_lambda_sweep_noalloc",
-                                                     "cggm_contract"):
+                                                     "cggm_contract", "cggm_server_create",
+                                                     "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -305,3 +334,68 @@ def make_opts(**kw) -> cggm_opts:
             v = -math.inf
         setattr(o, k, v)
     return o
+
+
+class Server:
+    """Regularisation-path server (cggm_server_*): submit requests as they arrive, poll
+    for results.  Keeps every submitted request's arrays alive until it is done."""
+
+    def __init__(self, device: int = 0, slots: int = 4, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib().cggm_server_create(ctypes.byref(h), int(device), int(slots),
+                                         int(hbm_budget_bytes)), "cggm_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, X, Y, lambdas, tol=0.01, max_iter=0, precision=CGGM_MIXED,
+               want_outputs=True):
+        n, p = X.shape
+        q = Y.shape[1]
+        xd, xt = _x_dtype(X)
+        yd, yt = _x_dtype(Y)
+        Xa, Ya = _Arr(X, xd), _Arr(Y, yd)
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        Lo = np.empty((len(lam), q, q)) if want_outputs else None
+        To = np.empty((len(lam), p, q)) if want_outputs else None
+        r = cggm_request(X=Xa.ptr, xdtype=xt, Y=Ya.ptr, ydtype=yt, n=n, p=p, q=q,
+                         n_lambda=len(lam), lambdas=lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                         tol=float(tol), max_iter=int(max_iter), precision=int(precision),
+                         Lambda_out=Lo.ctypes.data if Lo is not None else None,
+                         Theta_out=To.ctypes.data if To is not None else None)
+        rid = ctypes.c_uint64()
+        _check(_lib().cggm_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)),
+               "cggm_server_submit")
+        self._keep[rid.value] = (Xa, Ya, lam, Lo, To)
+        return rid.value
+
+    def poll(self, rid, wait=False):
+        out = cggm_result()
+        _check(_lib().cggm_server_poll(self._h, ctypes.c_uint64(rid), int(bool(wait)),
+                                       ctypes.byref(out)), "cggm_server_poll")
+        d = out.as_dict()
+        if d["done"]:
+            _, _, _, Lo, To = self._keep[rid]
+            d["Lambda"], d["Theta"] = Lo, To
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().cggm_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def footprint(n, p, q, precision=CGGM_MIXED) -> int:
+    return int(_lib().cggm_footprint(n, p, q, precision))
+

@@ -22,6 +22,7 @@
 #include "sweeps.cuh"
 
 #include <cooperative_groups.h>
+#include <mutex>
 
 namespace cggm {
 
@@ -621,6 +622,15 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
     }
 }
 
+// A persistent pass needs every SM at once; two of them issued from different host threads
+// (concurrent solves) could each hold part of the GPU while waiting at a grid barrier for
+// the rest.  One process-wide lock covers a pass from its launch to its completion check, so
+// passes of concurrent solves run one after another while other kernels still overlap.
+std::mutex &coop_mutex() {
+    static std::mutex m;
+    return m;
+}
+
 template <typename T>
 cggm_status launch_coop(const void *fn, void **args, size_t smem, cudaStream_t st) {
     CGGM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -722,6 +732,7 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
         case 256: fn = (const void *)lambda_sweep_kernel<T, 8>; break;
         default: return CGGM_EINVAL;
     }
+    std::lock_guard<std::mutex> lock(coop_mutex());
     CGGM_TRY(launch_coop<T>(fn, args, smem, st));
     return read_err(scr.err, st);
 }
@@ -748,6 +759,7 @@ cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const do
     const void *fn = B == 32 ? (const void *)lambda_sweep_kernel<double, 1>
                    : B == 64 ? (const void *)lambda_sweep_kernel<double, 2>
                              : (const void *)lambda_sweep_kernel<double, 4>;
+    std::lock_guard<std::mutex> lock(coop_mutex());
     CGGM_TRY(launch_coop<double>(fn, args, smem, st));
     return read_err(scr.err, st);
 }
@@ -776,6 +788,7 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
         case 256: fn = (const void *)theta_sweep_kernel<T, 8>; break;
         default: return CGGM_EINVAL;
     }
+    std::lock_guard<std::mutex> lock(coop_mutex());
     CGGM_TRY(launch_coop<T>(fn, args, smem, st));
     return read_err(scr.err, st);
 }
