@@ -123,14 +123,26 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x, world):
+def max_over_ranks(x, world, device="cuda"):
+    """Largest value over the ranks (the slowest rank's time decides the job's rate)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(rank):
+    """Each rank solves an independent replica of the workload: the seed is the rank."""
+    return rank
+
+
+def job_rate(iters_per_rank, sec_max, world):
+    """Whole-job Newton iterations per second: every rank runs the same number of
+    iterations on its replica; the job takes as long as its slowest rank."""
+    return world * iters_per_rank / sec_max
 
 
 def cpu_oracle_rate(pr, budget_s=25.0):
@@ -317,7 +329,7 @@ def run_cuda(args):
     pkg_build.build()
     import synth
 
-    pr = synth.workload(WORKLOAD, seed=rank)  # independent replica per rank
+    pr = synth.workload(WORKLOAD, seed=replica_seed(rank))  # independent replica per rank
     n, p = pr.X.shape
     q = pr.Y.shape[1]
     Xd = torch.tensor(pr.X, device=dev, dtype=torch.float64)
@@ -353,7 +365,7 @@ def run_cuda(args):
     sec_max = max_over_ranks(sec, world)
     info = res.info
     iters = info["iterations"]
-    value = world * iters / sec_max
+    value = job_rate(iters, sec_max, world)
     clocks = clk.summary()
 
     # roofline of the dominant kernel: the coordinate pass with the larger time
