@@ -71,7 +71,6 @@ struct cggm_ctx {
     // mixed path: float operands of the tensor-core products and their TF32 hi/lo splits
     Buf Xt_hi, Xt_lo, Sig_hi, Sig_lo, R_f, R_hi, R_lo, Pt_f, Pt_hi, Pt_lo, Zf, tcerr;
     Buf partial;
-    BatchPlan planL, planT;
     SweepScratch scr;
     cudaEvent_t ev[8];
     bool events = false;
@@ -521,7 +520,7 @@ struct Solver {
             CGGM_TRY(lambda_sweep<T>(q, SigT(), (const T *)c->Psi.p, P<double>(c->Sd),
                                      P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), hc[0],
                                      P<int32_t>(c->li), P<int32_t>(c->lj), lamL, lamLd,
-                                     P<double>(c->D), (T *)c->U.p, B, c->planL, c->scr, st));
+                                     P<double>(c->D), (T *)c->U.p, B, c->scr, st));
             cudaEventRecord(ev[4], st);
             // ---- Armijo (Algorithm 1) ----
             // delta = tr(G D) + lamL (||Lam + D||_1 - ||Lam||_1)
@@ -579,7 +578,7 @@ struct Solver {
             CGGM_TRY(theta_sweep<T>(p, q, (const T *)c->Sxx.p, P<double>(c->Xd), SigT(),
                                     P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), hc[1],
                                     P<int32_t>(c->ti), P<int32_t>(c->tj), lamT, (T *)c->dV.p, B,
-                                    c->planT, c->scr, st));
+                                    c->scr, st));
             cudaEventRecord(ev[6], st);
             CGGM_TRY(sync_err(c));
             CGGM_TRY(tc_check());
@@ -707,8 +706,6 @@ void cggm_destroy(cggm_ctx *c) {
                    &c->Sig_hi, &c->Sig_lo, &c->R_f, &c->R_hi, &c->R_lo, &c->Pt_f, &c->Pt_hi,
                    &c->Pt_lo, &c->Zf, &c->tcerr};
     for (Buf *b : bufs) if (b->p) cudaFree(b->p);
-    plan_free(c->planL);
-    plan_free(c->planT);
     scratch_free(c->scr);
     if (c->events) for (int i = 0; i < 8; i++) cudaEventDestroy(c->ev[i]);
     if (c->own_stream) cudaStreamDestroy(c->st);
@@ -905,7 +902,7 @@ cggm_status cggm_lambda_sweep(cggm_ctx *c, int64_t q, const double *Sigma, const
         CGGM_TRY(lambda_sweep<double>(q, P<double>(c->Sig), P<double>(c->work), P<double>(c->Sd),
                                       P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), m,
                                       P<int32_t>(c->li), P<int32_t>(c->lj), lam_L, lamd,
-                                      P<double>(c->D), P<double>(c->U), 128, c->planL, c->scr, c->st));
+                                      P<double>(c->D), P<double>(c->U), 128, c->scr, c->st));
     } else {
         CGGM_TRY(ensure(c->U, 4 * qq));
         CGGM_TRY(ensure(c->Sig_f, 4 * qq));
@@ -916,7 +913,7 @@ cggm_status cggm_lambda_sweep(cggm_ctx *c, int64_t q, const double *Sigma, const
         CGGM_TRY(lambda_sweep<float>(q, P<float>(c->Sig_f), P<float>(c->Psi), P<double>(c->Sd),
                                      P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), m,
                                      P<int32_t>(c->li), P<int32_t>(c->lj), lam_L, lamd,
-                                     P<double>(c->D), P<float>(c->U), 256, c->planL, c->scr, c->st));
+                                     P<double>(c->D), P<float>(c->U), 256, c->scr, c->st));
     }
     CGGM_TRY(store_double(c, D_out, c->D.p, qq));
     return sync_err(c);
@@ -961,7 +958,7 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
         CGGM_TRY(theta_sweep<double>(p, q, P<double>(c->Sxx), P<double>(c->Xd), P<double>(c->Sig),
                                      P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
                                      P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<double>(c->dV),
-                                     128, c->planT, c->scr, c->st));
+                                     128, c->scr, c->st));
     } else {
         CGGM_TRY(ensure(c->Xt_f, 4 * (size_t)p * n));
         CGGM_TRY(ensure(c->Sig_f, 4 * qq));
@@ -974,7 +971,7 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
         CGGM_TRY(theta_sweep<float>(p, q, P<float>(c->Sxx), P<double>(c->Xd), P<float>(c->Sig_f),
                                     P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
                                     P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<float>(c->dV),
-                                    256, c->planT, c->scr, c->st));
+                                    256, c->scr, c->st));
     }
     CGGM_TRY(store_double(c, Theta_out, c->Th.p, pq));
     return sync_err(c);

@@ -13,30 +13,19 @@ namespace {
 
 constexpr int64_t kMaxQ = CGGM_NOALLOC_MAX_Q;
 constexpr int kBatch = 64;
-constexpr int64_t kMaxCoords = kMaxQ * (kMaxQ + 1) / 2;
-constexpr int64_t kMaxBatches = (kMaxCoords + kBatch - 1) / kBatch;
-constexpr int kK = 2 * kBatch;
-
 // Byte offsets of the regions inside the array (each 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t OFF_G = 0;                                                   // q x q double
 constexpr size_t OFF_U = align256(OFF_G + 8 * kMaxQ * kMaxQ);                 // q x q double
 constexpr size_t OFF_SD = align256(OFF_U + 8 * kMaxQ * kMaxQ);                // q double
 constexpr size_t OFF_PD = align256(OFF_SD + 8 * kMaxQ);                       // q double
-constexpr size_t OFF_NIDX = align256(OFF_PD + 8 * kMaxQ);                     // batches int
-constexpr size_t OFF_NIDX2 = align256(OFF_NIDX + 4 * kMaxBatches);
-constexpr size_t OFF_IDX = align256(OFF_NIDX2 + 4 * kMaxBatches);             // batches x K
-constexpr size_t OFF_IDX2 = align256(OFF_IDX + 4 * kMaxBatches * kK);
-constexpr size_t OFF_PA = align256(OFF_IDX2 + 4 * kMaxBatches * kK);          // batches x B
-constexpr size_t OFF_PB = align256(OFF_PA + 4 * kMaxBatches * kBatch);
-constexpr size_t OFF_LPTR = align256(OFF_PB + 4 * kMaxBatches * kBatch);      // batches x (K+1)
-constexpr size_t OFF_LENT = align256(OFF_LPTR + 4 * kMaxBatches * (kK + 1));  // batches x K
-constexpr size_t OFF_MU = align256(OFF_LENT + 4 * kMaxBatches * kK);          // B double
+constexpr size_t OFF_MU = align256(OFF_PD + 8 * kMaxQ);                       // B double
 constexpr size_t OFF_SUB1 = align256(OFF_MU + 8 * kBatch);                    // step constants
-constexpr size_t OFF_SUB2 = align256(OFF_SUB1 + 16 * 1024);                   // coefficients
-constexpr size_t OFF_BAR = align256(OFF_SUB2 + 8 * kBatch * kBatch + 1024);   // barrier
-constexpr size_t OFF_TICKET = align256(OFF_BAR + sizeof(GridBarrier));
-constexpr size_t OFF_ERR = align256(OFF_TICKET + sizeof(unsigned));
+constexpr size_t kSub1 = scratch_sub1_bytes(kBatch, sizeof(double));
+constexpr size_t OFF_SUB2 = align256(OFF_SUB1 + kSub1);                       // coefficients
+constexpr size_t kSub2 = scratch_sub2_bytes(kBatch, sizeof(double));
+constexpr size_t OFF_BAR = align256(OFF_SUB2 + kSub2);                        // barrier
+constexpr size_t OFF_ERR = align256(OFF_BAR + sizeof(GridBarrier));
 constexpr size_t kBytes = align256(OFF_ERR + sizeof(int));
 static_assert(kBytes <= (size_t)CGGM_NOALLOC_SCRATCH_BYTES, "scratch layout exceeds its size");
 
@@ -101,28 +90,15 @@ extern "C" cggm_status cggm_lambda_sweep_noalloc(int64_t q, const double *Sigma,
     double *U = reinterpret_cast<double *>(base + OFF_U);
     double *Sd = reinterpret_cast<double *>(base + OFF_SD);
     double *Pd = reinterpret_cast<double *>(base + OFF_PD);
-    BatchPlan plan;
-    plan.B = kBatch;
-    plan.K = kK;
-    plan.cap = kMaxBatches;
-    plan.nidx = reinterpret_cast<int32_t *>(base + OFF_NIDX);
-    plan.nidx2 = reinterpret_cast<int32_t *>(base + OFF_NIDX2);
-    plan.idx = reinterpret_cast<int32_t *>(base + OFF_IDX);
-    plan.idx2 = reinterpret_cast<int32_t *>(base + OFF_IDX2);
-    plan.pa = reinterpret_cast<int32_t *>(base + OFF_PA);
-    plan.pb = reinterpret_cast<int32_t *>(base + OFF_PB);
-    plan.lptr = reinterpret_cast<int32_t *>(base + OFF_LPTR);
-    plan.lent = reinterpret_cast<int32_t *>(base + OFF_LENT);
     SweepScratch scr;
     scr.mu = reinterpret_cast<double *>(base + OFF_MU);
     scr.sub1 = base + OFF_SUB1;
     scr.sub2 = base + OFF_SUB2;
     scr.bar = reinterpret_cast<GridBarrier *>(base + OFF_BAR);
-    scr.ticket = reinterpret_cast<unsigned *>(base + OFF_TICKET);
     scr.err = reinterpret_cast<int *>(base + OFF_ERR);
 
     // What must start at zero: the direction and the cache U = D Sigma.  The gradient,
-    // the diagonals and the batch plan are rewritten in full below.
+    // and the diagonals are rewritten in full below.
     const size_t qq = (size_t)q * q;
     CGGM_CUDA_TRY(cudaMemsetAsync(D_out, 0, 8 * qq, st));
     CGGM_CUDA_TRY(cudaMemsetAsync(U, 0, 8 * qq, st));
@@ -132,5 +108,5 @@ extern "C" cggm_status cggm_lambda_sweep_noalloc(int64_t q, const double *Sigma,
     CGGM_CUDA_TRY(cudaGetLastError());
     const double lamd = penalize_diag ? lam_L : 0.0;
     return lambda_sweep_preplanned_f64(q, Sigma, Psi, Sd, Pd, G, Lambda, m, ai, aj, lam_L,
-                                       lamd, D_out, U, kBatch, plan, scr, st);
+                                       lamd, D_out, U, kBatch, scr, st);
 }

@@ -6,19 +6,22 @@
 // Delta Theta Sigma for Theta, Section 3.2).  The GPU form keeps that order and that
 // arithmetic exactly, up to the order of floating-point sums, by cutting the list into
 // batches of B consecutive coordinates:
-//   phase A (all CTAs): for every coordinate of the batch, the dot products against the
-//           cache as it stands at the start of the batch; the cache is read row by row
-//           (row t at the batch's column indices), so each CTA owns a band of rows and
-//           produces partial sums.  The same phase gathers the small submatrices of
-//           Sigma / Psi / S_xx on the batch's indices.
-//   phase B (the last CTA to finish A): sums the partials in a fixed order, then one
-//           warp runs the B coordinate steps in order.  A step's dot products differ
+//   phase A: for every coordinate of the batch, its dot products against the cache as
+//           it stands at the start of the batch, two coordinates per CTA, and from them
+//           the step constants; also the coefficients by which each step of the batch
+//           changes the dot products of the later ones (entries of Sigma, Psi, S_xx).
+//   phase B (one warp of CTA 0): the B steps in order.  A step's dot products differ
 //           from their batch-start values only by the updates of the earlier steps of
-//           the same batch, and those corrections are bilinear in entries of the
-//           gathered submatrices, so the warp applies them exactly (forward
-//           substitution with a soft-threshold at every step).
+//           the same batch, and those corrections are bilinear in the coefficients, so
+//           the warp applies them exactly (forward substitution with a soft-threshold
+//           at every step).
 //   phase C (all CTAs): applies the batch's B updates to the cache rows.
-// A grid barrier separates C from the next batch's A, and B from C.
+// Phase A of batch k+1 runs on CTAs 1.. while CTA 0 runs phase B of batch k; the cache it
+// reads then lacks batch k's update, and the missing part of each dot product is
+// sum_l X(k+1, k)[., l] mu_l over batch k's steps mu, with coefficients X of the same form
+// as the in-batch ones.  Phase C forms that sum once mu is known, and phase B of batch k+1
+// starts its correction sums from it.  Grid barriers separate B from C and C from the
+// next B.
 #include "sweeps.cuh"
 
 #include <cooperative_groups.h>
@@ -40,6 +43,7 @@ __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, 
 // With acc = the in-batch correction sum, w = u - acc/a and the step is vp - acc/a
 // (w > r), vm - acc/a (w < -r), -c otherwise (zero curvature: always -c).
 enum { PRE_UH, PRE_UL, PRE_VPH, PRE_VPL, PRE_VMH, PRE_VML, PRE_AI, PRE_R, PRE_MC, PRE_N };
+static_assert(PRE_N == kStepConstants, "step constant count");
 
 template <typename T>
 __device__ __forceinline__ void split(double v, T *hi, T *lo) {
@@ -81,12 +85,11 @@ __device__ __forceinline__ void decode_pair(int e, int &l, int &l1) {
 // of the warp read consecutive words.
 __host__ __device__ __forceinline__ int colbase(int l, int B) { return l * (2 * B - l - 1) / 2; }
 // shared-memory slots for the coefficients (16-byte multiple with copy slack)
-__host__ __device__ __forceinline__ int coef_slots(int B) { return ((B * (B - 1) / 2 + 8) + 3) & ~3; }
 
 
 struct SmemLayout {
-    size_t meta;  // sa[B], sb[B] (batch coordinates), sseg[B + 1] (segment starts), nseg (ints)
-    size_t work;  // union: phase B coef[coef_slots(B)] + step constants [PRE_N][B] (T);
+    size_t meta;  // twice (current and next batch): sa[B], sb[B], sseg[B + 1], nseg (ints)
+    size_t work;  // union: phase B coef[coef_slots(B)], step constants [PRE_N][B], corr[B] (T);
                   //        phase C mu[B] (T)
     size_t total;
 };
@@ -95,10 +98,10 @@ template <typename T>
 __host__ __device__ inline SmemLayout smem_layout(int B) {
     SmemLayout s;
     s.meta = 0;
-    size_t off = (size_t)(2 * B + (B + 1) + 1) * sizeof(int32_t);
+    size_t off = (size_t)2 * (3 * B + 2) * sizeof(int32_t);  // two batches' metadata
     off = (off + 15) & ~size_t(15);
     s.work = off;
-    const size_t phb = ((size_t)coef_slots(B) + PRE_N * B + 8) * sizeof(T);
+    const size_t phb = ((size_t)coef_slots(B) + PRE_N * B + B + 8) * sizeof(T);
     const size_t phc = (size_t)(B + 4) * sizeof(T);
     s.total = off + (phb > phc ? phb : phc);
     return s;
@@ -113,14 +116,14 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
 // so the dependent chain per coordinate is a few T operations and one warp shuffle.
 template <typename T, int NS>
 __device__ void forward_substitution(int nb, int B, const T *__restrict__ pre,
-                                     const T *coef, double *mu_out, int *err) {
+                                     const T *acc0, const T *coef, double *mu_out, int *err) {
     // pre[] holds, for padding coordinates l >= nb, constants that give mu = 0 whatever
     // the correction sum (ai = 0, u = 0, r = 1, mc = 0), so panels run all 32 steps
     // without branches.
     const int lane = threadIdx.x & 31;
-    T acc[NS];
+    T acc[NS];  // correction sums, starting from the corrections carried from the previous batch
 #pragma unroll
-    for (int s = 0; s < NS; s++) acc[s] = T(0);
+    for (int s = 0; s < NS; s++) acc[s] = acc0[s * 32 + lane];
     bool bad = false;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
@@ -163,23 +166,6 @@ __device__ void forward_substitution(int nb, int B, const T *__restrict__ pre,
     if (bad) set_err(err, DEV_NONFINITE);
 }
 
-// Ticket: returns true in the last CTA to arrive (all CTAs' prior global writes visible).
-__device__ __forceinline__ bool last_cta(unsigned *ticket, unsigned nblocks) {
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned t = atomicAdd(ticket, 1u);
-        s_last = (t == nblocks - 1);
-        if (s_last) {
-            *ticket = 0;
-            __threadfence();
-        }
-    }
-    __syncthreads();
-    return s_last != 0;
-}
-
 // Copy n elements global -> shared (both 16-byte aligned, n rounded up to 16 bytes; the
 // buffers have that slack) with 16-byte loads, eight in flight per thread.
 template <typename T>
@@ -205,11 +191,13 @@ __device__ void copy_to_smem(const T *g, T *sm, int n) {
 // Phase B body shared by both passes: stage the coefficients and step constants, run
 // the substitution.
 template <typename T, int NS>
-__device__ void phase_b(int nb, int B, const T *gcoef, const T *gpre, T *scoef, T *spre,
-                        double *mu, int *err) {
+__device__ void phase_b(int nb, int B, const T *gcoef, const T *gpre, const T *gcorr, T *scoef,
+                        T *spre, double *mu, int *err) {
     const int ncoef = colbase(nb - 1, B) + 1;  // through column nb - 2 (all entries used)
+    T *scorr = spre + PRE_N * B;
     copy_to_smem<T>(gcoef, scoef, ncoef);
     copy_to_smem<T>(gpre, spre, PRE_N * B);
+    for (int l = threadIdx.x; l < B; l += blockDim.x) scorr[l] = (l < nb) ? __ldcg(gcorr + l) : T(0);
     __syncthreads();
     for (int l = nb + threadIdx.x; l < B; l += blockDim.x) {  // padding: mu = 0
         for (int k = 0; k < PRE_N; k++) spre[k * B + l] = T(0);
@@ -218,7 +206,7 @@ __device__ void phase_b(int nb, int B, const T *gcoef, const T *gpre, T *scoef, 
     const int nc = colbase(nb - 1, B) + 1, ncb = B * (B - 1) / 2;
     for (int e = nc + threadIdx.x; e < ncb; e += blockDim.x) scoef[e] = T(0);
     __syncthreads();
-    if ((threadIdx.x >> 5) == 0) forward_substitution<T, NS>(nb, B, spre, scoef, mu, err);
+    if ((threadIdx.x >> 5) == 0) forward_substitution<T, NS>(nb, B, spre, scorr, scoef, mu, err);
     __syncthreads();
 }
 
@@ -282,7 +270,39 @@ __device__ void load_batch(const int32_t *__restrict__ ai, const int32_t *__rest
 
 // ---------------------------------------------------------------------------------
 // Lambda sweep kernel.  Cache: Ut = U^T (q x q), Ut[r][t] = U[t][r] = (D Sigma)[t][r].
+//
+// Batches are pipelined one deep: while CTA 0 runs the steps of batch k (phase B), the
+// other CTAs compute the dot products of batch k+1 against the cache as it stands before
+// batch k's update, together with the coefficients X(k+1, k) that give the change of those
+// dot products per unit step of each coordinate of batch k.  After the barrier, phase C
+// applies batch k's update to the cache and forms corr(k+1) = X(k+1, k) mu(k), which
+// phase B of batch k+1 takes as the initial correction sums.  The result is the same
+// sequential pass, with phase A of one batch overlapping phase B of the previous one.
 // ---------------------------------------------------------------------------------
+struct BatchMeta {
+    int32_t *sa, *sb, *sseg, *snseg;
+};
+
+__device__ __forceinline__ BatchMeta meta_at(unsigned char *base, int B, int which) {
+    int32_t *p = reinterpret_cast<int32_t *>(base) + which * (3 * B + 2);
+    return BatchMeta{p, p + B, p + 2 * B, p + 3 * B + 1};
+}
+
+// corr[l] = sum_{l'} X[l][l'] mu[l'] for l < nbn (one warp per coordinate over the grid)
+template <typename T>
+__device__ void cross_corrections(int nbn, int nbk, int B, const T *X, const double *mu,
+                                  T *corr) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
+    for (int l = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); l < nbn; l += warps) {
+        T acc = T(0);
+        for (int l1 = lane; l1 < nbk; l1 += 32)
+            acc = fma(__ldcg(X + (size_t)l * B + l1), (T)__ldcg(mu + l1), acc);
+        acc = warp_sum(acc);
+        if (lane == 0) corr[l] = acc;
+    }
+}
+
 template <typename T, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
 lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
@@ -294,34 +314,50 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[(kThreads / 32) * 6];
     const SmemLayout L = smem_layout<T>(B);
-    int32_t *sa = reinterpret_cast<int32_t *>(smem + L.meta);
-    int32_t *sb = sa + B;
-    int32_t *sseg = sb + B;
-    int32_t *snseg = sseg + B + 1;
     unsigned char *work = smem + L.work;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned nblk = gridDim.x;
-    T *pre = reinterpret_cast<T *>(scr.sub1);    // [PRE_N][B]
-    T *gcoef = reinterpret_cast<T *>(scr.sub2);  // column-packed coefficients
+    T *preb = reinterpret_cast<T *>(scr.sub1);                // [2][PRE_N][B]
+    T *coefb = reinterpret_cast<T *>(scr.sub2);               // [2][coef_slots(B)]
+    T *gX = coefb + 2 * (size_t)coef_slots(B);                // [B][B]
+    T *gcorr = gX + (size_t)B * B;                            // [B]
     const int64_t rows_per = (q + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gthreads = (int64_t)nblk * blockDim.x;
     using VT = typename V16<T>::type;
     constexpr int VN = V16<T>::n;
     const bool vec = (q % VN) == 0;
+    const int64_t nbatch = (m + B - 1) / B;
+    if (nbatch == 0) return;
 
-    for (int64_t s = 0; s < m; s += B) {
-        const int nb = (int)((m - s) < B ? (m - s) : B);
-        load_batch(ai, aj, s, nb, sa, sb, sseg, snseg);
+    auto S = [&](int64_t x, int64_t y) -> T { return Sig[x * q + y]; };
+    auto P = [&](int64_t x, int64_t y) -> T { return Psi[x * q + y]; };
+    // change of the three dot products of coordinate (pi, pj) per unit step of (pa, pb)
+    auto coefficient = [&](int64_t pi, int64_t pj, int64_t pa, int64_t pb) -> T {
+        T c1, c2, c3;
+        if (pa != pb) {
+            c1 = S(pi, pa) * S(pb, pj) + S(pi, pb) * S(pa, pj);
+            c2 = P(pi, pa) * S(pb, pj) + P(pi, pb) * S(pa, pj);
+            c3 = P(pj, pa) * S(pb, pi) + P(pj, pb) * S(pa, pi);
+        } else {
+            c1 = S(pi, pa) * S(pa, pj);
+            c2 = P(pi, pa) * S(pa, pj);
+            c3 = P(pj, pa) * S(pa, pi);
+        }
+        return (pi != pj) ? (c1 + c2 + c3) : (c1 + T(2) * c2);
+    };
 
-        // ---- phase A: dot products and step constants, two coordinates per CTA ----
-        for (int l = blockIdx.x; l < nb; l += 2 * nblk) {
-            const int lb = l + (int)nblk;
+    // Phase A of the batch held in `bm` (nb coordinates) by the CTAs rank0 .. nblk-1:
+    // dot products against the cache, step constants -> pre, in-batch coefficients -> coef,
+    // and, when prev is given, the cross coefficients against the previous batch -> gX.
+    auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
+                       int nbp, int rank0) {
+        const int nA = (int)nblk - rank0, rank = (int)blockIdx.x - rank0;
+        for (int l = rank; l < nb; l += 2 * nA) {
+            const int lb = l + nA;
             const bool two = lb < nb;
-            const int64_t i0 = sa[l], j0 = sb[l];
-            const int64_t i1 = two ? sa[lb] : i0, j1 = two ? sb[lb] : j0;
+            const int64_t i0 = bm.sa[l], j0 = bm.sb[l];
+            const int64_t i1 = two ? bm.sa[lb] : i0, j1 = two ? bm.sb[lb] : j0;
             // (Sigma D Sigma)_ij = Sigma_i . U_{:,j}, (Psi D Sigma)_ij = Psi_i . U_{:,j},
             // (Psi D Sigma)_ji = Psi_j . U_{:,i}
             const T *x0 = Sig + i0 * q, *x1 = Psi + i0 * q, *x2 = Psi + j0 * q;
@@ -395,80 +431,89 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                 step_constants<T>(bb, a, Lam[i * q + j], lam, pre, B, lw);
             }
         }
-        {
-            // coefficient of the correction of coordinate l = (i, j) by the earlier step of
-            // l1 = (a, b):  (Sigma dD Sigma)_ij + (Psi dD Sigma)_ij + (Psi dD Sigma)_ji per unit
-            // step, dD = E_ab + E_ba (one term when a == b); doubled middle term on the diagonal
-            const int ncoef = nb * (nb - 1) / 2;
-            for (int64_t e = gtid; e < ncoef; e += gthreads) {
-                int l, l1;
-                decode_pair((int)e, l, l1);
-                const int64_t pi = sa[l], pj = sb[l];
-                const int64_t pa = sa[l1], pb = sb[l1];
-                auto S = [&](int64_t x, int64_t y) -> T { return Sig[x * q + y]; };
-                auto P = [&](int64_t x, int64_t y) -> T { return Psi[x * q + y]; };
-                T c1, c2, c3;
-                if (pa != pb) {
-                    c1 = S(pi, pa) * S(pb, pj) + S(pi, pb) * S(pa, pj);
-                    c2 = P(pi, pa) * S(pb, pj) + P(pi, pb) * S(pa, pj);
-                    c3 = P(pj, pa) * S(pb, pi) + P(pj, pb) * S(pa, pi);
-                } else {
-                    c1 = S(pi, pa) * S(pa, pj);
-                    c2 = P(pi, pa) * S(pa, pj);
-                    c3 = P(pj, pa) * S(pa, pi);
-                }
-                gcoef[colbase(l1, B) + (l - l1 - 1)] = (pi != pj) ? (c1 + c2 + c3) : (c1 + T(2) * c2);
+        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
+        const int64_t nt = (int64_t)nA * blockDim.x;
+        const int ncoef = nb * (nb - 1) / 2;
+        for (int64_t e = t0; e < ncoef; e += nt) {
+            int l, l1;
+            decode_pair((int)e, l, l1);
+            coef[colbase(l1, B) + (l - l1 - 1)] = coefficient(bm.sa[l], bm.sb[l], bm.sa[l1], bm.sb[l1]);
+        }
+        if (prev) {
+            const int64_t ncross = (int64_t)nb * nbp;
+            for (int64_t e = t0; e < ncross; e += nt) {
+                const int l = (int)(e / nbp), l1 = (int)(e % nbp);
+                gX[(size_t)l * B + l1] = coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
             }
         }
+    };
 
-        // ---- phase B: last CTA runs the coordinate steps in order ----
-        if (last_cta(scr.ticket, nblk)) {
-            phase_b<T, NS>(nb, B, gcoef, pre, reinterpret_cast<T *>(work),
+    // prologue: phase A of batch 0 by every CTA; no correction from an earlier batch
+    BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
+    int nbk = (int)(m < B ? m : B);
+    load_batch(ai, aj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
+    phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
+    if (blockIdx.x == 0)
+        for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
+    if (!grid_sync(scr.bar, scr.err, nblk)) return;
+
+    for (int64_t k = 0; k < nbatch; k++) {
+        const int64_t sk = k * B, sn = sk + B;
+        const int nbn = (int)(sn < m ? ((m - sn) < B ? (m - sn) : B) : 0);
+        T *pre_k = preb + (size_t)(k & 1) * PRE_N * B, *coef_k = coefb + (size_t)(k & 1) * coef_slots(B);
+        T *pre_n = preb + (size_t)((k + 1) & 1) * PRE_N * B;
+        T *coef_n = coefb + (size_t)((k + 1) & 1) * coef_slots(B);
+        if (nbn > 0) load_batch(ai, aj, sn, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
+
+        // ---- phase B of batch k on CTA 0, phase A of batch k+1 on the others ----
+        if (blockIdx.x == 0) {
+            phase_b<T, NS>(nbk, B, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
-            for (int l = threadIdx.x; l < nb; l += blockDim.x) {
-                const int64_t i = sa[l], j = sb[l];
+            for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
+                const int64_t i = cur.sa[l], j = cur.sb[l];
                 const double mu = scr.mu[l];
                 D[i * q + j] = mu;
                 if (i != j) D[j * q + i] = mu;
             }
+        } else if (nbn > 0) {
+            phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
-        // ---- phase C: rows t of this CTA's band, segment by segment ----
+        // ---- phase C: batch k's update on this CTA's rows; corrections for batch k+1 ----
         // coordinate (a, b) of a segment with row a: U_a += mu Sigma_b, U_b += mu Sigma_a
         // (b != a); transposed: Ut[t][a] += sum mu Sigma[t][b], Ut[t][b] += mu Sigma[t][a]
         {
             T *smu = reinterpret_cast<T *>(work);
-            for (int l = threadIdx.x; l < nb; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
+            for (int l = threadIdx.x; l < nbk; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
             __syncthreads();
-            const int nseg = *snseg;
+            const int nseg = *cur.snseg;
             for (int64_t t = r0 + warp; t < r1; t += (kThreads / 32)) {
                 const T *Sr = Sig + t * q;
                 T *Ur = Ut + t * q;
                 for (int g = 0; g < nseg; g++) {
-                    const int l0 = sseg[g], l1 = sseg[g + 1];
-                    const int64_t a = sa[l0];
-                    // issue every load of this lane first (up to NS coordinates per lane)
+                    const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
+                    const int64_t a = cur.sa[l0];
                     T sv[NS], uv[NS], mv[NS];
                     int64_t bv[NS];
                     const T sta = Sr[a];
 #pragma unroll
-                    for (int k = 0; k < NS; k++) {
-                        const int l = l0 + lane + 32 * k;
-                        bv[k] = -1;
+                    for (int kk = 0; kk < NS; kk++) {
+                        const int l = l0 + lane + 32 * kk;
+                        bv[kk] = -1;
                         if (l < l1) {
-                            bv[k] = sb[l];
-                            mv[k] = smu[l];
-                            sv[k] = Sr[bv[k]];
-                            uv[k] = (bv[k] != a) ? __ldcg(Ur + bv[k]) : T(0);
+                            bv[kk] = cur.sb[l];
+                            mv[kk] = smu[l];
+                            sv[kk] = Sr[bv[kk]];
+                            uv[kk] = (bv[kk] != a) ? __ldcg(Ur + bv[kk]) : T(0);
                         }
                     }
                     T dot = T(0);
 #pragma unroll
-                    for (int k = 0; k < NS; k++) {
-                        if (bv[k] >= 0) {
-                            dot = fma(mv[k], sv[k], dot);
-                            if (bv[k] != a) Ur[bv[k]] = uv[k] + mv[k] * sta;
+                    for (int kk = 0; kk < NS; kk++) {
+                        if (bv[kk] >= 0) {
+                            dot = fma(mv[kk], sv[kk], dot);
+                            if (bv[kk] != a) Ur[bv[kk]] = uv[kk] + mv[kk] * sta;
                         }
                     }
                     dot = warp_sum(dot);
@@ -477,13 +522,19 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                     __syncwarp();
                 }
             }
+            if (nbn > 0) cross_corrections<T>(nbn, nbk, B, gX, scr.mu, gcorr);
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
+        BatchMeta tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        nbk = nbn;
     }
 }
 
 // ---------------------------------------------------------------------------------
 // Theta sweep kernel.  Cache: dVt = (Delta V)^T (q x p), dVt[j][t] = (Delta Theta Sigma)[t][j].
+// Pipelined like the Lambda pass.
 // ---------------------------------------------------------------------------------
 template <typename T, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -495,35 +546,36 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[(kThreads / 32) * 2];
     const SmemLayout L = smem_layout<T>(B);
-    int32_t *sa = reinterpret_cast<int32_t *>(smem + L.meta);
-    int32_t *sb = sa + B;
-    int32_t *sseg = sb + B;
-    int32_t *snseg = sseg + B + 1;
     unsigned char *work = smem + L.work;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned nblk = gridDim.x;
-    T *pre = reinterpret_cast<T *>(scr.sub1);
-    T *gcoef = reinterpret_cast<T *>(scr.sub2);
+    T *preb = reinterpret_cast<T *>(scr.sub1);
+    T *coefb = reinterpret_cast<T *>(scr.sub2);
+    T *gX = coefb + 2 * (size_t)coef_slots(B);
+    T *gcorr = gX + (size_t)B * B;
     const int64_t rows_per = (q + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
-    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t gthreads = (int64_t)nblk * blockDim.x;
     using VT = typename V16<T>::type;
     constexpr int VN = V16<T>::n;
+    const int64_t nbatch = (m + B - 1) / B;
+    if (nbatch == 0) return;
 
-    for (int64_t s = 0; s < m; s += B) {
-        const int nb = (int)((m - s) < B ? (m - s) : B);
-        load_batch(ti, tj, s, nb, sa, sb, sseg, snseg);
-        // rows of Delta V that can be nonzero: those at or before the batch's first row
-        const int64_t tmax = (int64_t)sa[0] + 1;
+    // change of (S_xx Delta V)_ij per unit step of Theta_ab, times 2: 2 (S_xx)_{i a} Sigma_{b j}
+    auto coefficient = [&](int64_t i, int64_t j, int64_t a, int64_t b) -> T {
+        return T(2) * Sxx[i * p + a] * Sig[b * q + j];
+    };
 
-        // ---- phase A (two coordinates per CTA in one pass) ----
-        for (int l = blockIdx.x; l < nb; l += 2 * nblk) {
-            const int lb = l + (int)nblk;
+    auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
+                       int nbp, int rank0) {
+        const int nA = (int)nblk - rank0, rank = (int)blockIdx.x - rank0;
+        // rows of Delta V that can be nonzero: those at or before this batch's first row
+        const int64_t tmax = (int64_t)bm.sa[0] + 1;
+        for (int l = rank; l < nb; l += 2 * nA) {
+            const int lb = l + nA;
             const bool two = lb < nb;
-            const int64_t i0 = sa[l], j0 = sb[l];
-            const int64_t i1 = two ? sa[lb] : i0, j1 = two ? sb[lb] : j0;
+            const int64_t i0 = bm.sa[l], j0 = bm.sb[l];
+            const int64_t i1 = two ? bm.sa[lb] : i0, j1 = two ? bm.sb[lb] : j0;
             // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
             const T *x0 = Sxx + i0 * p, *y0 = dVt + j0 * p, *x1 = Sxx + i1 * p, *y1 = dVt + j1 * p;
             T a0 = T(0), a1 = T(0);
@@ -562,63 +614,90 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                                   __ldcg(Theta + i * q + j), lam, pre, B, lw);
             }
         }
-        {
-            // 2 (S_xx)_{i a} Sigma_{b j}: coordinate l = (i, j), earlier l1 = (a, b)
-            const int ncoef = nb * (nb - 1) / 2;
-            for (int64_t e = gtid; e < ncoef; e += gthreads) {
-                int l, l1;
-                decode_pair((int)e, l, l1);
-                const int64_t i = sa[l], j = sb[l];
-                const int64_t a = sa[l1], bq = sb[l1];
-                gcoef[colbase(l1, B) + (l - l1 - 1)] = T(2) * Sxx[i * p + a] * Sig[bq * q + j];
+        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
+        const int64_t nt = (int64_t)nA * blockDim.x;
+        const int ncoef = nb * (nb - 1) / 2;
+        for (int64_t e = t0; e < ncoef; e += nt) {
+            int l, l1;
+            decode_pair((int)e, l, l1);
+            coef[colbase(l1, B) + (l - l1 - 1)] = coefficient(bm.sa[l], bm.sb[l], bm.sa[l1], bm.sb[l1]);
+        }
+        if (prev) {
+            const int64_t ncross = (int64_t)nb * nbp;
+            for (int64_t e = t0; e < ncross; e += nt) {
+                const int l = (int)(e / nbp), l1 = (int)(e % nbp);
+                gX[(size_t)l * B + l1] = coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
             }
         }
+    };
 
-        // ---- phase B ----
-        if (last_cta(scr.ticket, nblk)) {
-            phase_b<T, NS>(nb, B, gcoef, pre, reinterpret_cast<T *>(work),
+    BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
+    int nbk = (int)(m < B ? m : B);
+    load_batch(ti, tj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
+    phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
+    if (blockIdx.x == 0)
+        for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
+    if (!grid_sync(scr.bar, scr.err, nblk)) return;
+
+    for (int64_t k = 0; k < nbatch; k++) {
+        const int64_t sk = k * B, sn = sk + B;
+        const int nbn = (int)(sn < m ? ((m - sn) < B ? (m - sn) : B) : 0);
+        T *pre_k = preb + (size_t)(k & 1) * PRE_N * B, *coef_k = coefb + (size_t)(k & 1) * coef_slots(B);
+        T *pre_n = preb + (size_t)((k + 1) & 1) * PRE_N * B;
+        T *coef_n = coefb + (size_t)((k + 1) & 1) * coef_slots(B);
+        if (nbn > 0) load_batch(ti, tj, sn, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
+
+        if (blockIdx.x == 0) {
+            phase_b<T, NS>(nbk, B, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
-            for (int l = threadIdx.x; l < nb; l += blockDim.x) {
-                const int64_t i = sa[l], j = sb[l];
+            for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
+                const int64_t i = cur.sa[l], j = cur.sb[l];
                 Theta[i * q + j] = __ldcg(Theta + i * q + j) + scr.mu[l];
             }
+        } else if (nbn > 0) {
+            phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
         // ---- phase C: dVt[t][i] += sum over the segment of row i of mu Sigma[t][j] ----
         {
             T *smu = reinterpret_cast<T *>(work);
-            for (int l = threadIdx.x; l < nb; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
+            for (int l = threadIdx.x; l < nbk; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
             __syncthreads();
-            const int nseg = *snseg;
+            const int nseg = *cur.snseg;
             for (int64_t t = r0 + warp; t < r1; t += (kThreads / 32)) {
                 const T *Sr = Sig + t * q;
                 T *Vr = dVt + t * p;
                 for (int g = 0; g < nseg; g++) {
-                    const int l0 = sseg[g], l1 = sseg[g + 1];
+                    const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
                     T sv[NS], mv[NS];
 #pragma unroll
-                    for (int k = 0; k < NS; k++) {
-                        const int l = l0 + lane + 32 * k;
-                        sv[k] = T(0);
-                        mv[k] = T(0);
+                    for (int kk = 0; kk < NS; kk++) {
+                        const int l = l0 + lane + 32 * kk;
+                        sv[kk] = T(0);
+                        mv[kk] = T(0);
                         if (l < l1) {
-                            mv[k] = smu[l];
-                            sv[k] = Sr[sb[l]];
+                            mv[kk] = smu[l];
+                            sv[kk] = Sr[cur.sb[l]];
                         }
                     }
                     T dot = T(0);
 #pragma unroll
-                    for (int k = 0; k < NS; k++) dot = fma(mv[k], sv[k], dot);
+                    for (int kk = 0; kk < NS; kk++) dot = fma(mv[kk], sv[kk], dot);
                     dot = warp_sum(dot);
                     if (lane == 0) {
-                        const int64_t i = sa[l0];
+                        const int64_t i = cur.sa[l0];
                         Vr[i] = __ldcg(Vr + i) + dot;
                     }
                 }
             }
+            if (nbn > 0) cross_corrections<T>(nbn, nbk, B, gX, scr.mu, gcorr);
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
+        BatchMeta tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        nbk = nbn;
     }
 }
 
@@ -636,6 +715,7 @@ cggm_status launch_coop(const void *fn, void **args, size_t smem, cudaStream_t s
     CGGM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
     const int grid = sweep_grid();
+    if (grid < 2) return CGGM_ECUDA;  // phase B runs beside phase A: needs two CTAs at least
     note_launch();
     CGGM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kThreads), args, smem, st));
     return CGGM_OK;
@@ -654,55 +734,22 @@ cggm_status read_err(int *err, cudaStream_t st) {
 
 int sweep_grid() { return sm_count(); }
 
-cggm_status plan_reserve(BatchPlan &plan, int B, int64_t nbatch, bool theta) {
-    const int K = 2 * B;
-    const bool grow = !plan.idx || plan.B != B || nbatch > plan.cap ||
-                      (theta && !plan.idx2);
-    if (grow) {
-        plan_free(plan);
-        const int64_t nb = nbatch < 1 ? 1 : nbatch;
-        CGGM_CUDA_TRY(cudaMalloc(&plan.nidx, sizeof(int32_t) * nb));
-        CGGM_CUDA_TRY(cudaMalloc(&plan.nidx2, sizeof(int32_t) * nb));
-        CGGM_CUDA_TRY(cudaMalloc(&plan.idx, sizeof(int32_t) * nb * K));
-        CGGM_CUDA_TRY(cudaMalloc(&plan.idx2, sizeof(int32_t) * nb * K));
-        CGGM_CUDA_TRY(cudaMalloc(&plan.pa, sizeof(int32_t) * nb * B));
-        CGGM_CUDA_TRY(cudaMalloc(&plan.pb, sizeof(int32_t) * nb * B));
-        CGGM_CUDA_TRY(cudaMalloc(&plan.lptr, sizeof(int32_t) * nb * (K + 1)));
-        CGGM_CUDA_TRY(cudaMalloc(&plan.lent, sizeof(int32_t) * nb * K));
-        plan.B = B;
-        plan.K = K;
-        plan.nbatch = nb;
-        plan.cap = nb;
-    }
-    return CGGM_OK;
-}
-
-void plan_free(BatchPlan &plan) {
-    cudaFree(plan.nidx); cudaFree(plan.nidx2); cudaFree(plan.idx); cudaFree(plan.idx2);
-    cudaFree(plan.pa); cudaFree(plan.pb); cudaFree(plan.lptr); cudaFree(plan.lent);
-    plan = BatchPlan();
-}
-
-cggm_status scratch_reserve(SweepScratch &scr, int B, int grid) {
-    if (scr.partial) return CGGM_OK;
-    const int Bmax = 256, K = 2 * Bmax;
-    (void)B;
-    CGGM_CUDA_TRY(cudaMalloc(&scr.partial, sizeof(double) * (size_t)grid * Bmax * 3));
+cggm_status scratch_reserve(SweepScratch &scr) {
+    if (scr.mu) return CGGM_OK;
+    const int Bmax = 256;  // float; double batches are at most 128 and take less
     CGGM_CUDA_TRY(cudaMalloc(&scr.mu, sizeof(double) * Bmax));
-    CGGM_CUDA_TRY(cudaMalloc(&scr.sub1, sizeof(double) * (size_t)K * K));
-    CGGM_CUDA_TRY(cudaMalloc(&scr.sub2, sizeof(double) * (size_t)K * K));
+    CGGM_CUDA_TRY(cudaMalloc(&scr.sub1, scratch_sub1_bytes(Bmax, sizeof(float))));
+    CGGM_CUDA_TRY(cudaMalloc(&scr.sub2, scratch_sub2_bytes(Bmax, sizeof(float))));
     CGGM_CUDA_TRY(cudaMalloc(&scr.bar, sizeof(GridBarrier)));
-    CGGM_CUDA_TRY(cudaMalloc(&scr.ticket, sizeof(unsigned)));
     CGGM_CUDA_TRY(cudaMalloc(&scr.err, sizeof(int)));
     CGGM_CUDA_TRY(cudaMemset(scr.bar, 0, sizeof(GridBarrier)));
-    CGGM_CUDA_TRY(cudaMemset(scr.ticket, 0, sizeof(unsigned)));
     CGGM_CUDA_TRY(cudaMemset(scr.err, 0, sizeof(int)));
     return CGGM_OK;
 }
 
 void scratch_free(SweepScratch &scr) {
-    cudaFree(scr.partial); cudaFree(scr.mu); cudaFree(scr.sub1); cudaFree(scr.sub2);
-    cudaFree(scr.bar); cudaFree(scr.ticket); cudaFree(scr.err);
+    cudaFree(scr.mu); cudaFree(scr.sub1); cudaFree(scr.sub2);
+    cudaFree(scr.bar); cudaFree(scr.err);
     scr = SweepScratch();
 }
 
@@ -710,15 +757,13 @@ template <typename T>
 cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *Sd,
                          const double *Pd, const double *G, const double *Lambda, int64_t m,
                          const int32_t *ai, const int32_t *aj, double lam_off, double lam_diag,
-                         double *D, T *U, int B, BatchPlan &plan, SweepScratch &scr,
+                         double *D, T *U, int B, SweepScratch &scr,
                          cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
     if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
-    (void)plan;
-    CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
+    CGGM_TRY(scratch_reserve(scr));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
-    CGGM_CUDA_TRY(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), st));
     const size_t smem = smem_layout<T>(B).total;
     void *args[] = {(void *)&q, (void *)&Sigma, (void *)&Psi, (void *)&Sd, (void *)&Pd,
                     (void *)&G, (void *)&Lambda, (void *)&m, (void *)&ai, (void *)&aj,
@@ -737,20 +782,18 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
     return read_err(scr.err, st);
 }
 
-// Same pass as lambda_sweep on plan and scratch buffers that the caller has already laid
-// out (pointers set, capacity for ceil(m / B) batches); allocates nothing.
+// Same pass as lambda_sweep on scratch buffers that the caller has already laid out;
+// allocates nothing.
 cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const double *Psi,
                                         const double *Sd, const double *Pd, const double *G,
                                         const double *Lambda, int64_t m, const int32_t *ai,
                                         const int32_t *aj, double lam_off, double lam_diag,
-                                        double *D, double *U, int B, BatchPlan plan,
-                                        SweepScratch scr, cudaStream_t st) {
+                                        double *D, double *U, int B, SweepScratch scr,
+                                        cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
     if (B != 32 && B != 64 && B != 128) return CGGM_EINVAL;
-    (void)plan;
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
-    CGGM_CUDA_TRY(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), st));
     const size_t smem = smem_layout<double>(B).total;
     void *args[] = {(void *)&q, (void *)&Sigma, (void *)&Psi, (void *)&Sd, (void *)&Pd,
                     (void *)&G, (void *)&Lambda, (void *)&m, (void *)&ai, (void *)&aj,
@@ -768,14 +811,12 @@ template <typename T>
 cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, const T *Sigma,
                         const double *Sd, const double *W, double *Theta, int64_t m,
                         const int32_t *ti, const int32_t *tj, double lam, T *dV, int B,
-                        BatchPlan &plan, SweepScratch &scr, cudaStream_t st) {
+                        SweepScratch &scr, cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
     if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
-    (void)plan;
-    CGGM_TRY(scratch_reserve(scr, B, sweep_grid()));
+    CGGM_TRY(scratch_reserve(scr));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
-    CGGM_CUDA_TRY(cudaMemsetAsync(scr.ticket, 0, sizeof(unsigned), st));
     const size_t smem = smem_layout<T>(B).total;
     void *args[] = {(void *)&p, (void *)&q, (void *)&Sxx, (void *)&Xd, (void *)&Sigma,
                     (void *)&Sd, (void *)&W, (void *)&Theta, (void *)&m, (void *)&ti,
@@ -796,18 +837,18 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
 template cggm_status lambda_sweep<double>(int64_t, const double *, const double *, const double *,
                                           const double *, const double *, const double *, int64_t,
                                           const int32_t *, const int32_t *, double, double, double *,
-                                          double *, int, BatchPlan &, SweepScratch &, cudaStream_t);
+                                          double *, int, SweepScratch &, cudaStream_t);
 template cggm_status lambda_sweep<float>(int64_t, const float *, const float *, const double *,
                                          const double *, const double *, const double *, int64_t,
                                          const int32_t *, const int32_t *, double, double, double *,
-                                         float *, int, BatchPlan &, SweepScratch &, cudaStream_t);
+                                         float *, int, SweepScratch &, cudaStream_t);
 template cggm_status theta_sweep<double>(int64_t, int64_t, const double *, const double *,
                                          const double *, const double *, const double *, double *,
                                          int64_t, const int32_t *, const int32_t *, double, double *,
-                                         int, BatchPlan &, SweepScratch &, cudaStream_t);
+                                         int, SweepScratch &, cudaStream_t);
 template cggm_status theta_sweep<float>(int64_t, int64_t, const float *, const double *,
                                         const float *, const double *, const double *, double *,
                                         int64_t, const int32_t *, const int32_t *, double, float *,
-                                        int, BatchPlan &, SweepScratch &, cudaStream_t);
+                                        int, SweepScratch &, cudaStream_t);
 
 }  // namespace cggm

@@ -5,33 +5,13 @@
 
 namespace cggm {
 
-// Batch plan: the active list cut into batches of B consecutive coordinates, with the
-// sorted distinct indices each batch touches, every coordinate's positions in them,
-// and, per distinct index, the list of (coordinate, partner position) pairs whose
-// update lands on that index's row of the cache (U or Delta V).
-struct BatchPlan {
-    int B = 0;           // coordinates per batch (32, 64 or 128)
-    int K = 0;           // 2B
-    int64_t nbatch = 0;
-    int64_t cap = 0;     // batches the buffers hold
-    int32_t *nidx = nullptr;   // [nbatch]      distinct first indices (Theta: distinct i)
-    int32_t *nidx2 = nullptr;  // [nbatch]      Theta only: distinct j
-    int32_t *idx = nullptr;    // [nbatch][K]
-    int32_t *idx2 = nullptr;   // [nbatch][K]   Theta only
-    int32_t *pa = nullptr;     // [nbatch][B]
-    int32_t *pb = nullptr;     // [nbatch][B]
-    int32_t *lptr = nullptr;   // [nbatch][K+1]
-    int32_t *lent = nullptr;   // [nbatch][K]   (l << 16) | partner position
-};
-
-// Device scratch shared by the sweep kernels (sized for the largest B and grid).
+// Device scratch shared by the sweep kernels (sized for the largest B).
 struct SweepScratch {
-    double *partial = nullptr;  // [grid][B][3]
-    double *mu = nullptr;       // [B]
-    void *sub1 = nullptr;       // [K][K] gathered submatrix (T)
-    void *sub2 = nullptr;       // [K][K]
+    double *mu = nullptr;  // [B] the batch's steps
+    void *sub1 = nullptr;  // [2][PRE_N][B] step constants of two batches (T)
+    void *sub2 = nullptr;  // [2][coef_slots(B)] in-batch coefficients of two batches,
+                           // [B][B] cross coefficients, [B] corrections (T)
     GridBarrier *bar = nullptr;
-    unsigned *ticket = nullptr;
     int *err = nullptr;
 };
 
@@ -42,7 +22,7 @@ template <typename T>
 cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *Sd,
                          const double *Pd, const double *G, const double *Lambda, int64_t m,
                          const int32_t *ai, const int32_t *aj, double lam_off, double lam_diag,
-                         double *D, T *U, int B, BatchPlan &plan, SweepScratch &scr,
+                         double *D, T *U, int B, SweepScratch &scr,
                          cudaStream_t st);
 
 // Theta pass: coordinates (ti, tj) row-major.  Sxx (p x p, T) with double diagonal Xd,
@@ -52,21 +32,33 @@ template <typename T>
 cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, const T *Sigma,
                         const double *Sd, const double *W, double *Theta, int64_t m,
                         const int32_t *ti, const int32_t *tj, double lam, T *dV, int B,
-                        BatchPlan &plan, SweepScratch &scr, cudaStream_t st);
+                        SweepScratch &scr, cudaStream_t st);
 
-// lambda_sweep in double on plan and scratch buffers laid out by the caller (their
-// pointers set, plan.cap >= ceil(m / B)); allocates nothing.  B in {32, 64, 128}.
+// lambda_sweep in double on scratch buffers laid out by the caller (mu: B doubles, sub1:
+// scratch_sub1_bytes(B, 8), sub2: scratch_sub2_bytes(B, 8), bar, err); allocates nothing.
+// B in {32, 64, 128}.
 cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const double *Psi,
                                         const double *Sd, const double *Pd, const double *G,
                                         const double *Lambda, int64_t m, const int32_t *ai,
                                         const int32_t *aj, double lam_off, double lam_diag,
-                                        double *D, double *U, int B, BatchPlan plan,
-                                        SweepScratch scr, cudaStream_t st);
+                                        double *D, double *U, int B, SweepScratch scr,
+                                        cudaStream_t st);
 
-// Plan storage helpers (allocate on demand, grow only).
-cggm_status plan_reserve(BatchPlan &plan, int B, int64_t nbatch, bool theta);
-void plan_free(BatchPlan &plan);
-cggm_status scratch_reserve(SweepScratch &scr, int B, int grid);
+// Per-coordinate step constants kept for phase B, and the slots of a batch's in-batch
+// coefficients (B (B - 1) / 2 of them, padded).
+constexpr int kStepConstants = 9;
+__host__ __device__ constexpr int coef_slots(int B) { return ((B * (B - 1) / 2 + 8) + 3) & ~3; }
+
+// Scratch sizes for batch size B and element size esz.
+constexpr size_t scratch_sub1_bytes(int B, size_t esz) {
+    return esz * 2 * kStepConstants * (size_t)B;
+}
+constexpr size_t scratch_sub2_bytes(int B, size_t esz) {
+    return esz * (2 * (size_t)coef_slots(B) + (size_t)B * B + (size_t)B);
+}
+
+// Allocates the scratch once, for B 256 in float (which also covers B <= 128 in double).
+cggm_status scratch_reserve(SweepScratch &scr);
 void scratch_free(SweepScratch &scr);
 
 int sweep_grid();  // CTAs of the persistent sweep kernels (one per SM)
