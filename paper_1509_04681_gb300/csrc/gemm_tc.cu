@@ -23,6 +23,7 @@
 
 #include "common.cuh"
 #include "gemm_tc.cuh"
+#include "mbar.cuh"
 
 namespace cggm {
 
@@ -33,51 +34,7 @@ constexpr int STAGES_PLAIN = 4;  // 4 x 2 tiles x 16 KB = 128 KB of shared memor
 constexpr int STAGES_SPLIT = 3;  // 3 x 4 tiles x 16 KB = 192 KB
 constexpr int THREADS = 128;
 constexpr int TILE_BYTES = TM * TK * 4;     // 16 KB (A tile; B tile is the same size)
-constexpr uint64_t WAIT_NS = 1000000000ull; // 1 s
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: true when the phase completed, false (and *err set) at the deadline or when
-// another thread of the kernel has already failed.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, int *err) {
-    if (mbar_try(b, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (unsigned it = 1;; it++) {
-        if (mbar_try(b, parity)) return true;
-        if ((it & 255u) == 0) {
-            if (*(volatile int *)err != 0) return false;
-            if (global_ns() - t0 > WAIT_NS) {
-                atomicCAS(err, 0, (int)DEV_TIMEOUT);
-                return false;
-            }
-        }
-    }
-}
+constexpr uint64_t WAIT_NS = kMbarWaitNs;
 
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
                                             uint64_t *mbar) {
@@ -161,7 +118,7 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             mbar_init(&empty[s], 1);
         }
         mbar_init(&done, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
     }

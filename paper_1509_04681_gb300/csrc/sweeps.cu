@@ -23,6 +23,7 @@
 // starts its correction sums from it.  Grid barriers separate B from C and C from the
 // next B.
 #include "sweeps.cuh"
+#include "mbar.cuh"
 
 #include <cooperative_groups.h>
 #include <mutex>
@@ -31,6 +32,10 @@ namespace cggm {
 
 namespace {
 constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+// Phase C: each warp updates this many cache rows at once, their loads all issued before
+// the first use, so that the L2 round trips of different rows overlap.
+constexpr int kRowsInFlight = 4;
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
@@ -115,19 +120,37 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
 // step of its own coordinate of the current panel and the owner's candidate is broadcast,
 // so the dependent chain per coordinate is a few T operations and one warp shuffle.
 template <typename T, int NS>
-__device__ void forward_substitution(int nb, int B, const T *__restrict__ pre,
-                                     const T *acc0, const T *coef, double *mu_out, int *err) {
+__device__ void forward_substitution(int nb, const T *__restrict__ pre, const T *acc0,
+                                     const T *coef, uint64_t *mb, uint32_t &phase,
+                                     double *mu_out, int *err) {
     // pre[] holds, for padding coordinates l >= nb, constants that give mu = 0 whatever
     // the correction sum (ai = 0, u = 0, r = 1, mc = 0), so panels run all 32 steps
-    // without branches.
+    // without branches.  B is a compile-time constant, so that every coefficient address
+    // below is the lane index plus an immediate offset.
+    constexpr int B = NS * 32;
     const int lane = threadIdx.x & 31;
+    bool bad = false;
+    int lost = -1;  // first panel whose data did not arrive (NS: the step constants)
+    if (!mbar_wait(&mb[NS], (phase >> NS) & 1u, err)) {
+        lost = 0;
+        for (int s = 0; s * 32 < nb && s < NS; s++)
+            if (mbar_wait(&mb[s], (phase >> s) & 1u, err, false)) phase ^= 1u << s;
+        if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
+        return;
+    }
+    phase ^= 1u << NS;
     T acc[NS];  // correction sums, starting from the corrections carried from the previous batch
 #pragma unroll
     for (int s = 0; s < NS; s++) acc[s] = acc0[s * 32 + lane];
-    bool bad = false;
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         if (s * 32 >= nb) break;
+        // the coefficients of panel s (columns 32 s .. 32 s + 31) land on mb[s]
+        if (!mbar_wait(&mb[s], (phase >> s) & 1u, err)) {
+            lost = s;
+            break;
+        }
+        phase ^= 1u << s;
         const int lo = s * 32 + lane;
         const T uh = pre[PRE_UH * B + lo], ul = pre[PRE_UL * B + lo];
         const T vph = pre[PRE_VPH * B + lo], vpl = pre[PRE_VPL * B + lo];
@@ -163,50 +186,43 @@ __device__ void forward_substitution(int nb, int B, const T *__restrict__ pre,
             mu_out[lo] = m;
         }
     }
+    if (lost >= 0) {  // the pass is abandoned; wait (bounded) for the copies still in flight
+        for (int s = lost; s * 32 < nb && s < NS; s++)
+            if (mbar_wait(&mb[s], (phase >> s) & 1u, err, false)) phase ^= 1u << s;
+    }
     if (bad) set_err(err, DEV_NONFINITE);
 }
 
-// Copy n elements global -> shared (both 16-byte aligned, n rounded up to 16 bytes; the
-// buffers have that slack) with 16-byte loads, eight in flight per thread.
-template <typename T>
-__device__ void copy_to_smem(const T *g, T *sm, int n) {
-    const int nv = (int)((n * sizeof(T) + 15) / 16);
-    const int4 *gv = reinterpret_cast<const int4 *>(g);
-    int4 *sv = reinterpret_cast<int4 *>(sm);
-    for (int base = threadIdx.x; base < nv; base += 8 * blockDim.x) {
-        int4 v[8];
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int k = base + u * blockDim.x;
-            if (k < nv) v[u] = __ldcg(gv + k);
-        }
-#pragma unroll
-        for (int u = 0; u < 8; u++) {
-            const int k = base + u * blockDim.x;
-            if (k < nv) sv[k] = v[u];
-        }
-    }
-}
-
-// Phase B body shared by both passes: stage the coefficients and step constants, run
-// the substitution.
+// Phase B body shared by both passes: one thread starts bulk copies of the step constants
+// and carried corrections (completing on mb[NS]) and of each panel's coefficient columns
+// (panel s on mb[s]) into shared memory; warp 0 runs the substitution, starting each panel
+// as soon as its coefficients have landed.  The step constants of padding coordinates
+// (l >= nb) and their corrections were written in global memory with the batch, so the
+// copies bring whole arrays.  Coefficient slots of padding coordinates are never used by a
+// real coordinate: they only reach the correction sums of padding coordinates.
 template <typename T, int NS>
-__device__ void phase_b(int nb, int B, const T *gcoef, const T *gpre, const T *gcorr, T *scoef,
-                        T *spre, double *mu, int *err) {
-    const int ncoef = colbase(nb - 1, B) + 1;  // through column nb - 2 (all entries used)
+__device__ void phase_b(int nb, const T *gcoef, const T *gpre, const T *gcorr, T *scoef, T *spre,
+                        uint64_t *mb, uint32_t &phase, double *mu, int *err) {
+    constexpr int B = NS * 32;
     T *scorr = spre + PRE_N * B;
-    copy_to_smem<T>(gcoef, scoef, ncoef);
-    copy_to_smem<T>(gpre, spre, PRE_N * B);
-    for (int l = threadIdx.x; l < B; l += blockDim.x) scorr[l] = (l < nb) ? __ldcg(gcorr + l) : T(0);
-    __syncthreads();
-    for (int l = nb + threadIdx.x; l < B; l += blockDim.x) {  // padding: mu = 0
-        for (int k = 0; k < PRE_N; k++) spre[k * B + l] = T(0);
-        spre[PRE_R * B + l] = T(1);
+    if ((threadIdx.x >> 5) == 0) {
+        if (threadIdx.x == 0) {
+            // the sources were written by other CTAs (ordered before this point by the grid
+            // barrier) and the destination was last used through the generic proxy
+            fence_proxy_async();
+            mbar_expect_tx(&mb[NS], (uint32_t)((PRE_N * B + B) * sizeof(T)));
+            bulk_load(spre, gpre, (uint32_t)(PRE_N * B * sizeof(T)), &mb[NS]);
+            bulk_load(scorr, gcorr, (uint32_t)(B * sizeof(T)), &mb[NS]);
+            for (int s = 0; s * 32 < nb; s++) {
+                const int c0 = colbase(32 * s, B), c1 = colbase(32 * s + 32, B);
+                const uint32_t bytes = (uint32_t)((size_t)(c1 - c0) * sizeof(T));
+                mbar_expect_tx(&mb[s], bytes);
+                bulk_load(scoef + c0, gcoef + c0, bytes, &mb[s]);
+            }
+        }
+        __syncwarp();
+        forward_substitution<T, NS>(nb, spre, scorr, scoef, mb, phase, mu, err);
     }
-    const int nc = colbase(nb - 1, B) + 1, ncb = B * (B - 1) / 2;
-    for (int e = nc + threadIdx.x; e < ncb; e += blockDim.x) scoef[e] = T(0);
-    __syncthreads();
-    if ((threadIdx.x >> 5) == 0) forward_substitution<T, NS>(nb, B, spre, scorr, scoef, mu, err);
     __syncthreads();
 }
 
@@ -301,6 +317,8 @@ __device__ void cross_corrections(int nbn, int nbk, int B, const T *X, const dou
         acc = warp_sum(acc);
         if (lane == 0) corr[l] = acc;
     }
+    if (blockIdx.x == gridDim.x - 1)  // padding coordinates of the next batch
+        for (int l = nbn + threadIdx.x; l < B; l += blockDim.x) corr[l] = T(0);
 }
 
 template <typename T, int NS>
@@ -309,10 +327,14 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                     const double *__restrict__ Sd, const double *__restrict__ Pd,
                     const double *__restrict__ G, const double *__restrict__ Lam, int64_t m,
                     const int32_t *__restrict__ ai, const int32_t *__restrict__ aj,
-                    double lam_off, double lam_diag, double *D, T *Ut, int B,
+                    double lam_off, double lam_diag, double *D, T *Ut, int B_arg,
                     SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[(kThreads / 32) * 6];
+    __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
+    uint32_t mb_phase = 0;
+    constexpr int B = NS * 32;
+    if (B_arg != B) return;  // the host launches the instance of its batch size
     const SmemLayout L = smem_layout<T>(B);
     unsigned char *work = smem + L.work;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -332,17 +354,23 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
 
     auto S = [&](int64_t x, int64_t y) -> T { return Sig[x * q + y]; };
     auto P = [&](int64_t x, int64_t y) -> T { return Psi[x * q + y]; };
-    // change of the three dot products of coordinate (pi, pj) per unit step of (pa, pb)
+    // change of the three dot products of coordinate (pi, pj) per unit step of (pa, pb):
+    // (Sigma E Sigma)_ij + (Psi E Sigma)_ij + (Psi E Sigma)_ji with E = E_ab + E_ba (E_aa on
+    // the diagonal), the middle term doubled when i == j.  Sigma and Psi are symmetric, and
+    // every entry that involves pb (the index that varies fastest across threads) is read
+    // along a row, so that neighbouring threads read neighbouring words.
     auto coefficient = [&](int64_t pi, int64_t pj, int64_t pa, int64_t pb) -> T {
+        const T s_ia = S(pi, pa), s_ib = S(pi, pb), s_aj = S(pa, pj), s_jb = S(pj, pb);
+        const T p_ia = P(pi, pa), p_ib = P(pi, pb), p_ja = P(pj, pa), p_jb = P(pj, pb);
         T c1, c2, c3;
         if (pa != pb) {
-            c1 = S(pi, pa) * S(pb, pj) + S(pi, pb) * S(pa, pj);
-            c2 = P(pi, pa) * S(pb, pj) + P(pi, pb) * S(pa, pj);
-            c3 = P(pj, pa) * S(pb, pi) + P(pj, pb) * S(pa, pi);
+            c1 = s_ia * s_jb + s_ib * s_aj;
+            c2 = p_ia * s_jb + p_ib * s_aj;
+            c3 = p_ja * s_ib + p_jb * s_ia;
         } else {
-            c1 = S(pi, pa) * S(pa, pj);
-            c2 = P(pi, pa) * S(pa, pj);
-            c3 = P(pj, pa) * S(pa, pi);
+            c1 = s_ia * s_aj;
+            c2 = p_ia * s_aj;
+            c3 = p_ja * s_ia;
         }
         return (pi != pj) ? (c1 + c2 + c3) : (c1 + T(2) * c2);
     };
@@ -433,6 +461,10 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         }
         const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
         const int64_t nt = (int64_t)nA * blockDim.x;
+        for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
+            const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
+            pre[k * B + l] = (k == PRE_R) ? T(1) : T(0);
+        }
         const int ncoef = nb * (nb - 1) / 2;
         for (int64_t e = t0; e < ncoef; e += nt) {
             int l, l1;
@@ -453,8 +485,13 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
     int nbk = (int)(m < B ? m : B);
     load_batch(ai, aj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
     phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k <= NS; k++) mbar_init(&s_mb[k], 1);
+            mbar_init_fence();
+        }
+    }
     if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
     for (int64_t k = 0; k < nbatch; k++) {
@@ -467,14 +504,9 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
 
         // ---- phase B of batch k on CTA 0, phase A of batch k+1 on the others ----
         if (blockIdx.x == 0) {
-            phase_b<T, NS>(nbk, B, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
-            for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
-                const int64_t i = cur.sa[l], j = cur.sb[l];
-                const double mu = scr.mu[l];
-                D[i * q + j] = mu;
-                if (i != j) D[j * q + i] = mu;
-            }
+            phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
+                           reinterpret_cast<T *>(work) + coef_slots(B), s_mb, mb_phase, scr.mu,
+                           scr.err);
         } else if (nbn > 0) {
             phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
         }
@@ -485,42 +517,68 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         // (b != a); transposed: Ut[t][a] += sum mu Sigma[t][b], Ut[t][b] += mu Sigma[t][a]
         {
             T *smu = reinterpret_cast<T *>(work);
-            for (int l = threadIdx.x; l < nbk; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
+            for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
+                const double mu = __ldcg(scr.mu + l);
+                smu[l] = (T)mu;
+                if (blockIdx.x == nblk - 1) {  // the direction itself
+                    const int64_t i = cur.sa[l], j = cur.sb[l];
+                    D[i * q + j] = mu;
+                    if (i != j) D[j * q + i] = mu;
+                }
+            }
             __syncthreads();
             const int nseg = *cur.snseg;
-            for (int64_t t = r0 + warp; t < r1; t += (kThreads / 32)) {
-                const T *Sr = Sig + t * q;
-                T *Ur = Ut + t * q;
-                for (int g = 0; g < nseg; g++) {
-                    const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
-                    const int64_t a = cur.sa[l0];
-                    T sv[NS], uv[NS], mv[NS];
-                    int64_t bv[NS];
-                    const T sta = Sr[a];
+            constexpr int R = kRowsInFlight;
+            for (int g = 0; g < nseg; g++) {
+                const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
+                const int a = cur.sa[l0];
+                int bv[NS];
+                T mv[NS];
 #pragma unroll
-                    for (int kk = 0; kk < NS; kk++) {
-                        const int l = l0 + lane + 32 * kk;
-                        bv[kk] = -1;
-                        if (l < l1) {
-                            bv[kk] = cur.sb[l];
-                            mv[kk] = smu[l];
-                            sv[kk] = Sr[bv[kk]];
-                            uv[kk] = (bv[kk] != a) ? __ldcg(Ur + bv[kk]) : T(0);
-                        }
-                    }
-                    T dot = T(0);
-#pragma unroll
-                    for (int kk = 0; kk < NS; kk++) {
-                        if (bv[kk] >= 0) {
-                            dot = fma(mv[kk], sv[kk], dot);
-                            if (bv[kk] != a) Ur[bv[kk]] = uv[kk] + mv[kk] * sta;
-                        }
-                    }
-                    dot = warp_sum(dot);
-                    __syncwarp();
-                    if (lane == 0) Ur[a] = __ldcg(Ur + a) + dot;
-                    __syncwarp();
+                for (int kk = 0; kk < NS; kk++) {
+                    const int l = l0 + lane + 32 * kk;
+                    bv[kk] = (l < l1) ? cur.sb[l] : -1;
+                    mv[kk] = (l < l1) ? smu[l] : T(0);
                 }
+                for (int64_t tb = r0 + warp; tb < r1; tb += kWarps * R) {
+                    T sta[R], sv[R][NS], uv[R][NS];
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int64_t t = tb + (int64_t)kWarps * r;
+                        sta[r] = T(0);
+#pragma unroll
+                        for (int kk = 0; kk < NS; kk++) sv[r][kk] = uv[r][kk] = T(0);
+                        if (t < r1) {
+                            const T *Sr = Sig + t * q;
+                            const T *Ur = Ut + t * q;
+                            sta[r] = Sr[a];
+#pragma unroll
+                            for (int kk = 0; kk < NS; kk++) {
+                                if (bv[kk] >= 0) {
+                                    sv[r][kk] = Sr[bv[kk]];
+                                    if (bv[kk] != a) uv[r][kk] = __ldcg(Ur + bv[kk]);
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int64_t t = tb + (int64_t)kWarps * r;
+                        if (t >= r1) break;  // warp-uniform
+                        T *Ur = Ut + t * q;
+                        T dot = T(0);
+#pragma unroll
+                        for (int kk = 0; kk < NS; kk++) {
+                            if (bv[kk] >= 0) {
+                                dot = fma(mv[kk], sv[r][kk], dot);
+                                if (bv[kk] != a) Ur[bv[kk]] = uv[r][kk] + mv[kk] * sta[r];
+                            }
+                        }
+                        dot = warp_sum(dot);
+                        if (lane == 0) Ur[a] = __ldcg(Ur + a) + dot;
+                    }
+                }
+                __syncwarp();  // this segment's writes before the next segment's reads
             }
             if (nbn > 0) cross_corrections<T>(nbn, nbk, B, gX, scr.mu, gcorr);
         }
@@ -542,9 +600,13 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                    const T *__restrict__ Sig, const double *__restrict__ Sd,
                    const double *__restrict__ W, double *Theta, int64_t m,
                    const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam,
-                   T *dVt, int B, SweepScratch scr) {
+                   T *dVt, int B_arg, SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[(kThreads / 32) * 2];
+    __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
+    uint32_t mb_phase = 0;
+    constexpr int B = NS * 32;
+    if (B_arg != B) return;  // the host launches the instance of its batch size
     const SmemLayout L = smem_layout<T>(B);
     unsigned char *work = smem + L.work;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -561,9 +623,10 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
     const int64_t nbatch = (m + B - 1) / B;
     if (nbatch == 0) return;
 
-    // change of (S_xx Delta V)_ij per unit step of Theta_ab, times 2: 2 (S_xx)_{i a} Sigma_{b j}
+    // change of (S_xx Delta V)_ij per unit step of Theta_ab, times 2: 2 (S_xx)_{i a} Sigma_{j b}
+    // (Sigma symmetric; read along row j, b varying fastest across threads)
     auto coefficient = [&](int64_t i, int64_t j, int64_t a, int64_t b) -> T {
-        return T(2) * Sxx[i * p + a] * Sig[b * q + j];
+        return T(2) * Sxx[i * p + a] * Sig[j * q + b];
     };
 
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
@@ -616,6 +679,10 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
         }
         const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
         const int64_t nt = (int64_t)nA * blockDim.x;
+        for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
+            const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
+            pre[k * B + l] = (k == PRE_R) ? T(1) : T(0);
+        }
         const int ncoef = nb * (nb - 1) / 2;
         for (int64_t e = t0; e < ncoef; e += nt) {
             int l, l1;
@@ -635,8 +702,13 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
     int nbk = (int)(m < B ? m : B);
     load_batch(ti, tj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
     phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
-    if (blockIdx.x == 0)
+    if (blockIdx.x == 0) {
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k <= NS; k++) mbar_init(&s_mb[k], 1);
+            mbar_init_fence();
+        }
+    }
     if (!grid_sync(scr.bar, scr.err, nblk)) return;
 
     for (int64_t k = 0; k < nbatch; k++) {
@@ -648,12 +720,9 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
         if (nbn > 0) load_batch(ti, tj, sn, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
 
         if (blockIdx.x == 0) {
-            phase_b<T, NS>(nbk, B, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_slots(B), scr.mu, scr.err);
-            for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
-                const int64_t i = cur.sa[l], j = cur.sb[l];
-                Theta[i * q + j] = __ldcg(Theta + i * q + j) + scr.mu[l];
-            }
+            phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
+                           reinterpret_cast<T *>(work) + coef_slots(B), s_mb, mb_phase, scr.mu,
+                           scr.err);
         } else if (nbn > 0) {
             phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
         }
@@ -662,32 +731,49 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
         // ---- phase C: dVt[t][i] += sum over the segment of row i of mu Sigma[t][j] ----
         {
             T *smu = reinterpret_cast<T *>(work);
-            for (int l = threadIdx.x; l < nbk; l += blockDim.x) smu[l] = (T)__ldcg(scr.mu + l);
+            for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
+                const double mu = __ldcg(scr.mu + l);
+                smu[l] = (T)mu;
+                if (blockIdx.x == nblk - 1) {  // Theta itself
+                    const int64_t i = cur.sa[l], j = cur.sb[l];
+                    Theta[i * q + j] = __ldcg(Theta + i * q + j) + mu;
+                }
+            }
             __syncthreads();
             const int nseg = *cur.snseg;
-            for (int64_t t = r0 + warp; t < r1; t += (kThreads / 32)) {
-                const T *Sr = Sig + t * q;
-                T *Vr = dVt + t * p;
-                for (int g = 0; g < nseg; g++) {
-                    const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
-                    T sv[NS], mv[NS];
+            constexpr int R = kRowsInFlight;
+            for (int g = 0; g < nseg; g++) {
+                const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
+                const int i = cur.sa[l0];
+                int jv[NS];
+                T mv[NS];
 #pragma unroll
-                    for (int kk = 0; kk < NS; kk++) {
-                        const int l = l0 + lane + 32 * kk;
-                        sv[kk] = T(0);
-                        mv[kk] = T(0);
-                        if (l < l1) {
-                            mv[kk] = smu[l];
-                            sv[kk] = Sr[cur.sb[l]];
-                        }
+                for (int kk = 0; kk < NS; kk++) {
+                    const int l = l0 + lane + 32 * kk;
+                    jv[kk] = (l < l1) ? cur.sb[l] : -1;
+                    mv[kk] = (l < l1) ? smu[l] : T(0);
+                }
+                for (int64_t tb = r0 + warp; tb < r1; tb += kWarps * R) {
+                    T sv[R][NS];
+#pragma unroll
+                    for (int r = 0; r < R; r++) {
+                        const int64_t t = tb + (int64_t)kWarps * r;
+#pragma unroll
+                        for (int kk = 0; kk < NS; kk++)
+                            sv[r][kk] = (t < r1 && jv[kk] >= 0) ? Sig[t * q + jv[kk]] : T(0);
                     }
-                    T dot = T(0);
 #pragma unroll
-                    for (int kk = 0; kk < NS; kk++) dot = fma(mv[kk], sv[kk], dot);
-                    dot = warp_sum(dot);
-                    if (lane == 0) {
-                        const int64_t i = cur.sa[l0];
-                        Vr[i] = __ldcg(Vr + i) + dot;
+                    for (int r = 0; r < R; r++) {
+                        const int64_t t = tb + (int64_t)kWarps * r;
+                        if (t >= r1) break;  // warp-uniform
+                        T dot = T(0);
+#pragma unroll
+                        for (int kk = 0; kk < NS; kk++) dot = fma(mv[kk], sv[r][kk], dot);
+                        dot = warp_sum(dot);
+                        if (lane == 0) {
+                            T *Vr = dVt + t * p;
+                            Vr[i] = __ldcg(Vr + i) + dot;
+                        }
                     }
                 }
             }
