@@ -43,11 +43,15 @@ __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, 
 // shared pieces of the sweep kernels
 // ---------------------------------------------------------------------------------
 // Per-coordinate step constants, formed in double in phase A and stored in the cache
-// type T (hi + lo pairs where the value carries the result):
-//   u = c - base/a, r = lam/a, vp = u - r - c, vm = u + r - c, ai = 1/a, mc = -c.
-// With acc = the in-batch correction sum, w = u - acc/a and the step is vp - acc/a
-// (w > r), vm - acc/a (w < -r), -c otherwise (zero curvature: always -c).
-enum { PRE_UH, PRE_UL, PRE_VPH, PRE_VPL, PRE_VMH, PRE_VML, PRE_AI, PRE_R, PRE_MC, PRE_N };
+// type T (hi + lo pairs where the value carries the result).  The exact minimiser of
+// (a/2) mu^2 + b mu + lam |c + mu| (Appendix A.1) is mu = -c + S_{lam/a}(c - b/a); written
+// with  vp = -(b + lam)/a  (the step when the soft-threshold takes its upper branch),
+// vm = (lam - b)/a  (lower branch) and mc = -c  (the entry goes to zero), and since vp <= vm,
+//   mu = median(vp, mc, vm) = max(vp, min(vm, mc)):
+// the upper branch is taken exactly when vp > -c, the lower one when vm < -c.  A correction
+// sum acc added to b shifts both vp and vm by -acc/a, so they are kept as
+// vp - ai acc, vm - ai acc with ai = 1/a.  Zero curvature (a = 0): vp = vm = -c, ai = 0.
+enum { PRE_VPH, PRE_VPL, PRE_VMH, PRE_VML, PRE_AI, PRE_MC, PRE_N };
 static_assert(PRE_N == kStepConstants, "step constant count");
 
 template <typename T>
@@ -61,18 +65,13 @@ __device__ void step_constants(double base, double a, double c, double lam, T *p
     T *o = pre;
     if (a > 0.0 && isfinite(a)) {
         const double ai = 1.0 / a;
-        const double u = c - base * ai, r = lam * ai;
-        split<T>(u, o + PRE_UH * B + l, o + PRE_UL * B + l);
-        split<T>(u - r - c, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
-        split<T>(u + r - c, o + PRE_VMH * B + l, o + PRE_VML * B + l);
+        split<T>(-(base + lam) * ai, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
+        split<T>((lam - base) * ai, o + PRE_VMH * B + l, o + PRE_VML * B + l);
         o[PRE_AI * B + l] = (T)ai;
-        o[PRE_R * B + l] = (T)r;
-    } else {  // zero curvature: w = 0 inside [-1, 1] selects -c
-        o[PRE_UH * B + l] = T(0); o[PRE_UL * B + l] = T(0);
+    } else {  // zero curvature: the entry goes to zero
         split<T>(-c, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
         split<T>(-c, o + PRE_VMH * B + l, o + PRE_VML * B + l);
         o[PRE_AI * B + l] = T(0);
-        o[PRE_R * B + l] = T(1);
     }
     o[PRE_MC * B + l] = (T)(-c);
 }
@@ -123,9 +122,9 @@ template <typename T, int NS>
 __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T *acc0,
                                      const T *coef, uint64_t *mb, uint32_t &phase,
                                      double *mu_out, int *err) {
-    // pre[] holds, for padding coordinates l >= nb, constants that give mu = 0 whatever
-    // the correction sum (ai = 0, u = 0, r = 1, mc = 0), so panels run all 32 steps
-    // without branches.  B is a compile-time constant, so that every coefficient address
+    // pre[] holds zeros for padding coordinates l >= nb, which give mu = 0 whatever the
+    // correction sum (also a non-finite one: fmin / fmax return the other operand), so
+    // panels run all 32 steps without branches.  B is a compile-time constant, so that every coefficient address
     // below is the lane index plus an immediate offset.
     constexpr int B = NS * 32;
     const int lane = threadIdx.x & 31;
@@ -152,33 +151,29 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
         }
         phase ^= 1u << s;
         const int lo = s * 32 + lane;
-        const T uh = pre[PRE_UH * B + lo], ul = pre[PRE_UL * B + lo];
         const T vph = pre[PRE_VPH * B + lo], vpl = pre[PRE_VPL * B + lo];
         const T vmh = pre[PRE_VMH * B + lo], vml = pre[PRE_VML * B + lo];
-        const T ai = pre[PRE_AI * B + lo], r = pre[PRE_R * B + lo], mc = pre[PRE_MC * B + lo];
-        // this panel's own coefficients coef(lo, 32 s + o) for o < lane, in registers
-        T cw[32];
-#pragma unroll
-        for (int o = 0; o < 32; o++) {
-            const int l = s * 32 + o;
-            cw[o] = (lane > o) ? coef[colbase(l, B) + (lo - l - 1)] : T(0);
-        }
+        const T ai = pre[PRE_AI * B + lo], mc = pre[PRE_MC * B + lo];
+        // the two branch values of this lane's coordinate with the corrections so far
+        T xp = fma(-acc[s], ai, vph) + vpl;
+        T xm = fma(-acc[s], ai, vmh) + vml;
         T mymu = T(0);
-#pragma unroll
+        // Steps are unrolled by four only: fully unrolled, the batch is tens of kilobytes of
+        // straight-line code that the instruction cache has to bring back for every batch.
+        // col points at column l of the packed coefficients, col[l2] = coef(l2, l), l2 > l.
+        const T *col = coef + colbase(32 * s, B) - 32 * s - 1;
+#pragma unroll 4
         for (int o = 0; o < 32; o++) {
             const int l = s * 32 + o;
-            const T w = fma(-acc[s], ai, uh) + ul;
-            const T mp = fma(-acc[s], ai, vph) + vpl;
-            const T mm = fma(-acc[s], ai, vmh) + vml;
-            const T cand = (w > r) ? mp : ((w < -r) ? mm : mc);
+            const T y = (lane > o) ? ai * col[lane > o ? lo : l + 1] : T(0);
+            const T cand = fmax(xp, fmin(xm, mc));
             const T mu = __shfl_sync(0xffffffffu, cand, o);
             mymu = (lane == o) ? cand : mymu;
-            acc[s] = fma(cw[o], mu, acc[s]);
+            xp = fma(-y, mu, xp);
+            xm = fma(-y, mu, xm);
 #pragma unroll
-            for (int s2 = s + 1; s2 < NS; s2++) {
-                const int l2 = s2 * 32 + lane;
-                acc[s2] = fma(coef[colbase(l, B) + (l2 - l - 1)], mu, acc[s2]);
-            }
+            for (int s2 = s + 1; s2 < NS; s2++) acc[s2] = fma(col[s2 * 32 + lane], mu, acc[s2]);
+            col += B - l - 2;  // colbase(l + 1) - (l + 1) - 1 = colbase(l) - l - 1 + (B - l - 2)
         }
         if (lo < nb) {
             double m = (double)mymu;
@@ -463,7 +458,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         const int64_t nt = (int64_t)nA * blockDim.x;
         for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
             const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
-            pre[k * B + l] = (k == PRE_R) ? T(1) : T(0);
+            pre[k * B + l] = T(0);
         }
         const int ncoef = nb * (nb - 1) / 2;
         for (int64_t e = t0; e < ncoef; e += nt) {
@@ -681,7 +676,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
         const int64_t nt = (int64_t)nA * blockDim.x;
         for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
             const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
-            pre[k * B + l] = (k == PRE_R) ? T(1) : T(0);
+            pre[k * B + l] = T(0);
         }
         const int ncoef = nb * (nb - 1) / 2;
         for (int64_t e = t0; e < ncoef; e += nt) {

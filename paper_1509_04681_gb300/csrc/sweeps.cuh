@@ -46,7 +46,7 @@ cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const do
 
 // Per-coordinate step constants kept for phase B, and the slots of a batch's in-batch
 // coefficients (B (B - 1) / 2 of them, padded).
-constexpr int kStepConstants = 9;
+constexpr int kStepConstants = 6;
 __host__ __device__ constexpr int coef_slots(int B) { return ((B * (B - 1) / 2 + 8) + 3) & ~3; }
 
 // Scratch sizes for batch size B and element size esz.
