@@ -36,6 +36,11 @@ constexpr int kWarps = kThreads / 32;
 // Phase C: each warp updates this many cache rows at once, their loads all issued before
 // the first use, so that the L2 round trips of different rows overlap.
 constexpr int kRowsInFlight = 4;
+// Phase A: rows per CTA held at once, chunks in flight, bytes per row and chunk.
+constexpr int kRingRows = 10;
+constexpr int kStages = 3;
+constexpr int kChunkBytes = 4096;
+constexpr size_t kRingBytes = (size_t)kStages * kRingRows * kChunkBytes;
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
@@ -93,7 +98,8 @@ __host__ __device__ __forceinline__ int colbase(int l, int B) { return l * (2 * 
 
 struct SmemLayout {
     size_t meta;  // twice (current and next batch): sa[B], sb[B], sseg[B + 1], nseg (ints)
-    size_t work;  // union: phase B coef[coef_slots(B)], step constants [PRE_N][B], corr[B] (T);
+    size_t work;  // union: phase A ring of row chunks (kRingBytes);
+                  //        phase B coef[coef_slots(B)], step constants [PRE_N][B], corr[B] (T);
                   //        phase C mu[B] (T)
     size_t total;
 };
@@ -107,7 +113,9 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
     s.work = off;
     const size_t phb = ((size_t)coef_slots(B) + PRE_N * B + B + 8) * sizeof(T);
     const size_t phc = (size_t)(B + 4) * sizeof(T);
-    s.total = off + (phb > phc ? phb : phc);
+    size_t w = phb > phc ? phb : phc;
+    w = w > kRingBytes ? w : kRingBytes;
+    s.total = off + w;
     return s;
 }
 
@@ -229,25 +237,118 @@ template <> struct V16<double> { using type = double2; static const int n = 2; }
 __device__ __forceinline__ float vget(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 __device__ __forceinline__ double vget(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
 
-// Sum of NV per-thread values over the CTA, in double, in a fixed order; results in r[]
-// (valid in every thread).  red: shared scratch of kThreads / 32 * NV doubles.
-template <int NV>
-__device__ void cta_sums(double *v, double *red, double *r) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+// Per-warp sums of ND per-thread values, written to red[warp][d] (shared); after a
+// __syncthreads, cta_total(red, d) adds the warps' sums in double, in a fixed order.
+template <typename T, int ND>
+__device__ __forceinline__ void warp_partials(const T (&v)[ND], double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < NV; k++) v[k] = warp_sum(v[k]);
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; k++) red[warp * NV + k] = v[k];
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < NV; k++) {
-        double s = 0.0;
-        for (int w = 0; w < nw; w++) s += red[w * NV + k];
-        r[k] = s;
+    for (int d = 0; d < ND; d++) {
+        const T w = warp_sum(v[d]);
+        if (lane == 0) red[warp * ND + d] = (double)w;
     }
-    __syncthreads();
+}
+
+template <int ND>
+__device__ __forceinline__ double cta_total(const double *red, int d) {
+    double s[kWarps];
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) s[w] = red[w * ND + d];
+#pragma unroll
+    for (int h = kWarps / 2; h > 0; h /= 2)  // pairwise: three dependent additions, not seven
+#pragma unroll
+        for (int w = 0; w < h; w++) s[w] += s[w + h];
+    return s[0];
+}
+
+// ---------------------------------------------------------------------------------
+// Phase A dot products from shared memory.  The rows that one CTA's dot products read
+// (kRingRows at most) are brought into shared memory in column chunks by bulk copies,
+// kStages chunks ahead, so that an SM keeps kStages x rows x kChunkBytes in flight rather
+// than the few loads per thread its warps would have outstanding.
+// ---------------------------------------------------------------------------------
+
+template <typename T, int ND>
+struct DotPlan {
+    const T *rows[kRingRows];  // row bases, 16-byte aligned (read by thread 0)
+    int nrows;
+    int ia[ND], ib[ND];        // dot product d = rows[ia[d]] . rows[ib[d]]
+};
+
+// Per-thread partial sums acc[d] of the plan's dot products over columns [0, len), with
+// len * sizeof(T) a multiple of 16.  Every thread of the CTA calls it.  A copy that does
+// not land within the wait limit makes the whole CTA give up (false, err set), after
+// thread 0 has waited, again with a limit, for the copies it still has in flight.
+template <typename T, int ND>
+__device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
+                          unsigned char *ring, uint64_t *mb, uint32_t &phase, int *err) {
+    constexpr int CW = kChunkBytes / (int)sizeof(T);
+    using VT = typename V16<T>::type;
+    constexpr int VN = V16<T>::n;
+    const int64_t nch = (len + CW - 1) / CW;
+    int64_t issued = 0;  // chunks issued (thread 0)
+    auto issue = [&](int64_t c) {
+        const int st = (int)(c % kStages);
+        const int64_t c0 = c * CW;
+        const int64_t n = (len - c0) < CW ? (len - c0) : CW;
+        const uint32_t bytes = (uint32_t)(n * (int64_t)sizeof(T));
+        T *dst = reinterpret_cast<T *>(ring + (size_t)st * kRingRows * kChunkBytes);
+        mbar_expect_tx(&mb[st], bytes * (uint32_t)pl.nrows);
+        for (int r = 0; r < pl.nrows; r++)
+            bulk_load(dst + (size_t)r * CW, pl.rows[r] + c0, bytes, &mb[st]);
+    };
+    int oa[ND], ob[ND];  // the operands' offsets in a stage, in 16-byte words
+#pragma unroll
+    for (int d = 0; d < ND; d++) {
+        acc[d] = T(0);
+        oa[d] = pl.ia[d] * (CW / VN);
+        ob[d] = pl.ib[d] * (CW / VN);
+    }
+    if (threadIdx.x == 0) {
+        // the ring was last read (and the rows possibly written) through the generic proxy
+        fence_proxy_async();
+        for (; issued < nch && issued < kStages; issued++) issue(issued);
+    }
+    for (int64_t c = 0; c < nch; c++) {
+        const int st = (int)(c % kStages);
+        const bool ok = mbar_wait(&mb[st], (phase >> st) & 1u, err);
+        if (ok) {
+            phase ^= 1u << st;
+            const VT *src = reinterpret_cast<const VT *>(ring + (size_t)st * kRingRows * kChunkBytes);
+            const int64_t c0 = c * CW;
+            const int nv = (int)(((len - c0) < CW ? (len - c0) : CW) / VN);
+            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+#pragma unroll
+                for (int d = 0; d < ND; d++) {
+                    const VT x = src[oa[d] + v];
+                    const VT y = src[ob[d] + v];
+#pragma unroll
+                    for (int k = 0; k < VN; k++) acc[d] = fma(vget(x, k), vget(y, k), acc[d]);
+                }
+            }
+        }
+        if (!__syncthreads_and(ok)) {
+            if (threadIdx.x == 0)
+                for (int64_t c2 = ok ? c + 1 : c; c2 < issued; c2++) {
+                    const int s2 = (int)(c2 % kStages);
+                    if (!mbar_wait(&mb[s2], (phase >> s2) & 1u, err, false)) break;
+                    phase ^= 1u << s2;
+                }
+            __syncthreads();
+            return false;
+        }
+        if (threadIdx.x == 0 && issued < nch) {  // stage st is free again
+            fence_proxy_async();
+            issue(issued);
+            issued++;
+        }
+    }
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ bool aligned16(const T *p) {
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
 }
 
 // Load the coordinates of the batch [s, s + nb) into shared memory and find its segments
@@ -325,9 +426,10 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                     double lam_off, double lam_diag, double *D, T *Ut, int B_arg,
                     SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_red[(kThreads / 32) * 6];
+    __shared__ double s_red[kWarps * 6];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
-    uint32_t mb_phase = 0;
+    __shared__ uint64_t s_ring[kStages];  // phase A ring
+    uint32_t mb_phase = 0, ring_phase = 0;
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
     const SmemLayout L = smem_layout<T>(B);
@@ -341,9 +443,9 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
     const int64_t rows_per = (q + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
-    using VT = typename V16<T>::type;
-    constexpr int VN = V16<T>::n;
-    const bool vec = (q % VN) == 0;
+    // phase A reads rows through the ring when bulk copies can address them
+    const bool use_ring = ((q * (int64_t)sizeof(T)) % 16) == 0 && aligned16(Sig) &&
+                          aligned16(Psi) && aligned16(Ut);
     const int64_t nbatch = (m + B - 1) / B;
     if (nbatch == 0) return;
 
@@ -381,77 +483,88 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             const bool two = lb < nb;
             const int64_t i0 = bm.sa[l], j0 = bm.sb[l];
             const int64_t i1 = two ? bm.sa[lb] : i0, j1 = two ? bm.sb[lb] : j0;
+            // thread 0 finishes coordinate l, thread 32 coordinate lb; the scalars they need
+            // are loaded first, so that their latency hides behind the dot products
+            const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
+            const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
+            double sij = 0.0, pij = 0.0, gij = 0.0, cij = 0.0;
+            double sdi = 0.0, sdj = 0.0, pdi = 0.0, pdj = 0.0;
+            if (which >= 0) {
+                sij = (double)Sig[ii * q + jj];
+                pij = (double)Psi[ii * q + jj];
+                gij = G[ii * q + jj];
+                cij = Lam[ii * q + jj];
+                sdi = Sd[ii];
+                sdj = Sd[jj];
+                pdi = Pd[ii];
+                pdj = Pd[jj];
+            }
             // (Sigma D Sigma)_ij = Sigma_i . U_{:,j}, (Psi D Sigma)_ij = Psi_i . U_{:,j},
-            // (Psi D Sigma)_ji = Psi_j . U_{:,i}
-            const T *x0 = Sig + i0 * q, *x1 = Psi + i0 * q, *x2 = Psi + j0 * q;
-            const T *y0 = Ut + j0 * q, *y1 = Ut + i0 * q;
-            const T *z0 = Sig + i1 * q, *z1 = Psi + i1 * q, *z2 = Psi + j1 * q;
-            const T *w0 = Ut + j1 * q, *w1 = Ut + i1 * q;
-            T a0 = T(0), a1 = T(0), a2 = T(0), b0 = T(0), b1 = T(0), b2 = T(0);
-            if (vec) {
-                const int64_t nv = q / VN;
-#pragma unroll 4
-                for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
-                    const VT X0 = reinterpret_cast<const VT *>(x0)[v];
-                    const VT X1 = reinterpret_cast<const VT *>(x1)[v];
-                    const VT X2 = reinterpret_cast<const VT *>(x2)[v];
-                    const VT Y0 = __ldcg(reinterpret_cast<const VT *>(y0) + v);
-                    const VT Y1 = __ldcg(reinterpret_cast<const VT *>(y1) + v);
-#pragma unroll
-                    for (int k = 0; k < VN; k++) {
-                        a0 = fma(vget(X0, k), vget(Y0, k), a0);
-                        a1 = fma(vget(X1, k), vget(Y0, k), a1);
-                        a2 = fma(vget(X2, k), vget(Y1, k), a2);
-                    }
-                    if (two) {
-                        const VT Z0 = reinterpret_cast<const VT *>(z0)[v];
-                        const VT Z1 = reinterpret_cast<const VT *>(z1)[v];
-                        const VT Z2 = reinterpret_cast<const VT *>(z2)[v];
-                        const VT W0 = __ldcg(reinterpret_cast<const VT *>(w0) + v);
-                        const VT W1 = __ldcg(reinterpret_cast<const VT *>(w1) + v);
-#pragma unroll
-                        for (int k = 0; k < VN; k++) {
-                            b0 = fma(vget(Z0, k), vget(W0, k), b0);
-                            b1 = fma(vget(Z1, k), vget(W0, k), b1);
-                            b2 = fma(vget(Z2, k), vget(W1, k), b2);
-                        }
-                    }
-                }
+            // (Psi D Sigma)_ji = Psi_j . U_{:,i}; rows 0..4 serve coordinate l, and the
+            // second coordinate shares rows 0..2 when it lies in the same row of Lambda
+            DotPlan<T, 6> pl;
+            pl.rows[0] = Sig + i0 * q;
+            pl.rows[1] = Psi + i0 * q;
+            pl.rows[2] = Ut + i0 * q;
+            pl.rows[3] = Psi + j0 * q;
+            pl.rows[4] = Ut + j0 * q;
+            pl.ia[0] = 0; pl.ib[0] = 4;
+            pl.ia[1] = 1; pl.ib[1] = 4;
+            pl.ia[2] = 3; pl.ib[2] = 2;
+            if (!two) {
+                pl.nrows = 5;
+                pl.ia[3] = 0; pl.ib[3] = 4;
+                pl.ia[4] = 1; pl.ib[4] = 4;
+                pl.ia[5] = 3; pl.ib[5] = 2;
+            } else if (i1 == i0) {
+                pl.nrows = 7;
+                pl.rows[5] = Psi + j1 * q;
+                pl.rows[6] = Ut + j1 * q;
+                pl.ia[3] = 0; pl.ib[3] = 6;
+                pl.ia[4] = 1; pl.ib[4] = 6;
+                pl.ia[5] = 5; pl.ib[5] = 2;
             } else {
+                pl.nrows = 10;
+                pl.rows[5] = Sig + i1 * q;
+                pl.rows[6] = Psi + i1 * q;
+                pl.rows[7] = Ut + i1 * q;
+                pl.rows[8] = Psi + j1 * q;
+                pl.rows[9] = Ut + j1 * q;
+                pl.ia[3] = 5; pl.ib[3] = 9;
+                pl.ia[4] = 6; pl.ib[4] = 9;
+                pl.ia[5] = 8; pl.ib[5] = 7;
+            }
+            T acc[6];
+            if (use_ring) {
+                if (!ring_dots<T, 6>(pl, q, acc, work, s_ring, ring_phase, scr.err)) return;
+            } else {
+#pragma unroll
+                for (int d = 0; d < 6; d++) acc[d] = T(0);
                 for (int64_t t = threadIdx.x; t < q; t += blockDim.x) {
-                    const T u0 = __ldcg(y0 + t), u1 = __ldcg(y1 + t);
-                    a0 = fma(x0[t], u0, a0);
-                    a1 = fma(x1[t], u0, a1);
-                    a2 = fma(x2[t], u1, a2);
-                    if (two) {
-                        const T v0 = __ldcg(w0 + t), v1 = __ldcg(w1 + t);
-                        b0 = fma(z0[t], v0, b0);
-                        b1 = fma(z1[t], v0, b1);
-                        b2 = fma(z2[t], v1, b2);
-                    }
+                    T x[kRingRows];
+                    for (int r = 0; r < pl.nrows; r++) x[r] = __ldcg(pl.rows[r] + t);
+#pragma unroll
+                    for (int d = 0; d < 6; d++) acc[d] = fma(x[pl.ia[d]], x[pl.ib[d]], acc[d]);
                 }
             }
-            double v6[6] = {(double)a0, (double)a1, (double)a2, (double)b0, (double)b1, (double)b2};
-            double d[6];
-            cta_sums<6>(v6, s_red, d);
-            const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
+            warp_partials<T, 6>(acc, s_red);
+            __syncthreads();
             if (which >= 0) {
                 const int lw = which ? lb : l;
-                const int64_t i = which ? i1 : i0, j = which ? j1 : j0;
-                const double d0 = which ? d[3] : d[0], d1 = which ? d[4] : d[1],
-                             d2 = which ? d[5] : d[2];
+                const double d0 = cta_total<6>(s_red, 3 * which);
+                const double d1 = cta_total<6>(s_red, 3 * which + 1);
+                const double d2 = cta_total<6>(s_red, 3 * which + 2);
                 double a, bb, lam;
-                if (i != j) {
-                    const double sij = (double)Sig[i * q + j], pij = (double)Psi[i * q + j];
-                    a = sij * sij + Sd[i] * Sd[j] + Sd[i] * Pd[j] + Sd[j] * Pd[i] + 2.0 * sij * pij;
-                    bb = G[i * q + j] + d0 + d1 + d2;
+                if (ii != jj) {
+                    a = sij * sij + sdi * sdj + sdi * pdj + sdj * pdi + 2.0 * sij * pij;
+                    bb = gij + d0 + d1 + d2;
                     lam = lam_off;
                 } else {
-                    a = Sd[i] * Sd[i] + 2.0 * Sd[i] * Pd[i];
-                    bb = G[i * q + i] + d0 + 2.0 * d1;
+                    a = sdi * sdi + 2.0 * sdi * pdi;
+                    bb = gij + d0 + 2.0 * d1;
                     lam = lam_diag;
                 }
-                step_constants<T>(bb, a, Lam[i * q + j], lam, pre, B, lw);
+                step_constants<T>(bb, a, cij, lam, pre, B, lw);
             }
         }
         const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
@@ -476,6 +589,10 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
     };
 
     // prologue: phase A of batch 0 by every CTA; no correction from an earlier batch
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kStages; k++) mbar_init(&s_ring[k], 1);
+        mbar_init_fence();
+    }
     BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
     int nbk = (int)(m < B ? m : B);
     load_batch(ai, aj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
@@ -597,9 +714,10 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                    const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam,
                    T *dVt, int B_arg, SweepScratch scr) {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double s_red[(kThreads / 32) * 2];
+    __shared__ double s_red[kWarps * 2];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
-    uint32_t mb_phase = 0;
+    __shared__ uint64_t s_ring[kStages];  // phase A ring
+    uint32_t mb_phase = 0, ring_phase = 0;
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
     const SmemLayout L = smem_layout<T>(B);
@@ -613,10 +731,10 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
     const int64_t rows_per = (q + nblk - 1) / nblk;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
-    using VT = typename V16<T>::type;
     constexpr int VN = V16<T>::n;
     const int64_t nbatch = (m + B - 1) / B;
     if (nbatch == 0) return;
+    const bool use_ring = ((p * (int64_t)sizeof(T)) % 16) == 0 && aligned16(Sxx) && aligned16(dVt);
 
     // change of (S_xx Delta V)_ij per unit step of Theta_ab, times 2: 2 (S_xx)_{i a} Sigma_{j b}
     // (Sigma symmetric; read along row j, b varying fastest across threads)
@@ -628,48 +746,61 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                        int nbp, int rank0) {
         const int nA = (int)nblk - rank0, rank = (int)blockIdx.x - rank0;
         // rows of Delta V that can be nonzero: those at or before this batch's first row
+        // (the ring copies whole 16-byte words: entries beyond tmax are zero)
         const int64_t tmax = (int64_t)bm.sa[0] + 1;
+        const int64_t tlen = ((tmax + VN - 1) / VN) * VN < p ? ((tmax + VN - 1) / VN) * VN : p;
         for (int l = rank; l < nb; l += 2 * nA) {
             const int lb = l + nA;
             const bool two = lb < nb;
             const int64_t i0 = bm.sa[l], j0 = bm.sb[l];
             const int64_t i1 = two ? bm.sa[lb] : i0, j1 = two ? bm.sb[lb] : j0;
-            // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
-            const T *x0 = Sxx + i0 * p, *y0 = dVt + j0 * p, *x1 = Sxx + i1 * p, *y1 = dVt + j1 * p;
-            T a0 = T(0), a1 = T(0);
-            int64_t tv = 0;
-            if ((p % VN) == 0) {
-                const int64_t nv = tmax / VN;
-#pragma unroll 4
-                for (int64_t v = threadIdx.x; v < nv; v += blockDim.x) {
-                    const VT X0 = reinterpret_cast<const VT *>(x0)[v];
-                    const VT Y0 = __ldcg(reinterpret_cast<const VT *>(y0) + v);
-#pragma unroll
-                    for (int k = 0; k < VN; k++) a0 = fma(vget(X0, k), vget(Y0, k), a0);
-                    if (two) {
-                        const VT X1 = reinterpret_cast<const VT *>(x1)[v];
-                        const VT Y1 = __ldcg(reinterpret_cast<const VT *>(y1) + v);
-#pragma unroll
-                        for (int k = 0; k < VN; k++) a1 = fma(vget(X1, k), vget(Y1, k), a1);
-                    }
-                }
-                tv = nv * VN;
-            }
-            for (int64_t t = tv + threadIdx.x; t < tmax; t += blockDim.x) {
-                a0 = fma(x0[t], __ldcg(y0 + t), a0);
-                if (two) a1 = fma(x1[t], __ldcg(y1 + t), a1);
-            }
-            double v2[2] = {(double)a0, (double)a1};
-            double d[2];
-            cta_sums<2>(v2, s_red, d);
+            // thread 0 finishes coordinate l, thread 32 coordinate lb; their scalars first
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
+            const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
+            double wij = 0.0, cij = 0.0, xii = 0.0, sdj = 0.0;
+            if (which >= 0) {
+                wij = W[ii * q + jj];
+                cij = __ldcg(Theta + ii * q + jj);
+                xii = Xd[ii];
+                sdj = Sd[jj];
+            }
+            // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
+            DotPlan<T, 2> pl;
+            pl.rows[0] = Sxx + i0 * p;
+            pl.rows[1] = dVt + j0 * p;
+            pl.ia[0] = 0; pl.ib[0] = 1;
+            if (!two) {
+                pl.nrows = 2;
+                pl.ia[1] = 0; pl.ib[1] = 1;
+            } else if (i1 == i0) {
+                pl.nrows = 3;
+                pl.rows[2] = dVt + j1 * p;
+                pl.ia[1] = 0; pl.ib[1] = 2;
+            } else {
+                pl.nrows = 4;
+                pl.rows[2] = Sxx + i1 * p;
+                pl.rows[3] = dVt + j1 * p;
+                pl.ia[1] = 2; pl.ib[1] = 3;
+            }
+            T acc[2];
+            if (use_ring) {
+                if (!ring_dots<T, 2>(pl, tlen, acc, work, s_ring, ring_phase, scr.err)) return;
+            } else {
+                acc[0] = acc[1] = T(0);
+                for (int64_t t = threadIdx.x; t < tmax; t += blockDim.x) {
+                    T x[4];
+                    for (int r = 0; r < pl.nrows; r++) x[r] = __ldcg(pl.rows[r] + t);
+                    acc[0] = fma(x[pl.ia[0]], x[pl.ib[0]], acc[0]);
+                    acc[1] = fma(x[pl.ia[1]], x[pl.ib[1]], acc[1]);
+                }
+            }
+            warp_partials<T, 2>(acc, s_red);
+            __syncthreads();
             if (which >= 0) {
                 const int lw = which ? lb : l;
-                const int64_t i = which ? i1 : i0, j = which ? j1 : j0;
-                const double xii = Xd[i];
-                const double a = (xii != 0.0) ? 2.0 * Sd[j] * xii : 0.0;
-                step_constants<T>(2.0 * W[i * q + j] + 2.0 * d[which], a,
-                                  __ldcg(Theta + i * q + j), lam, pre, B, lw);
+                const double d = cta_total<2>(s_red, which);
+                const double a = (xii != 0.0) ? 2.0 * sdj * xii : 0.0;
+                step_constants<T>(2.0 * wij + 2.0 * d, a, cij, lam, pre, B, lw);
             }
         }
         const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
@@ -693,6 +824,10 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
         }
     };
 
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kStages; k++) mbar_init(&s_ring[k], 1);
+        mbar_init_fence();
+    }
     BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
     int nbk = (int)(m < B ? m : B);
     load_batch(ti, tj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);

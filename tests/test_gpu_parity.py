@@ -154,6 +154,42 @@ def test_theta_sweep(ctx, shape, prec, tol):
     assert rel(T, T_ref) < tol
 
 
+@pytest.mark.parametrize("prec,tol", [(0, 1e-9), (1, 2e-4)])
+@pytest.mark.parametrize("length", [1032, 1030])
+def test_sweeps_long_rows(ctx, prec, tol, length):
+    """Rows longer than one shared-memory chunk of the dot-product ring (1032 entries: several
+    chunks in float and in double), and a row length that is not a whole number of 16-byte
+    words (1030: direct loads instead of bulk copies)."""
+    def inputs(p, q, seed):
+        # the true parameters, scaled, stand in for an interior iterate (an oracle solve at
+        # these sizes would take longer than the check itself)
+        pr = problem(p, q, 40, seed=seed)
+        Lam = pr.Lambda_true.toarray()
+        Th = 0.5 * pr.Theta_true.toarray()
+        Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+        G_L, G_T, Sigma, Psi = oracle.gradients(Lam, Th, Sxx, Sxy, Syy)
+        return pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi
+
+    q = length
+    pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi = inputs(24, q, 5)
+    iu, ju = np.triu_indices(q)
+    keep = (iu < 2) | ((iu == ju) & (iu % 97 == 0)) | ((iu == q - 3) & (ju > q - 40))
+    li, lj = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+    D_ref = oracle.lambda_sweep(Sigma, Psi, Syy, Lam, li, lj, 0.05)
+    D = ctx.cggm_lambda_sweep(Sigma, Psi, Syy, Lam, li, lj, 0.05, precision=prec)
+    assert np.abs(D_ref).max() > 0
+    assert rel(D, D_ref) < tol
+    p = length
+    pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi = inputs(p, 24, 6)
+    rows = np.array([0, 3, p - 7, p - 1])
+    ti = np.repeat(rows, 24).astype(np.int32)
+    tj = np.tile(np.arange(24), rows.size).astype(np.int32)
+    T_ref = oracle.theta_sweep(Sxx, Sxy, Sigma, Th, ti, tj, 0.02)
+    T = ctx.cggm_theta_sweep(pr.X, Sxy, Sigma, Th, ti, tj, 0.02, precision=prec)
+    assert np.abs(T_ref - Th).max() > 0
+    assert rel(T, T_ref) < tol
+
+
 def test_sweeps_with_empty_active_set(ctx):
     pr, Lam, Th, Sxx, Sxy, Syy, Sigma, Psi, _, _, _, _ = lambda_inputs(20, 10, 15, seed=2)
     e = np.zeros(0, dtype=np.int32)
