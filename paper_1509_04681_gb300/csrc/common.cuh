@@ -57,8 +57,7 @@ inline void note_launch() { __atomic_add_fetch(&launch_counter(), 1, __ATOMIC_RE
 // waiter also leaves as soon as the error word is nonzero.  Returns false on error.
 // ---------------------------------------------------------------------------------
 struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
+    unsigned long long arrived;  // arrivals since the launch (zeroed before it); monotonic
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -67,48 +66,48 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ int ld_acquire_int(const int *p) {
     int v;
     asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
+// Grid-wide barrier of a cooperative launch.  Every CTA adds one to a counter that only
+// grows; the CTAs of round r wait until it reaches (r + 1) nblocks, where r follows from the
+// value the CTA's own addition returned (no CTA can arrive at round r + 1 before all have
+// arrived at round r).  One L2 round trip per CTA plus the time for the last arrival to be
+// seen.  A wait that exceeds deadline_ns, or sees another CTA's error, returns false (and
+// records DEV_TIMEOUT in the first case).
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int *err, unsigned nblocks,
                                           uint64_t deadline_ns = 2000000000ull) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
-        const unsigned g = ld_acquire(&bar->gen);
-        __threadfence();
-        const unsigned arrived = atomicAdd(&bar->count, 1u);
+        __threadfence();  // this CTA's writes before its arrival
+        const unsigned long long old = atomicAdd(&bar->arrived, 1ull);
+        const unsigned long long target = (old / nblocks + 1) * nblocks;
         int ok = 1;
-        if (arrived == nblocks - 1) {
-            bar->count = 0;
-            __threadfence();
-            st_release(&bar->gen, g + 1);
-        } else {
+        if (old + 1 != target) {
             const uint64_t t0 = global_ns();
             unsigned spins = 0;
-            while (ld_acquire(&bar->gen) == g) {
-                if (ld_acquire_int(err) != 0) { ok = 0; break; }
-                if ((++spins & 63u) == 0 && global_ns() - t0 > deadline_ns) {
-                    atomicCAS(err, 0, (int)DEV_TIMEOUT);
-                    ok = 0;
-                    break;
+            while (ld_acquire_u64(&bar->arrived) < target) {
+                if ((++spins & 63u) == 0) {
+                    if (ld_acquire_int(err) != 0) { ok = 0; break; }
+                    if (global_ns() - t0 > deadline_ns) {
+                        atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(64);
             }
         }
+        __threadfence();  // the other CTAs' writes before this CTA's later reads
         if (ok && ld_acquire_int(err) != 0) ok = 0;
         s_ok = ok;
     }

@@ -35,7 +35,7 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 // Phase C: each warp updates this many cache rows at once, their loads all issued before
 // the first use, so that the L2 round trips of different rows overlap.
-constexpr int kRowsInFlight = 4;
+constexpr int kRowsInFlight = 5;
 // Phase A: rows per CTA held at once, chunks in flight, bytes per row and chunk.
 constexpr int kRingRows = 10;
 constexpr int kStages = 3;
@@ -400,20 +400,28 @@ __device__ __forceinline__ BatchMeta meta_at(unsigned char *base, int B, int whi
     return BatchMeta{p, p + B, p + 2 * B, p + 3 * B + 1};
 }
 
-// corr[l] = sum_{l'} X[l][l'] mu[l'] for l < nbn (one warp per coordinate over the grid)
-template <typename T>
-__device__ void cross_corrections(int nbn, int nbk, int B, const T *X, const double *mu,
+// corr[l] = sum_{l'} X[l][l'] mu[l'] for l < nbn, one warp per coordinate over the grid;
+// the row of X of this warp's first coordinate (l = its global warp index) was loaded into
+// xw before the cache update, so that its latency overlapped that update.  The corrections
+// of padding coordinates are zeroed.
+template <typename T, int NS>
+__device__ void cross_corrections(int nbn, int nbk, const T *X, const T *smu, const T (&xw)[NS],
                                   T *corr) {
+    constexpr int B = NS * 32;
     const int lane = threadIdx.x & 31;
-    const int warps = (int)(gridDim.x * (blockDim.x >> 5));
-    for (int l = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)); l < nbn; l += warps) {
+    const int gw = (int)(blockIdx.x * kWarps + (threadIdx.x >> 5));
+    const int gwarps = (int)(gridDim.x * kWarps);
+    for (int l = gw; l < nbn; l += gwarps) {
         T acc = T(0);
-        for (int l1 = lane; l1 < nbk; l1 += 32)
-            acc = fma(__ldcg(X + (size_t)l * B + l1), (T)__ldcg(mu + l1), acc);
+#pragma unroll
+        for (int kk = 0; kk < NS; kk++) {
+            const int l1 = lane + 32 * kk;
+            if (l1 < nbk) acc = fma(l == gw ? xw[kk] : __ldcg(X + (size_t)l * B + l1), smu[l1], acc);
+        }
         acc = warp_sum(acc);
         if (lane == 0) corr[l] = acc;
     }
-    if (blockIdx.x == gridDim.x - 1)  // padding coordinates of the next batch
+    if (blockIdx.x == gridDim.x - 1)
         for (int l = nbn + threadIdx.x; l < B; l += blockDim.x) corr[l] = T(0);
 }
 
@@ -639,6 +647,15 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                 }
             }
             __syncthreads();
+            T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
+            {
+                const int gw = (int)(blockIdx.x * kWarps + warp);
+#pragma unroll
+                for (int kk = 0; kk < NS; kk++) {
+                    const int l1 = lane + 32 * kk;
+                    xw[kk] = (gw < nbn && l1 < nbk) ? __ldcg(gX + (size_t)gw * B + l1) : T(0);
+                }
+            }
             const int nseg = *cur.snseg;
             constexpr int R = kRowsInFlight;
             for (int g = 0; g < nseg; g++) {
@@ -692,7 +709,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                 }
                 __syncwarp();  // this segment's writes before the next segment's reads
             }
-            if (nbn > 0) cross_corrections<T>(nbn, nbk, B, gX, scr.mu, gcorr);
+            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr);
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
         BatchMeta tmp = cur;
@@ -870,6 +887,15 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                 }
             }
             __syncthreads();
+            T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
+            {
+                const int gw = (int)(blockIdx.x * kWarps + warp);
+#pragma unroll
+                for (int kk = 0; kk < NS; kk++) {
+                    const int l1 = lane + 32 * kk;
+                    xw[kk] = (gw < nbn && l1 < nbk) ? __ldcg(gX + (size_t)gw * B + l1) : T(0);
+                }
+            }
             const int nseg = *cur.snseg;
             constexpr int R = kRowsInFlight;
             for (int g = 0; g < nseg; g++) {
@@ -907,7 +933,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                     }
                 }
             }
-            if (nbn > 0) cross_corrections<T>(nbn, nbk, B, gX, scr.mu, gcorr);
+            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr);
         }
         if (!grid_sync(scr.bar, scr.err, nblk)) return;
         BatchMeta tmp = cur;
