@@ -52,7 +52,7 @@ potrf_diag_kernel(double *A, int64_t lda, int64_t k0, int nb, double *logd, int 
     if (tid == 0 && s_bad) atomicCAS(err, 0, (int)DEV_NOTPD);
 }
 
-// Rows r >= r0 of the panel A[:, k0:k0+nb] <- A[r, k0:k0+nb] L_kk^-T  (solve L x = a per row)
+// Rows r0 <= r < n of the panel A[:, k0:k0+nb] <- A[r, k0:k0+nb] L_kk^-T (solve L x = a per row)
 __global__ void __launch_bounds__(128)
 trsm_panel_kernel(int64_t n, double *A, int64_t lda, int64_t k0, int nb, int64_t r0) {
     __shared__ double L[NB][NB + 1];
@@ -140,21 +140,73 @@ inline unsigned grid_cap(int64_t len) {
 }
 }  // namespace
 
+// Recursive forms: every level halves the problem (at a multiple of NB) and does the
+// off-diagonal work as one GEMM, so that most of the flops run in a few large GEMMs rather
+// than in n / NB thin ones (a 64-row GEMM fills a fraction of the GPU).
+namespace {
+int64_t split_at(int64_t n) {
+    const int64_t h = (n / 2 / NB) * NB;
+    return h < NB ? NB : h;
+}
+
+// X L^T = A[r0:r1, c0:c0+w] in place, with L = A[c0:c0+w, c0:c0+w] (lower, factored).
+void trsm_right_rec(int64_t r0, int64_t r1, int64_t c0, int64_t w, double *A, int64_t lda,
+                    cudaStream_t st) {
+    if (r1 <= r0) return;
+    if (w <= NB) {
+        note_launch();
+        trsm_panel_kernel<<<ceil_div(r1 - r0, 128), 128, 0, st>>>(r1, A, lda, c0, (int)w, r0);
+        return;
+    }
+    const int64_t w1 = split_at(w);
+    trsm_right_rec(r0, r1, c0, w1, A, lda, st);
+    // A[r0:r1, c0+w1 : c0+w] -= X1 L21^T
+    gemm<double>(false, true, r1 - r0, w - w1, w1, -1.0, A + r0 * lda + c0, lda,
+                 A + (c0 + w1) * lda + c0, lda, 1.0, A + r0 * lda + c0 + w1, lda, st);
+    trsm_right_rec(r0, r1, c0 + w1, w - w1, A, lda, st);
+}
+
+// Factor A[k0:k0+n, k0:k0+n] (updates from the columns before k0 already applied).
+void chol_rec(int64_t k0, int64_t n, double *A, int64_t lda, double *logd, int *err,
+              cudaStream_t st) {
+    if (n <= NB) {
+        note_launch();
+        potrf_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, (int)n, logd, err);
+        return;
+    }
+    const int64_t n1 = split_at(n), k1 = k0 + n1, k2 = k0 + n;
+    chol_rec(k0, n1, A, lda, logd, err, st);
+    trsm_right_rec(k1, k2, k0, n1, A, lda, st);  // L21 = A21 L11^-T
+    // A22 -= L21 L21^T (lower triangle)
+    gemm<double>(false, true, k2 - k1, k2 - k1, n1, -1.0, A + k1 * lda + k0, lda,
+                 A + k1 * lda + k0, lda, 1.0, A + k1 * lda + k1, lda, st, /*tri=*/1);
+    chol_rec(k1, n - n1, A, lda, logd, err, st);
+}
+
+// Rows [r0, r0 + n) of B <- L^-1 B, the rows before r0 solved and applied.  With tri the
+// right-hand side (and solution) is lower triangular: row i has no nonzero beyond column i.
+void trsm_left_rec(int64_t r0, int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb,
+                   int64_t ncols, bool tri, cudaStream_t st) {
+    const int64_t nc = tri ? ((r0 + n) < ncols ? (r0 + n) : ncols) : ncols;
+    if (n <= NB) {
+        note_launch();
+        trsv_block_kernel<<<ceil_div(nc, 128), 128, 0, st>>>(L, ldl, r0, (int)n, B, ldb, nc);
+        return;
+    }
+    const int64_t n1 = split_at(n);
+    trsm_left_rec(r0, n1, L, ldl, B, ldb, ncols, tri, st);
+    const int64_t nc1 = tri ? ((r0 + n1) < ncols ? (r0 + n1) : ncols) : ncols;
+    // B[r0+n1 : r0+n] -= L[r0+n1 : r0+n, r0 : r0+n1] X[r0 : r0+n1]
+    gemm<double>(false, false, n - n1, nc1, n1, -1.0, L + (r0 + n1) * ldl + r0, ldl,
+                 B + r0 * ldb, ldb, 1.0, B + (r0 + n1) * ldb, ldb, st);
+    trsm_left_rec(r0 + n1, n - n1, L, ldl, B, ldb, ncols, tri, st);
+}
+}  // namespace
+
 void cholesky_inplace(int64_t n, double *A, int64_t lda, double *logd, int *err,
                       cudaStream_t st) {
-    for (int64_t k0 = 0; k0 < n; k0 += NB) {
-        const int nb = (int)((n - k0) < NB ? (n - k0) : NB);
-        note_launch();
-        potrf_diag_kernel<<<1, 256, 0, st>>>(A, lda, k0, nb, logd, err);
-        const int64_t k1 = k0 + nb;
-        if (k1 < n) {
-            note_launch();
-            trsm_panel_kernel<<<ceil_div(n - k1, 128), 128, 0, st>>>(n, A, lda, k0, nb, k1);
-            // trailing lower update A[k1:, k1:] -= P P^T with P = A[k1:, k0:k1]
-            gemm<double>(false, true, n - k1, n - k1, nb, -1.0, A + k1 * lda + k0, lda,
-                         A + k1 * lda + k0, lda, 1.0, A + k1 * lda + k1, lda, st, /*tri=*/1);
-        }
-    }
+    if (n <= 0) return;
+    chol_rec(0, n, A, lda, logd, err, st);
     note_launch();
     zero_upper_kernel<<<grid_cap(n * n), 256, 0, st>>>(n, A, lda);
 }
@@ -166,17 +218,8 @@ void logdet_from_logd(int64_t n, const double *logd, double *out, cudaStream_t s
 
 void trsm_lower_inplace(int64_t n, const double *L, int64_t ldl, double *B, int64_t ldb,
                         int64_t ncols, bool lower_tri_rhs, cudaStream_t st) {
-    for (int64_t i0 = 0; i0 < n; i0 += NB) {
-        const int rb = (int)((n - i0) < NB ? (n - i0) : NB);
-        // columns that can be nonzero in this row block of the solution: when the
-        // right-hand side is lower triangular (inverse), only c < i0 + rb
-        const int64_t nc = lower_tri_rhs ? ((i0 + rb) < ncols ? (i0 + rb) : ncols) : ncols;
-        if (i0 > 0)
-            gemm<double>(false, false, rb, nc, i0, -1.0, L + i0 * ldl, ldl, B, ldb, 1.0,
-                         B + i0 * ldb, ldb, st);
-        note_launch();
-        trsv_block_kernel<<<ceil_div(nc, 128), 128, 0, st>>>(L, ldl, i0, rb, B, ldb, nc);
-    }
+    if (n <= 0 || ncols <= 0) return;
+    trsm_left_rec(0, n, L, ldl, B, ldb, ncols, lower_tri_rhs, st);
 }
 
 void inverse_from_cholesky(int64_t n, const double *L, double *Sigma, double *work,
