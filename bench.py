@@ -37,6 +37,32 @@ SMALL = "chain-gauss-p200-q100-n100"
 METRIC = "time to 1e-6 rel obj gap, mixed vs FP64 GPU; λ-path solves/s, p50/p99"
 
 
+SWEEP_SOURCES = ["paper_1509_04681_gb300/csrc/sweeps.cu", "paper_1509_04681_gb300/csrc/sweeps.cuh",
+                 "paper_1509_04681_gb300/csrc/common.cuh", "paper_1509_04681_gb300/csrc/mbar.cuh"]
+
+
+def profiled_traffic(kernel, units):
+    """DRAM bytes (read + write) of one launch of `kernel` over `units` coordinates, scaled
+    from the committed ncu summary of a bounded launch of the same kernel; None when there
+    is none, or when the kernel sources no longer hash to the captured version."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"{kernel}-q5000-bounded.md")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if line.startswith("    ") and ":" in line:
+            k, v = line.strip().split(":", 1)
+            kv[k.strip()] = v.strip()
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    if kv.get("kernel") != kernel or kv.get("source_sha256") != h.hexdigest():
+        return None
+    return float(kv["dram_bytes"]) / float(kv["units"]) * units
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -380,8 +406,10 @@ def run_cuda(args):
         kname, kbytes, ksec = "theta_sweep_kernel", th_bytes, info["sec_sweep_theta"]
         per_unit = f"(2 p + 3 q) x {esz} B per Theta coordinate"
     achieved = kbytes / ksec / 1e9 if ksec > 0 else 0.0
+    units = info["coords_lambda" if kname == "lambda_sweep_kernel" else "coords_theta"]
+    traffic = profiled_traffic(kname, units / max(1, iters))  # per launch (one per iteration)
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+            "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
             "peak_source": src, "algorithmic_bytes": per_unit,
             "launch_seconds": ksec / max(1, iters), "share_of_step": ksec / sec}
 
