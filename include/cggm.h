@@ -53,7 +53,13 @@ typedef enum {
                     /* and Psi diagonals and coordinate coefficients in double          */
 } cggm_precision;
 
-typedef enum { CGGM_F32 = 0, CGGM_F64 = 1 } cggm_dtype;
+/* Element types of X and Y (row-major n x p, n x q).  CGGM_BF16: bfloat16 values, used as
+ * they are.  CGGM_I8_GENO (X only): int8 values, typically genotype counts {0, 1, 2}; the
+ * library standardises every column with its mean and population standard deviation over
+ * the n rows, (x - mean) / sd in double, so that diag(S_xx) = 1 (a constant column becomes
+ * zero, and its Theta row stays zero).  The paper does not fix the storage; its genomic
+ * inputs are genotype counts (Section 5.2). */
+typedef enum { CGGM_F32 = 0, CGGM_F64 = 1, CGGM_BF16 = 2, CGGM_I8_GENO = 3 } cggm_dtype;
 
 typedef struct {
     double tol;          /* stopping ratio of Section 5.1: stop when

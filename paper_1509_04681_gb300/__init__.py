@@ -16,6 +16,10 @@ from .cggm import (  # noqa: F401
     LIB_PATH,
     EXPORTED,
     CGGM_FP64,
+    CGGM_F32,
+    CGGM_F64,
+    CGGM_BF16,
+    CGGM_I8_GENO,
     CGGM_MIXED,
     CGGM_OK,
     CGGM_EMAXITER,

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libcggm.so")
 CGGM_OK, CGGM_EINVAL, CGGM_ENOTPD, CGGM_ENOMEM, CGGM_EMAXITER = 0, -1, -2, -3, -4
 CGGM_ELINESEARCH, CGGM_ECUDA, CGGM_ETIMEDOUT, CGGM_ENONFINITE, CGGM_ECANCELLED = -5, -6, -7, -8, -9
 CGGM_FP64, CGGM_MIXED = 0, 1
-CGGM_F32, CGGM_F64 = 0, 1
+CGGM_F32, CGGM_F64, CGGM_BF16, CGGM_I8_GENO = 0, 1, 2, 3
 
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
@@ -147,8 +147,9 @@ class _Arr:
         try:
             import torch
             if isinstance(a, torch.Tensor):
-                tdt = {np.float64: torch.float64, np.float32: torch.float32,
-                       np.int32: torch.int32}[np.dtype(dtype).type]
+                tdt = torch.bfloat16 if dtype == "bf16" else {
+                    np.float64: torch.float64, np.float32: torch.float32, np.int32: torch.int32,
+                    np.int8: torch.int8}[np.dtype(dtype).type]
                 t = a.to(dtype=tdt).contiguous()
                 self.obj = t
                 self.ptr = t.data_ptr()
@@ -161,13 +162,18 @@ class _Arr:
 
 
 def _x_dtype(a):
+    """(element type, cggm_dtype) of an input matrix: float32, float64, bfloat16 (torch
+    tensors) and int8 (genotype counts, standardised by the library) pass through as they
+    are; anything else is converted to float64."""
     try:
         import torch
         if isinstance(a, torch.Tensor):
-            return (np.float32, CGGM_F32) if a.dtype == torch.float32 else (np.float64, CGGM_F64)
+            return {torch.float32: (np.float32, CGGM_F32), torch.bfloat16: ("bf16", CGGM_BF16),
+                    torch.int8: (np.int8, CGGM_I8_GENO)}.get(a.dtype, (np.float64, CGGM_F64))
     except ImportError:
         pass
-    return (np.float32, CGGM_F32) if np.asarray(a).dtype == np.float32 else (np.float64, CGGM_F64)
+    return {np.dtype(np.float32): (np.float32, CGGM_F32), np.dtype(np.int8): (np.int8, CGGM_I8_GENO)}.get(
+        np.asarray(a).dtype, (np.float64, CGGM_F64))
 
 
 def opts_default() -> cggm_opts:

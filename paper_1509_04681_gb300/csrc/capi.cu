@@ -11,6 +11,7 @@
 #include "dense.cuh"
 #include "gemm_tc.cuh"
 #include "iter.cuh"
+#include "load.cuh"
 #include "sweeps.cuh"
 
 using namespace cggm;
@@ -58,7 +59,7 @@ struct cggm_ctx {
     cudaStream_t st = nullptr;
     bool own_stream = false;
     // data
-    Buf stage, Xt, Yt, Xt_f, Syy, Sxy, Sxx, Xd;
+    Buf stage, Xt, Yt, Xt_f, Syy, Sxy, Sxx, Xd, colstats;
     // parameters and factorisations
     Buf Lam, Th, Lch, logd, Sig, Sig_f, Sd, Lam_a, Lch_a, logd_a, work;
     // products and gradients
@@ -98,9 +99,17 @@ cggm_status read_dev_err(cggm_ctx *c, int *out) {
 
 // Copy a row-major rows x cols matrix of dtype dt (host or device) into a device double
 // matrix transposed (cols x rows).  Also optionally a float copy.
+// X may be any cggm_dtype; Y any but the genotype type (it is not standardised).
+bool dtypes_ok(int xdt, int ydt) {
+    const bool x = xdt == CGGM_F32 || xdt == CGGM_F64 || xdt == CGGM_BF16 || xdt == CGGM_I8_GENO;
+    const bool y = ydt == CGGM_F32 || ydt == CGGM_F64 || ydt == CGGM_BF16;
+    return x && y;
+}
+
 cggm_status load_transposed(cggm_ctx *c, const void *src, int dt, int64_t rows, int64_t cols,
                             Buf &dst, Buf *dst_f) {
-    const size_t esz = dt == CGGM_F64 ? 8 : 4;
+    const size_t esz = dtype_size(dt);
+    if (esz == 0) return CGGM_EINVAL;
     const size_t bytes = esz * (size_t)rows * (size_t)cols;
     const void *dsrc = src;
     if (!is_device_ptr(src)) {
@@ -109,10 +118,15 @@ cggm_status load_transposed(cggm_ctx *c, const void *src, int dt, int64_t rows, 
         dsrc = c->stage.p;
     }
     CGGM_TRY(ensure(dst, 8 * (size_t)rows * cols));
-    if (dt == CGGM_F64)
+    if (dt == CGGM_F64) {
         transpose<double, double>(rows, cols, (const double *)dsrc, P<double>(dst), c->st);
-    else
+    } else if (dt == CGGM_F32) {
         transpose<float, double>(rows, cols, (const float *)dsrc, P<double>(dst), c->st);
+    } else {
+        CGGM_TRY(ensure(c->colstats, 16 * (size_t)cols));
+        CGGM_TRY(load_input_transposed(dsrc, dt, rows, cols, P<double>(dst), P<double>(c->colstats),
+                                       c->st));
+    }
     if (dst_f) {
         CGGM_TRY(ensure(*dst_f, 4 * (size_t)rows * cols));
         convert_d2f(rows * cols, P<double>(dst), P<float>(*dst_f), c->st);
@@ -701,7 +715,7 @@ void cggm_destroy(cggm_ctx *c) {
                    &c->Lam, &c->Th, &c->Lch, &c->logd, &c->Sig, &c->Sig_f, &c->Sd, &c->Lam_a,
                    &c->Lch_a, &c->logd_a, &c->work, &c->Rt, &c->Pt, &c->Z, &c->Psi, &c->Pd,
                    &c->GL, &c->GT, &c->W, &c->D, &c->U, &c->dV, &c->li, &c->lj, &c->ti,
-                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial,
+                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial, &c->colstats,
                    &c->tcA_hi, &c->tcA_lo, &c->tcB_hi, &c->tcB_lo, &c->Xt_hi, &c->Xt_lo,
                    &c->Sig_hi, &c->Sig_lo, &c->R_f, &c->R_hi, &c->R_lo, &c->Pt_f, &c->Pt_hi,
                    &c->Pt_lo, &c->Zf, &c->tcerr};
@@ -719,8 +733,7 @@ cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, in
     if (!c || !X || !Y) return CGGM_EINVAL;
     CGGM_TRY(check_sizes(n, p, q));
     if (!(lam_L >= 0.0) || !(lam_T >= 0.0)) return CGGM_EINVAL;
-    if ((xdtype != CGGM_F32 && xdtype != CGGM_F64) || (ydtype != CGGM_F32 && ydtype != CGGM_F64))
-        return CGGM_EINVAL;
+    if (!dtypes_ok(xdtype, ydtype)) return CGGM_EINVAL;
     cggm_opts o;
     if (opts) o = *opts; else cggm_opts_default(&o);
     if (tol > 0.0) o.tol = tol;
@@ -761,6 +774,7 @@ cggm_status cggm_objective(cggm_ctx *c, const void *X, int xdtype, const void *Y
                            const double *Theta, double lam_L, double lam_T, int penalize_diag,
                            double *f_out) {
     if (!c || !X || !Y || !Lambda || !Theta || !f_out) return CGGM_EINVAL;
+    if (!dtypes_ok(xdtype, ydtype)) return CGGM_EINVAL;
     CGGM_TRY(check_sizes(n, p, q));
     CGGM_TRY(set_device(c));
     CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
@@ -803,6 +817,7 @@ cggm_status cggm_grad(cggm_ctx *c, const void *X, int xdtype, const void *Y, int
                       int64_t n, int64_t p, int64_t q, const double *Lambda, const double *Theta,
                       double *G_Lambda, double *G_Theta) {
     if (!c || !X || !Y || !Lambda || !Theta) return CGGM_EINVAL;
+    if (!dtypes_ok(xdtype, ydtype)) return CGGM_EINVAL;
     CGGM_TRY(check_sizes(n, p, q));
     CGGM_TRY(set_device(c));
     CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "load.cuh"
 
 namespace {
 
@@ -78,8 +79,8 @@ int64_t footprint_bytes(int64_t n, int64_t p, int64_t q, int precision) {
 void cggm_server::run(Job *j, cggm_ctx *ctx) {
     const cggm_request &r = j->req;
     const int64_t n = r.n, p = r.p, q = r.q;
-    const size_t xs = (r.xdtype == CGGM_F64 ? 8 : 4) * (size_t)(n * p);
-    const size_t ys = (r.ydtype == CGGM_F64 ? 8 : 4) * (size_t)(n * q);
+    const size_t xs = cggm::dtype_size(r.xdtype) * (size_t)(n * p);
+    const size_t ys = cggm::dtype_size(r.ydtype) * (size_t)(n * q);
     void *dX = nullptr, *dY = nullptr;
     double *dL = nullptr, *dT = nullptr;
     cggm_status st = CGGM_OK;
@@ -205,6 +206,9 @@ cggm_status cggm_server_submit(cggm_server *s, const cggm_request *req, uint64_t
         req->n_lambda <= 0 || !req->lambdas || !(req->tol >= 0.0))
         return CGGM_EINVAL;
     if (req->precision != CGGM_FP64 && req->precision != CGGM_MIXED) return CGGM_EINVAL;
+    if (cggm::dtype_size(req->xdtype) == 0 || cggm::dtype_size(req->ydtype) == 0 ||
+        req->ydtype == CGGM_I8_GENO)
+        return CGGM_EINVAL;
     Job *j = new Job();
     j->req = *req;
     j->lambdas.assign(req->lambdas, req->lambdas + req->n_lambda);
