@@ -256,6 +256,25 @@ cggm_status cggm_contract(cggm_ctx *ctx, int64_t M, int64_t N, int64_t K, float 
                           const float *A, int64_t lda, const float *B, int64_t ldb, float beta,
                           float *C, int64_t ldc, int mode);
 
+/* Sparse symmetric positive definite solve by conjugate gradient.  Section 4 (the block
+ * regime of Algorithm 2) never forms Sigma = Lambda^-1 whole: it computes blocks of its
+ * columns by conjugate gradient on the sparse Lambda, and P = R Sigma through
+ * Lambda P^T = R^T.  This entry point solves Lambda X = B for k right-hand sides at once.
+ *   Lambda: q x q in CSR (row_ptr[q + 1] int64, col[nnz] int32, val[nnz] double; host or
+ *           device), symmetric positive definite, both triangles stored.
+ *   B:      q x k row-major double (host or device), or NULL for the identity columns
+ *           c0 .. c0 + k - 1 (then X = Sigma[:, c0 : c0 + k]; 0 <= c0, c0 + k <= q).
+ *   X:      q x k row-major double output (host or device).
+ * Jacobi-preconditioned CG in double, all k columns advancing together; stops when every
+ * column's residual norm is <= tol times its right-hand side's norm (tol > 0), or after
+ * max_iter iterations (CGGM_EMAXITER; X holds the last iterate).  iters_out, resid_out
+ * (optional): iterations run and the largest residual ratio at exit.  Errors: CGGM_EINVAL
+ * (shapes, tol, a malformed CSR: row pointers not non-decreasing from 0 to nnz or a column
+ * outside [0, q)), CGGM_ENOTPD (a non-positive diagonal or curvature), CGGM_ENOMEM. */
+cggm_status cggm_spd_solve(cggm_ctx *ctx, int64_t q, const int64_t *row_ptr, const int32_t *col,
+                           const double *val, int64_t k, const double *B, int64_t c0, double tol,
+                           int max_iter, double *X, int *iters_out, double *resid_out);
+
 /*
  * No-allocation variant of cggm_lambda_sweep (the paper has no counterpart: this is an
  * interface for embedding).  Some callers cannot call cudaMalloc: code that runs under

@@ -27,4 +27,5 @@ from .cggm_oracle import (  # noqa: F401
     line_search,
     solve,
     soft_threshold,
+    spd_solve,
 )

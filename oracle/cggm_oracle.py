@@ -93,6 +93,16 @@ def _chol(Lam: np.ndarray) -> np.ndarray:
         raise NotPositiveDefinite(str(e)) from None
 
 
+def spd_solve(Lam: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """X = Lambda^-1 B for a symmetric positive definite Lambda (dense).  Section 4 computes
+    columns of Sigma = Lambda^-1 (B = identity columns) and P = R Sigma (B = R^T) this way by
+    conjugate gradient on the sparse Lambda; the oracle is the definition, with a Cholesky
+    factorisation and two triangular solves as library steps."""
+    L = _chol(Lam)
+    Z = np.linalg.solve(L, B)
+    return np.linalg.solve(L.T, Z)
+
+
 def _l1(A: np.ndarray, penalize_diag: bool = True) -> float:
     s = float(np.abs(A).sum())
     if not penalize_diag and A.shape[0] == A.shape[1]:

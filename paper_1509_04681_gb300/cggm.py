@@ -29,6 +29,7 @@ EXPORTED = [
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
+    "cggm_spd_solve",
 ]
 
 
@@ -119,6 +120,8 @@ def _lib():
         lib.cggm_footprint.restype = i64
         lib.cggm_lambda_sweep_noalloc.argtypes = [i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp,
                                                   vp]
+        lib.cggm_spd_solve.argtypes = [vp, i64, vp, vp, vp, i64, vp, i64, dbl, ip, vp,
+                                       ctypes.POINTER(ip), ctypes.POINTER(dbl)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -127,6 +130,7 @@ def _lib():
                                                      "cggm_active_sets",
                                                      "cggm_lambda_sweep_noalloc",
                                                      "cggm_contract", "cggm_server_create",
+                                                     "cggm_spd_solve",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -314,6 +318,27 @@ class Context:
                                     B.data_ptr(), B.stride(0), float(beta), C.data_ptr(),
                                     C.stride(0), int(mode)), "cggm_contract")
         return C
+
+    def cggm_spd_solve(self, indptr, indices, data, B=None, c0=0, k=None, tol=1e-10,
+                       max_iter=1000, allow_maxiter=False):
+        """Solve Lambda X = B by conjugate gradient, Lambda q x q in CSR (indptr, indices,
+        data); B q x k, or None for the identity columns c0 .. c0 + k - 1 (columns of
+        Sigma = Lambda^-1).  Returns (X, iterations, largest residual ratio)."""
+        q = len(indptr) - 1
+        rp = _Arr(indptr, np.int64)
+        ci = _Arr(indices, np.int32)
+        va = _Arr(data, np.float64)
+        if B is not None:
+            b = _Arr(B, np.float64)
+            k = b.obj.shape[1]
+        X = np.empty((q, int(k)))
+        it, res = ctypes.c_int(), ctypes.c_double()
+        st = _lib().cggm_spd_solve(self._h, q, rp.ptr, ci.ptr, va.ptr, int(k),
+                                   b.ptr if B is not None else None, int(c0), float(tol),
+                                   int(max_iter), X.ctypes.data, ctypes.byref(it),
+                                   ctypes.byref(res))
+        _check(st, "cggm_spd_solve", (CGGM_OK, CGGM_EMAXITER) if allow_maxiter else (CGGM_OK,))
+        return X, it.value, res.value
 
     def cggm_active_sets(self, G_L, G_T, Lam, Th, lam_L, lam_T, penalize_diag=True):
         q = Lam.shape[0]

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <vector>
 
+#include "cg.cuh"
 #include "chol.cuh"
 #include "common.cuh"
 #include "dense.cuh"
@@ -60,6 +61,8 @@ struct cggm_ctx {
     bool own_stream = false;
     // data
     Buf stage, Xt, Yt, Xt_f, Syy, Sxy, Sxx, Xd, colstats;
+    // sparse solves (cggm_spd_solve)
+    Buf cg_rp, cg_ci, cg_v, cg_b, cg_x, cg_w;
     // parameters and factorisations
     Buf Lam, Th, Lch, logd, Sig, Sig_f, Sd, Lam_a, Lch_a, logd_a, work;
     // products and gradients
@@ -715,7 +718,7 @@ void cggm_destroy(cggm_ctx *c) {
                    &c->Lam, &c->Th, &c->Lch, &c->logd, &c->Sig, &c->Sig_f, &c->Sd, &c->Lam_a,
                    &c->Lch_a, &c->logd_a, &c->work, &c->Rt, &c->Pt, &c->Z, &c->Psi, &c->Pd,
                    &c->GL, &c->GT, &c->W, &c->D, &c->U, &c->dV, &c->li, &c->lj, &c->ti,
-                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial, &c->colstats,
+                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial, &c->colstats, &c->cg_rp, &c->cg_ci, &c->cg_v, &c->cg_b, &c->cg_x, &c->cg_w,
                    &c->tcA_hi, &c->tcA_lo, &c->tcB_hi, &c->tcB_lo, &c->Xt_hi, &c->Xt_lo,
                    &c->Sig_hi, &c->Sig_lo, &c->R_f, &c->R_hi, &c->R_lo, &c->Pt_f, &c->Pt_hi,
                    &c->Pt_lo, &c->Zf, &c->tcerr};
@@ -1028,6 +1031,48 @@ cggm_status cggm_active_sets(cggm_ctx *c, int64_t p, int64_t q, const double *G_
     CGGM_CUDA_TRY(cudaMemcpyAsync(ti, c->ti.p, 4 * (size_t)hc[1], cudaMemcpyDefault, c->st));
     CGGM_CUDA_TRY(cudaMemcpyAsync(tj, c->tj.p, 4 * (size_t)hc[1], cudaMemcpyDefault, c->st));
     return sync_err(c);
+}
+
+cggm_status cggm_spd_solve(cggm_ctx *c, int64_t q, const int64_t *row_ptr, const int32_t *col,
+                           const double *val, int64_t k, const double *B, int64_t c0, double tol,
+                           int max_iter, double *X, int *iters_out, double *resid_out) {
+    if (!c || q < 1 || k < 1 || !row_ptr || !X || !(tol > 0.0) || max_iter < 1) return CGGM_EINVAL;
+    if (!B && (c0 < 0 || c0 + k > q)) return CGGM_EINVAL;
+    CGGM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = c->st;
+    int64_t nnz = 0;
+    CGGM_CUDA_TRY(cudaMemcpyAsync(&nnz, row_ptr + q, sizeof(int64_t), cudaMemcpyDefault, st));
+    CGGM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (nnz < 1 || nnz > q * q || !col || !val) return CGGM_EINVAL;
+    CGGM_TRY(ensure(c->cg_rp, 8 * (size_t)(q + 1)));
+    CGGM_TRY(ensure(c->cg_ci, 4 * (size_t)nnz));
+    CGGM_TRY(ensure(c->cg_v, 8 * (size_t)nnz));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->cg_rp.p, row_ptr, 8 * (size_t)(q + 1), cudaMemcpyDefault, st));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->cg_ci.p, col, 4 * (size_t)nnz, cudaMemcpyDefault, st));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->cg_v.p, val, 8 * (size_t)nnz, cudaMemcpyDefault, st));
+    CGGM_TRY(ensure(c->err, sizeof(int)));
+    CGGM_TRY(csr_check(q, nnz, P<int64_t>(c->cg_rp), P<int32_t>(c->cg_ci), P<int>(c->err), st));
+    const size_t qk = (size_t)q * k;
+    const double *dB = nullptr;
+    if (B) {
+        CGGM_TRY(ensure(c->cg_b, 8 * qk));
+        CGGM_CUDA_TRY(cudaMemcpyAsync(c->cg_b.p, B, 8 * qk, cudaMemcpyDefault, st));
+        dB = P<double>(c->cg_b);
+    }
+    double *dX = X;
+    if (!is_device_ptr(X)) {
+        CGGM_TRY(ensure(c->cg_x, 8 * qk));
+        dX = P<double>(c->cg_x);
+    }
+    CGGM_TRY(ensure(c->cg_w, 8 * cg_work_doubles(q, k)));
+    const CgWork w = cg_work_at(P<double>(c->cg_w), P<int>(c->err), q, k);
+    const cggm_status s = pcg_solve(q, P<int64_t>(c->cg_rp), P<int32_t>(c->cg_ci),
+                                    P<double>(c->cg_v), k, dB, c0, tol, max_iter, dX, w,
+                                    iters_out, resid_out, st);
+    if (s != CGGM_OK && s != CGGM_EMAXITER) return s;
+    if (dX != X) CGGM_CUDA_TRY(cudaMemcpyAsync(X, dX, 8 * qk, cudaMemcpyDeviceToHost, st));
+    CGGM_CUDA_TRY(cudaStreamSynchronize(st));
+    return s;
 }
 
 cggm_status cggm_contract(cggm_ctx *c, int64_t M, int64_t N, int64_t K, float alpha,

@@ -313,3 +313,29 @@ def test_active_set_strict_threshold():
     li, lj, ti, tj = oracle.active_sets(G_L, G_T, np.eye(2), np.zeros((1, 2)), 0.1, 0.2)
     assert list(zip(li, lj)) == [(0, 0), (1, 1)]
     assert list(zip(ti, tj)) == [(0, 1)]
+
+
+# ------------------------------------------------------------------------------------
+# sparse SPD solve (Section 4's Sigma columns and P = R Sigma)
+# ------------------------------------------------------------------------------------
+def test_spd_solve_closed_forms():
+    """Diagonal Lambda: X = B / diag.  2 x 2: the adjugate formula.  Chain: the residual
+    Lambda X - B vanishes and Sigma = Lambda^-1 is symmetric, with the known sign pattern
+    of the inverse of a tridiagonal M-matrix-like chain with positive off-diagonals
+    (Sigma_ij (-1)^(i+j) > 0)."""
+    rng = np.random.default_rng(0)
+    d = rng.uniform(0.5, 2.0, size=9)
+    B = rng.standard_normal((9, 4))
+    np.testing.assert_allclose(oracle.spd_solve(np.diag(d), B), B / d[:, None], rtol=1e-14)
+    a, b, c = 2.0, 0.7, 1.5
+    A = np.array([[a, b], [b, c]])
+    inv = np.array([[c, -b], [-b, a]]) / (a * c - b * b)
+    np.testing.assert_allclose(oracle.spd_solve(A, np.eye(2)), inv, rtol=1e-14)
+    Lam = synth.chain_precision(40).toarray()
+    S = oracle.spd_solve(Lam, np.eye(40))
+    np.testing.assert_allclose(Lam @ S, np.eye(40), atol=1e-12)
+    np.testing.assert_allclose(S, S.T, atol=1e-13)
+    i, j = np.indices(S.shape)
+    assert np.all(S * (-1.0) ** (i + j) > 0)
+    with pytest.raises(oracle.NotPositiveDefinite):
+        oracle.spd_solve(np.array([[1.0, 2.0], [2.0, 1.0]]), np.eye(2))
