@@ -78,25 +78,38 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     return v;
 }
 
-// Grid-wide barrier of a cooperative launch.  Every CTA adds one to a counter that only
-// grows; the CTAs of round r wait until it reaches (r + 1) nblocks, where r follows from the
-// value the CTA's own addition returned (no CTA can arrive at round r + 1 before all have
-// arrived at round r).  One L2 round trip per CTA plus the time for the last arrival to be
-// seen.  A wait that exceeds deadline_ns, or sees another CTA's error, returns false (and
-// records DEV_TIMEOUT in the first case).
-__device__ __forceinline__ bool grid_sync(GridBarrier *bar, int *err, unsigned nblocks,
-                                          uint64_t deadline_ns = 2000000000ull) {
-    __syncthreads();
-    __shared__ int s_ok;
+// Grid-wide barrier of a cooperative launch, in two halves so that a CTA can issue loads
+// between its arrival and its wait (the fence before the arrival would otherwise wait for
+// them).  Every CTA adds one to a counter that only grows; the CTAs of round r wait until
+// it reaches (r + 1) nblocks, where r follows from the value the CTA's own addition returned
+// (no CTA can arrive at round r + 1 before all have arrived at round r).  One L2 round trip
+// per CTA plus the time for the last arrival to be seen.  A wait that exceeds deadline_ns,
+// or sees another CTA's error, returns false (and records DEV_TIMEOUT in the first case).
+struct GridTicket {
+    unsigned long long target;  // thread 0: the count that ends this round (0: arrived last)
+};
+
+__device__ __forceinline__ GridTicket grid_arrive(GridBarrier *bar, unsigned nblocks) {
+    __syncthreads();  // the CTA's work of this round is done
+    GridTicket t{0};
     if (threadIdx.x == 0) {
         __threadfence();  // this CTA's writes before its arrival
         const unsigned long long old = atomicAdd(&bar->arrived, 1ull);
         const unsigned long long target = (old / nblocks + 1) * nblocks;
+        t.target = (old + 1 == target) ? 0ull : target;
+    }
+    return t;
+}
+
+__device__ __forceinline__ bool grid_wait(GridBarrier *bar, int *err, GridTicket t,
+                                          uint64_t deadline_ns = 2000000000ull) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
         int ok = 1;
-        if (old + 1 != target) {
+        if (t.target != 0) {
             const uint64_t t0 = global_ns();
             unsigned spins = 0;
-            while (ld_acquire_u64(&bar->arrived) < target) {
+            while (ld_acquire_u64(&bar->arrived) < t.target) {
                 if ((++spins & 63u) == 0) {
                     if (ld_acquire_int(err) != 0) { ok = 0; break; }
                     if (global_ns() - t0 > deadline_ns) {
@@ -106,13 +119,22 @@ __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int *err, unsigned n
                     }
                 }
             }
+        } else {
+            // the last arrival: an acquire read of the counter (its own addition is the last
+            // in the counter's order) orders the other CTAs' writes before later reads without
+            // waiting, as a fence would, for this thread's loads still in flight
+            (void)ld_acquire_u64(&bar->arrived);
         }
-        __threadfence();  // the other CTAs' writes before this CTA's later reads
         if (ok && ld_acquire_int(err) != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier *bar, int *err, unsigned nblocks,
+                                          uint64_t deadline_ns = 2000000000ull) {
+    return grid_wait(bar, err, grid_arrive(bar, nblocks), deadline_ns);
 }
 
 // Warp reductions

@@ -630,7 +630,47 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         } else if (nbn > 0) {
             phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
         }
-        if (!grid_sync(scr.bar, scr.err, nblk)) return;
+        // Phase C's first reads (segment 0, this warp's first R rows) do not depend on the
+        // steps: they are issued between this CTA's arrival at the barrier and its wait, so
+        // that their latency overlaps the wait.
+        constexpr int R = kRowsInFlight;
+        T sta[R], sv[R][NS], uv[R][NS];
+        int bv[NS];
+        auto seg_columns = [&](int g) {
+            const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
+#pragma unroll
+            for (int kk = 0; kk < NS; kk++) {
+                const int l = l0 + lane + 32 * kk;
+                bv[kk] = (l < l1) ? cur.sb[l] : -1;
+            }
+        };
+        auto load_rows = [&](int a, int64_t tb) {
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int64_t t = tb + (int64_t)kWarps * r;
+                sta[r] = T(0);
+#pragma unroll
+                for (int kk = 0; kk < NS; kk++) sv[r][kk] = uv[r][kk] = T(0);
+                if (t < r1) {
+                    const T *Sr = Sig + t * q;
+                    const T *Ur = Ut + t * q;
+                    sta[r] = Sr[a];
+#pragma unroll
+                    for (int kk = 0; kk < NS; kk++) {
+                        if (bv[kk] >= 0) {
+                            sv[r][kk] = Sr[bv[kk]];
+                            if (bv[kk] != a) uv[r][kk] = __ldcg(Ur + bv[kk]);
+                        }
+                    }
+                }
+            }
+        };
+        {
+            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            seg_columns(0);
+            load_rows(cur.sa[cur.sseg[0]], r0 + warp);
+            if (!grid_wait(scr.bar, scr.err, tk)) return;
+        }
 
         // ---- phase C: batch k's update on this CTA's rows; corrections for batch k+1 ----
         // coordinate (a, b) of a segment with row a: U_a += mu Sigma_b, U_b += mu Sigma_a
@@ -657,39 +697,18 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                 }
             }
             const int nseg = *cur.snseg;
-            constexpr int R = kRowsInFlight;
             for (int g = 0; g < nseg; g++) {
                 const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
                 const int a = cur.sa[l0];
-                int bv[NS];
+                if (g > 0) seg_columns(g);
                 T mv[NS];
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++) {
                     const int l = l0 + lane + 32 * kk;
-                    bv[kk] = (l < l1) ? cur.sb[l] : -1;
                     mv[kk] = (l < l1) ? smu[l] : T(0);
                 }
                 for (int64_t tb = r0 + warp; tb < r1; tb += kWarps * R) {
-                    T sta[R], sv[R][NS], uv[R][NS];
-#pragma unroll
-                    for (int r = 0; r < R; r++) {
-                        const int64_t t = tb + (int64_t)kWarps * r;
-                        sta[r] = T(0);
-#pragma unroll
-                        for (int kk = 0; kk < NS; kk++) sv[r][kk] = uv[r][kk] = T(0);
-                        if (t < r1) {
-                            const T *Sr = Sig + t * q;
-                            const T *Ur = Ut + t * q;
-                            sta[r] = Sr[a];
-#pragma unroll
-                            for (int kk = 0; kk < NS; kk++) {
-                                if (bv[kk] >= 0) {
-                                    sv[r][kk] = Sr[bv[kk]];
-                                    if (bv[kk] != a) uv[r][kk] = __ldcg(Ur + bv[kk]);
-                                }
-                            }
-                        }
-                    }
+                    if (g > 0 || tb != r0 + warp) load_rows(a, tb);  // else: loaded before the barrier
 #pragma unroll
                     for (int r = 0; r < R; r++) {
                         const int64_t t = tb + (int64_t)kWarps * r;
@@ -873,7 +892,35 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
         } else if (nbn > 0) {
             phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
         }
-        if (!grid_sync(scr.bar, scr.err, nblk)) return;
+        // Phase C's first reads (segment 0, this warp's first R rows of Sigma) do not depend
+        // on the steps: they are issued between this CTA's arrival at the barrier and its
+        // wait.
+        constexpr int R = kRowsInFlight;
+        T sv[R][NS];
+        int jv[NS];
+        auto seg_columns = [&](int g) {
+            const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
+#pragma unroll
+            for (int kk = 0; kk < NS; kk++) {
+                const int l = l0 + lane + 32 * kk;
+                jv[kk] = (l < l1) ? cur.sb[l] : -1;
+            }
+        };
+        auto load_rows = [&](int64_t tb) {
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int64_t t = tb + (int64_t)kWarps * r;
+#pragma unroll
+                for (int kk = 0; kk < NS; kk++)
+                    sv[r][kk] = (t < r1 && jv[kk] >= 0) ? Sig[t * q + jv[kk]] : T(0);
+            }
+        };
+        {
+            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            seg_columns(0);
+            load_rows(r0 + warp);
+            if (!grid_wait(scr.bar, scr.err, tk)) return;
+        }
 
         // ---- phase C: dVt[t][i] += sum over the segment of row i of mu Sigma[t][j] ----
         {
@@ -897,27 +944,18 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                 }
             }
             const int nseg = *cur.snseg;
-            constexpr int R = kRowsInFlight;
             for (int g = 0; g < nseg; g++) {
                 const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
                 const int i = cur.sa[l0];
-                int jv[NS];
+                if (g > 0) seg_columns(g);
                 T mv[NS];
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++) {
                     const int l = l0 + lane + 32 * kk;
-                    jv[kk] = (l < l1) ? cur.sb[l] : -1;
                     mv[kk] = (l < l1) ? smu[l] : T(0);
                 }
                 for (int64_t tb = r0 + warp; tb < r1; tb += kWarps * R) {
-                    T sv[R][NS];
-#pragma unroll
-                    for (int r = 0; r < R; r++) {
-                        const int64_t t = tb + (int64_t)kWarps * r;
-#pragma unroll
-                        for (int kk = 0; kk < NS; kk++)
-                            sv[r][kk] = (t < r1 && jv[kk] >= 0) ? Sig[t * q + jv[kk]] : T(0);
-                    }
+                    if (g > 0 || tb != r0 + warp) load_rows(tb);  // else: loaded before the barrier
 #pragma unroll
                     for (int r = 0; r < R; r++) {
                         const int64_t t = tb + (int64_t)kWarps * r;
