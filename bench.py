@@ -299,6 +299,26 @@ def run_profile_sweep(args):
                                         "d_abs_sum": float(np.abs(D).sum())}}))
 
 
+def run_profile_contract(args):
+    """The tensor-core contraction alone at 8192 x 8192 x 4096 (3xTF32 split mode, the mode
+    the mixed path uses), twice through cggm_contract: for ncu captures of gemm_tc_kernel."""
+    import torch
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(0)
+    M, N, K = 8192, 8192, 4096
+    A = torch.randn(M, K, device=dev, generator=g)
+    B = torch.randn(N, K, device=dev, generator=g)
+    with cg.Context(0) as ctx:
+        for _ in range(2):
+            C = ctx.cggm_contract(A, B, mode=1)
+        torch.cuda.synchronize()
+    print(json.dumps({"profile_contract": {"M": M, "N": N, "K": K, "mode": "split",
+                                           "c_abs_sum": float(C.abs().sum())}}))
+
+
 def run_serve(args):
     """Served regularisation paths: requests of uneven size arriving as a Poisson process
     (20 per second), each an 8-point lambda grid from 0.5 down to 0.02 solved with warm
@@ -494,9 +514,13 @@ def main():
     ap.add_argument("--serve-max-iter", type=int, default=100)
     ap.add_argument("--profile-sweep", action="store_true",
                     help="run only a bounded Lambda pass at q=5000 (for ncu captures)")
+    ap.add_argument("--profile-contract", action="store_true",
+                    help="run only the tensor-core contraction at 8192^2 x 4096 (for ncu captures)")
     args = ap.parse_args()
     if args.profile_sweep:
         run_profile_sweep(args)
+    elif args.profile_contract:
+        run_profile_contract(args)
     elif args.serve:
         run_serve(args)
     elif args.impl == "reference":
