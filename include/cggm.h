@@ -70,7 +70,8 @@ typedef struct {
     double ls_beta;      /* Armijo step shrink factor; 0.5                                */
     int ls_max_trials;   /* Armijo trials before CGGM_ELINESEARCH; 50                     */
     int penalize_diag;   /* include diag(Lambda) in ||Lambda||_1; 1                       */
-    int sweep_batch;     /* coordinates per blocked Gauss-Seidel batch, 0 = default      */
+    int sweep_batch;     /* coordinates per blocked Gauss-Seidel batch: 32, 64, 128, or   
+                            256 and 512 in the mixed path; 0 = default (128 FP64, 256)  */
     double target_f;     /* also stop once f <= target_f (time-to-gap runs); -inf = off  */
     int verbose;         /* per-iteration line on stderr                                  */
 } cggm_opts;

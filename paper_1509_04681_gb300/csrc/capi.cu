@@ -743,7 +743,7 @@ cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, in
     if (!(o.tol > 0.0) || o.max_iter < 0 || o.ls_max_trials < 1 || !(o.ls_beta > 0.0 && o.ls_beta < 1.0))
         return CGGM_EINVAL;
     if (o.sweep_batch != 0 && o.sweep_batch != 32 && o.sweep_batch != 64 && o.sweep_batch != 128 &&
-        !(o.sweep_batch == 256 && o.precision == CGGM_MIXED))
+        !((o.sweep_batch == 256 || o.sweep_batch == 512) && o.precision == CGGM_MIXED))
         return CGGM_EINVAL;
     if (info) memset(info, 0, sizeof(*info));
     const int64_t launches0 = launch_counter();

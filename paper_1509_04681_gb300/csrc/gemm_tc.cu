@@ -33,6 +33,7 @@ constexpr int TM = 128, TN = 128, TK = 32;  // TK floats = 128 B = one swizzle r
 constexpr int STAGES_PLAIN = 4;  // 4 x 2 tiles x 16 KB = 128 KB of shared memory
 constexpr int STAGES_SPLIT = 3;  // 3 x 4 tiles x 16 KB = 192 KB
 constexpr int THREADS = 128;
+constexpr int kGroupM = 8;     // tile rows per band of the launch order
 constexpr int TILE_BYTES = TM * TK * 4;     // 16 KB (A tile; B tile is the same size)
 constexpr uint64_t WAIT_NS = kMbarWaitNs;
 
@@ -109,7 +110,20 @@ gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     __shared__ uint32_t s_tmem;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    // Tile order: CTAs that run at the same time (consecutive linear indices) take tiles from
+    // a band of kGroupM tile rows, column by column, so that a wave reads kGroupM row blocks
+    // of A and a few column blocks of B, which stay in L2, instead of every column block.
+    int m0, n0;
+    {
+        const int gn = (int)gridDim.x, gm = (int)gridDim.y;
+        const int lin = (int)(blockIdx.y * gridDim.x + blockIdx.x);
+        const int per_group = kGroupM * gn;
+        const int first_m = (lin / per_group) * kGroupM;
+        const int rows = (gm - first_m) < kGroupM ? (gm - first_m) : kGroupM;
+        const int in_group = lin % per_group;
+        m0 = (first_m + in_group % rows) * TM;
+        n0 = (in_group / rows) * TN;
+    }
     const int nk = (K + TK - 1) / TK;
 
     if (threadIdx.x == 0) {

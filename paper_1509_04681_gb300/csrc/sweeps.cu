@@ -93,13 +93,28 @@ __device__ __forceinline__ void decode_pair(int e, int &l, int &l1) {
 // later l2 > l are contiguous, at colbase(l) + (l2 - l - 1), so that at step l the lanes
 // of the warp read consecutive words.
 __host__ __device__ __forceinline__ int colbase(int l, int B) { return l * (2 * B - l - 1) / 2; }
+
+// Phase B keeps every panel's coefficients in shared memory up to B = 256; above, they do not
+// fit (B = 512: 523 KB in float) and two panel buffers take turns.  Panel s (columns 32 s ..
+// 32 s + 31) holds colbase(32 s + 32) - colbase(32 s) = 32 (B - 1) - 1024 s - 496 entries,
+// the largest for s = 0.
+__host__ __device__ constexpr int panel_bufs(int B) { return B <= 256 ? B / 32 : 2; }
+__host__ __device__ constexpr int panel_max(int B) { return ((32 * B - 528) + 3) & ~3; }
+__host__ __device__ constexpr int coef_area(int B) {
+    return panel_bufs(B) == B / 32 ? coef_slots(B) : panel_bufs(B) * panel_max(B);
+}
+// offset of panel s's buffer in the coefficient area
+__host__ __device__ __forceinline__ int panel_off(int s, int B) {
+    return panel_bufs(B) == B / 32 ? colbase(32 * s, B) : (s % panel_bufs(B)) * panel_max(B);
+}
 // shared-memory slots for the coefficients (16-byte multiple with copy slack)
 
 
 struct SmemLayout {
     size_t meta;  // twice (current and next batch): sa[B], sb[B], sseg[B + 1], nseg (ints)
     size_t work;  // union: phase A ring of row chunks (kRingBytes);
-                  //        phase B coef[coef_slots(B)], step constants [PRE_N][B], corr[B] (T);
+                  //        phase B coefficient panels [coef_area(B)], step constants
+                  //          [PRE_N][B], corr[B] (T);
                   //        phase C mu[B] (T)
     size_t total;
 };
@@ -111,7 +126,7 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
     size_t off = (size_t)2 * (3 * B + 2) * sizeof(int32_t);  // two batches' metadata
     off = (off + 15) & ~size_t(15);
     s.work = off;
-    const size_t phb = ((size_t)coef_slots(B) + PRE_N * B + B + 8) * sizeof(T);
+    const size_t phb = ((size_t)coef_area(B) + PRE_N * B + B + 8) * sizeof(T);
     const size_t phc = (size_t)(B + 4) * sizeof(T);
     size_t w = phb > phc ? phb : phc;
     w = w > kRingBytes ? w : kRingBytes;
@@ -126,22 +141,36 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
 // memory (column-packed, see colbase).  Lane k owns coordinates 32 s + k; at step l every lane forms the candidate
 // step of its own coordinate of the current panel and the owner's candidate is broadcast,
 // so the dependent chain per coordinate is a few T operations and one warp shuffle.
+// Issues the bulk copy of panel s's coefficient columns into its buffer (one thread).
+template <typename T, int NS>
+__device__ __forceinline__ void issue_panel(int s, const T *gcoef, T *scoef, uint64_t *mb) {
+    constexpr int B = NS * 32;
+    const int c0 = colbase(32 * s, B), c1 = colbase(32 * s + 32, B);
+    const uint32_t bytes = (uint32_t)((size_t)(c1 - c0) * sizeof(T));
+    uint64_t *bar = &mb[s % panel_bufs(B)];
+    mbar_expect_tx(bar, bytes);
+    bulk_load(scoef + panel_off(s, B), gcoef + c0, bytes, bar);
+}
+
 template <typename T, int NS>
 __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T *acc0,
-                                     const T *coef, uint64_t *mb, uint32_t &phase,
+                                     const T *gcoef, T *coef, uint64_t *mb, uint32_t &phase,
                                      double *mu_out, int *err) {
     // pre[] holds zeros for padding coordinates l >= nb, which give mu = 0 whatever the
     // correction sum (also a non-finite one: fmin / fmax return the other operand), so
     // panels run all 32 steps without branches.  B is a compile-time constant, so that every coefficient address
     // below is the lane index plus an immediate offset.
     constexpr int B = NS * 32;
+    constexpr int NBUF = panel_bufs(B);
     const int lane = threadIdx.x & 31;
+    const int npan = (nb + 31) / 32;
+    int issued = npan < NBUF ? npan : NBUF;  // panels whose copies have been started
     bool bad = false;
-    int lost = -1;  // first panel whose data did not arrive (NS: the step constants)
+    int lost = -1;  // first panel whose data did not arrive
     if (!mbar_wait(&mb[NS], (phase >> NS) & 1u, err)) {
-        lost = 0;
-        for (int s = 0; s * 32 < nb && s < NS; s++)
-            if (mbar_wait(&mb[s], (phase >> s) & 1u, err, false)) phase ^= 1u << s;
+        for (int s = 0; s < issued; s++)
+            if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
+                phase ^= 1u << (s % NBUF);
         if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
         return;
     }
@@ -152,12 +181,13 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         if (s * 32 >= nb) break;
-        // the coefficients of panel s (columns 32 s .. 32 s + 31) land on mb[s]
-        if (!mbar_wait(&mb[s], (phase >> s) & 1u, err)) {
+        // the coefficients of panel s (columns 32 s .. 32 s + 31) land on its buffer's mbarrier
+        const int bi = s % NBUF;
+        if (!mbar_wait(&mb[bi], (phase >> bi) & 1u, err)) {
             lost = s;
             break;
         }
-        phase ^= 1u << s;
+        phase ^= 1u << bi;
         const int lo = s * 32 + lane;
         const T vph = pre[PRE_VPH * B + lo], vpl = pre[PRE_VPL * B + lo];
         const T vmh = pre[PRE_VMH * B + lo], vml = pre[PRE_VML * B + lo];
@@ -169,7 +199,7 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
         // Steps are unrolled by four only: fully unrolled, the batch is tens of kilobytes of
         // straight-line code that the instruction cache has to bring back for every batch.
         // col points at column l of the packed coefficients, col[l2] = coef(l2, l), l2 > l.
-        const T *col = coef + colbase(32 * s, B) - 32 * s - 1;
+        const T *col = coef + panel_off(s, B) - 32 * s - 1;
 #pragma unroll 4
         for (int o = 0; o < 32; o++) {
             const int l = s * 32 + o;
@@ -188,10 +218,19 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
             if (!isfinite(m)) { bad = true; m = 0.0; }
             mu_out[lo] = m;
         }
+        if (issued < npan) {  // this panel's buffer is free: bring in panel s + NBUF
+            __syncwarp();
+            if (lane == 0) {
+                fence_proxy_async();
+                issue_panel<T, NS>(issued, gcoef, coef, mb);
+            }
+            issued++;
+        }
     }
     if (lost >= 0) {  // the pass is abandoned; wait (bounded) for the copies still in flight
-        for (int s = lost; s * 32 < nb && s < NS; s++)
-            if (mbar_wait(&mb[s], (phase >> s) & 1u, err, false)) phase ^= 1u << s;
+        for (int s = lost; s < issued; s++)
+            if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
+                phase ^= 1u << (s % NBUF);
     }
     if (bad) set_err(err, DEV_NONFINITE);
 }
@@ -216,15 +255,11 @@ __device__ void phase_b(int nb, const T *gcoef, const T *gpre, const T *gcorr, T
             mbar_expect_tx(&mb[NS], (uint32_t)((PRE_N * B + B) * sizeof(T)));
             bulk_load(spre, gpre, (uint32_t)(PRE_N * B * sizeof(T)), &mb[NS]);
             bulk_load(scorr, gcorr, (uint32_t)(B * sizeof(T)), &mb[NS]);
-            for (int s = 0; s * 32 < nb; s++) {
-                const int c0 = colbase(32 * s, B), c1 = colbase(32 * s + 32, B);
-                const uint32_t bytes = (uint32_t)((size_t)(c1 - c0) * sizeof(T));
-                mbar_expect_tx(&mb[s], bytes);
-                bulk_load(scoef + c0, gcoef + c0, bytes, &mb[s]);
-            }
+            for (int s = 0; s * 32 < nb && s < panel_bufs(B); s++)
+                issue_panel<T, NS>(s, gcoef, scoef, mb);
         }
         __syncwarp();
-        forward_substitution<T, NS>(nb, spre, scorr, scoef, mb, phase, mu, err);
+        forward_substitution<T, NS>(nb, spre, scorr, gcoef, scoef, mb, phase, mu, err);
     }
     __syncthreads();
 }
@@ -625,7 +660,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         // ---- phase B of batch k on CTA 0, phase A of batch k+1 on the others ----
         if (blockIdx.x == 0) {
             phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_slots(B), s_mb, mb_phase, scr.mu,
+                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
                            scr.err);
         } else if (nbn > 0) {
             phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
@@ -633,7 +668,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         // Phase C's first reads (segment 0, this warp's first R rows) do not depend on the
         // steps: they are issued between this CTA's arrival at the barrier and its wait, so
         // that their latency overlaps the wait.
-        constexpr int R = kRowsInFlight;
+        constexpr int R = NS <= 8 ? kRowsInFlight : 2;  // registers: R x NS values per lane
         T sta[R], sv[R][NS], uv[R][NS];
         int bv[NS];
         auto seg_columns = [&](int g) {
@@ -887,7 +922,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
 
         if (blockIdx.x == 0) {
             phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_slots(B), s_mb, mb_phase, scr.mu,
+                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
                            scr.err);
         } else if (nbn > 0) {
             phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
@@ -895,7 +930,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
         // Phase C's first reads (segment 0, this warp's first R rows of Sigma) do not depend
         // on the steps: they are issued between this CTA's arrival at the barrier and its
         // wait.
-        constexpr int R = kRowsInFlight;
+        constexpr int R = NS <= 8 ? kRowsInFlight : 2;  // registers: R x NS values per lane
         T sv[R][NS];
         int jv[NS];
         auto seg_columns = [&](int g) {
@@ -1016,7 +1051,7 @@ int sweep_grid() { return sm_count(); }
 
 cggm_status scratch_reserve(SweepScratch &scr) {
     if (scr.mu) return CGGM_OK;
-    const int Bmax = 256;  // float; double batches are at most 128 and take less
+    const int Bmax = 512;  // float; double batches are at most 128 and take less
     CGGM_CUDA_TRY(cudaMalloc(&scr.mu, sizeof(double) * Bmax));
     CGGM_CUDA_TRY(cudaMalloc(&scr.sub1, scratch_sub1_bytes(Bmax, sizeof(float))));
     CGGM_CUDA_TRY(cudaMalloc(&scr.sub2, scratch_sub2_bytes(Bmax, sizeof(float))));
@@ -1040,7 +1075,7 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
                          double *D, T *U, int B, SweepScratch &scr,
                          cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
-    if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
+    if (B < 32 || B > (sizeof(T) == 4 ? 512 : 128) || (B & (B - 1))) return CGGM_EINVAL;
     CGGM_TRY(scratch_reserve(scr));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
@@ -1055,6 +1090,7 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
         case 64: fn = (const void *)lambda_sweep_kernel<T, 2>; break;
         case 128: fn = (const void *)lambda_sweep_kernel<T, 4>; break;
         case 256: fn = (const void *)lambda_sweep_kernel<T, 8>; break;
+        case 512: fn = (const void *)lambda_sweep_kernel<float, 16>; break;
         default: return CGGM_EINVAL;
     }
     std::lock_guard<std::mutex> lock(coop_mutex());
@@ -1093,7 +1129,7 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
                         const int32_t *ti, const int32_t *tj, double lam, T *dV, int B,
                         SweepScratch &scr, cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
-    if (B < 32 || B > (sizeof(T) == 4 ? 256 : 128) || (B & (B - 1))) return CGGM_EINVAL;
+    if (B < 32 || B > (sizeof(T) == 4 ? 512 : 128) || (B & (B - 1))) return CGGM_EINVAL;
     CGGM_TRY(scratch_reserve(scr));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
@@ -1107,6 +1143,7 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, co
         case 64: fn = (const void *)theta_sweep_kernel<T, 2>; break;
         case 128: fn = (const void *)theta_sweep_kernel<T, 4>; break;
         case 256: fn = (const void *)theta_sweep_kernel<T, 8>; break;
+        case 512: fn = (const void *)theta_sweep_kernel<float, 16>; break;
         default: return CGGM_EINVAL;
     }
     std::lock_guard<std::mutex> lock(coop_mutex());

@@ -224,6 +224,16 @@ def test_solve_small_chain_matches_oracle(ctx, prec):
     check_solution(pr, r, ref, f_star)
 
 
+def test_solve_batch_of_512_matches_oracle(ctx):
+    """The mixed path with batches of 512 coordinates (coefficient panels streamed through two
+    shared-memory buffers in phase B) on the 200 x 100 workload, by the same bar."""
+    pr = synth.workload("chain-gauss-p200-q100-n100")
+    ref = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, max_iter=3000)
+    o = cg.make_opts(precision=cg.CGGM_MIXED, max_iter=3000, sweep_batch=512)
+    r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, opts=o)
+    check_solution(pr, r, ref, ref.f)
+
+
 def test_solve_first_iterates_track_oracle(ctx):
     """FP64 path: the objective after each of the first iterations equals the oracle's."""
     pr = problem(60, 40, 50, seed=8, lam=0.1)
