@@ -276,6 +276,24 @@ cggm_status cggm_spd_solve(cggm_ctx *ctx, int64_t q, const int64_t *row_ptr, con
                            const double *val, int64_t k, const double *B, int64_t c0, double tol,
                            int max_iter, double *X, int *iters_out, double *resid_out);
 
+/* A block of columns C = c0 .. c0 + k - 1 of the Lambda gradient (Eq. 3),
+ * G_Lambda[:, C] = S_yy[:, C] - Sigma[:, C] - Psi[:, C], without forming Sigma or Psi whole:
+ * the block regime of Section 4 visits Lambda column block by column block, and the
+ * block's active set (Section 2.2) is the threshold of this gradient.  Sigma[:, C] and
+ * P^T = Sigma R^T (R = X Theta) come from conjugate-gradient solves on the sparse Lambda
+ * (as cggm_spd_solve, tolerance tol, at most max_iter iterations each), Psi[:, C] = P^T P_C / n
+ * and S_yy[:, C] = Y^T Y_C / n from products over the n samples.
+ *   X, Y: as for cggm_solve.  Lambda: q x q CSR as for cggm_spd_solve.  Theta: p x q
+ *   row-major double (host or device).  G_out: q x k row-major double (host or device).
+ *   iters_out (optional): the larger iteration count of the two solves.
+ * Errors: as cggm_spd_solve (CGGM_EMAXITER if a solve did not reach tol), and CGGM_EINVAL
+ * for c0 + k > q. */
+cggm_status cggm_grad_lambda_block(cggm_ctx *ctx, const void *X, int xdtype, const void *Y,
+                                   int ydtype, int64_t n, int64_t p, int64_t q,
+                                   const int64_t *row_ptr, const int32_t *col, const double *val,
+                                   const double *Theta, int64_t c0, int64_t k, double tol,
+                                   int max_iter, double *G_out, int *iters_out);
+
 /*
  * No-allocation variant of cggm_lambda_sweep (the paper has no counterpart: this is an
  * interface for embedding).  Some callers cannot call cudaMalloc: code that runs under

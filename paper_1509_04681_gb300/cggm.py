@@ -29,7 +29,7 @@ EXPORTED = [
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
-    "cggm_spd_solve",
+    "cggm_spd_solve", "cggm_grad_lambda_block",
 ]
 
 
@@ -122,6 +122,8 @@ def _lib():
                                                   vp]
         lib.cggm_spd_solve.argtypes = [vp, i64, vp, vp, vp, i64, vp, i64, dbl, ip, vp,
                                        ctypes.POINTER(ip), ctypes.POINTER(dbl)]
+        lib.cggm_grad_lambda_block.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, vp, vp,
+                                               i64, i64, dbl, ip, vp, ctypes.POINTER(ip)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -130,7 +132,7 @@ def _lib():
                                                      "cggm_active_sets",
                                                      "cggm_lambda_sweep_noalloc",
                                                      "cggm_contract", "cggm_server_create",
-                                                     "cggm_spd_solve",
+                                                     "cggm_spd_solve", "cggm_grad_lambda_block",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -339,6 +341,25 @@ class Context:
                                    ctypes.byref(res))
         _check(st, "cggm_spd_solve", (CGGM_OK, CGGM_EMAXITER) if allow_maxiter else (CGGM_OK,))
         return X, it.value, res.value
+
+    def cggm_grad_lambda_block(self, X, Y, indptr, indices, data, Th, c0, k, tol=1e-10,
+                               max_iter=1000):
+        """Columns c0 .. c0 + k - 1 of the Lambda gradient from the sparse Lambda (CSR) by
+        conjugate gradient, without forming Sigma.  Returns (G block q x k, iterations)."""
+        n, p = X.shape
+        q = Y.shape[1]
+        xd, xt = _x_dtype(X)
+        yd, yt = _x_dtype(Y)
+        Xa, Ya = _Arr(X, xd), _Arr(Y, yd)
+        rp, ci, va = _Arr(indptr, np.int64), _Arr(indices, np.int32), _Arr(data, np.float64)
+        Ta = _Arr(Th, np.float64)
+        G = np.empty((q, int(k)))
+        it = ctypes.c_int()
+        _check(_lib().cggm_grad_lambda_block(self._h, Xa.ptr, xt, Ya.ptr, yt, n, p, q, rp.ptr,
+                                             ci.ptr, va.ptr, Ta.ptr, int(c0), int(k), float(tol),
+                                             int(max_iter), G.ctypes.data, ctypes.byref(it)),
+               "cggm_grad_lambda_block")
+        return G, it.value
 
     def cggm_active_sets(self, G_L, G_T, Lam, Th, lam_L, lam_T, penalize_diag=True):
         q = Lam.shape[0]

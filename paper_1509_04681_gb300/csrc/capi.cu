@@ -63,6 +63,8 @@ struct cggm_ctx {
     Buf stage, Xt, Yt, Xt_f, Syy, Sxy, Sxx, Xd, colstats;
     // sparse solves (cggm_spd_solve)
     Buf cg_rp, cg_ci, cg_v, cg_b, cg_x, cg_w;
+    // block gradients (cggm_grad_lambda_block)
+    Buf bk_th, bk_rt, bk_pt, bk_sig, bk_psi, bk_g;
     // parameters and factorisations
     Buf Lam, Th, Lch, logd, Sig, Sig_f, Sd, Lam_a, Lch_a, logd_a, work;
     // products and gradients
@@ -718,7 +720,7 @@ void cggm_destroy(cggm_ctx *c) {
                    &c->Lam, &c->Th, &c->Lch, &c->logd, &c->Sig, &c->Sig_f, &c->Sd, &c->Lam_a,
                    &c->Lch_a, &c->logd_a, &c->work, &c->Rt, &c->Pt, &c->Z, &c->Psi, &c->Pd,
                    &c->GL, &c->GT, &c->W, &c->D, &c->U, &c->dV, &c->li, &c->lj, &c->ti,
-                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial, &c->colstats, &c->cg_rp, &c->cg_ci, &c->cg_v, &c->cg_b, &c->cg_x, &c->cg_w,
+                   &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial, &c->colstats, &c->cg_rp, &c->cg_ci, &c->cg_v, &c->cg_b, &c->cg_x, &c->cg_w, &c->bk_th, &c->bk_rt, &c->bk_pt, &c->bk_sig, &c->bk_psi, &c->bk_g,
                    &c->tcA_hi, &c->tcA_lo, &c->tcB_hi, &c->tcB_lo, &c->Xt_hi, &c->Xt_lo,
                    &c->Sig_hi, &c->Sig_lo, &c->R_f, &c->R_hi, &c->R_lo, &c->Pt_f, &c->Pt_hi,
                    &c->Pt_lo, &c->Zf, &c->tcerr};
@@ -1033,12 +1035,9 @@ cggm_status cggm_active_sets(cggm_ctx *c, int64_t p, int64_t q, const double *G_
     return sync_err(c);
 }
 
-cggm_status cggm_spd_solve(cggm_ctx *c, int64_t q, const int64_t *row_ptr, const int32_t *col,
-                           const double *val, int64_t k, const double *B, int64_t c0, double tol,
-                           int max_iter, double *X, int *iters_out, double *resid_out) {
-    if (!c || q < 1 || k < 1 || !row_ptr || !X || !(tol > 0.0) || max_iter < 1) return CGGM_EINVAL;
-    if (!B && (c0 < 0 || c0 + k > q)) return CGGM_EINVAL;
-    CGGM_CUDA_TRY(cudaSetDevice(c->device));
+// Copies a CSR matrix (host or device) into the context and validates it on the device.
+cggm_status upload_csr(cggm_ctx *c, int64_t q, const int64_t *row_ptr, const int32_t *col,
+                       const double *val, int64_t *nnz_out) {
     cudaStream_t st = c->st;
     int64_t nnz = 0;
     CGGM_CUDA_TRY(cudaMemcpyAsync(&nnz, row_ptr + q, sizeof(int64_t), cudaMemcpyDefault, st));
@@ -1052,6 +1051,19 @@ cggm_status cggm_spd_solve(cggm_ctx *c, int64_t q, const int64_t *row_ptr, const
     CGGM_CUDA_TRY(cudaMemcpyAsync(c->cg_v.p, val, 8 * (size_t)nnz, cudaMemcpyDefault, st));
     CGGM_TRY(ensure(c->err, sizeof(int)));
     CGGM_TRY(csr_check(q, nnz, P<int64_t>(c->cg_rp), P<int32_t>(c->cg_ci), P<int>(c->err), st));
+    *nnz_out = nnz;
+    return CGGM_OK;
+}
+
+cggm_status cggm_spd_solve(cggm_ctx *c, int64_t q, const int64_t *row_ptr, const int32_t *col,
+                           const double *val, int64_t k, const double *B, int64_t c0, double tol,
+                           int max_iter, double *X, int *iters_out, double *resid_out) {
+    if (!c || q < 1 || k < 1 || !row_ptr || !X || !(tol > 0.0) || max_iter < 1) return CGGM_EINVAL;
+    if (!B && (c0 < 0 || c0 + k > q)) return CGGM_EINVAL;
+    CGGM_CUDA_TRY(cudaSetDevice(c->device));
+    cudaStream_t st = c->st;
+    int64_t nnz = 0;
+    CGGM_TRY(upload_csr(c, q, row_ptr, col, val, &nnz));
     const size_t qk = (size_t)q * k;
     const double *dB = nullptr;
     if (B) {
@@ -1073,6 +1085,61 @@ cggm_status cggm_spd_solve(cggm_ctx *c, int64_t q, const int64_t *row_ptr, const
     if (dX != X) CGGM_CUDA_TRY(cudaMemcpyAsync(X, dX, 8 * qk, cudaMemcpyDeviceToHost, st));
     CGGM_CUDA_TRY(cudaStreamSynchronize(st));
     return s;
+}
+
+cggm_status cggm_grad_lambda_block(cggm_ctx *c, const void *X, int xdtype, const void *Y,
+                                   int ydtype, int64_t n, int64_t p, int64_t q,
+                                   const int64_t *row_ptr, const int32_t *col, const double *val,
+                                   const double *Theta, int64_t c0, int64_t k, double tol,
+                                   int max_iter, double *G_out, int *iters_out) {
+    if (!c || !X || !Y || !row_ptr || !Theta || !G_out || k < 1 || c0 < 0 || !(tol > 0.0) ||
+        max_iter < 1)
+        return CGGM_EINVAL;
+    if (!dtypes_ok(xdtype, ydtype)) return CGGM_EINVAL;
+    CGGM_TRY(check_sizes(n, p, q));
+    if (c0 + k > q) return CGGM_EINVAL;
+    CGGM_TRY(set_device(c));
+    cudaStream_t st = c->st;
+    int64_t nnz = 0;
+    CGGM_TRY(upload_csr(c, q, row_ptr, col, val, &nnz));
+    CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
+    CGGM_TRY(load_transposed(c, Y, ydtype, n, q, c->Yt, nullptr));
+    const size_t pq = (size_t)p * q, qn = (size_t)q * n, qk = (size_t)q * k;
+    CGGM_TRY(load_double(c, Theta, pq, c->bk_th));
+    CGGM_TRY(ensure(c->bk_rt, 8 * qn));
+    CGGM_TRY(ensure(c->bk_pt, 8 * qn));
+    CGGM_TRY(ensure(c->bk_sig, 8 * qk));
+    CGGM_TRY(ensure(c->bk_psi, 8 * qk));
+    CGGM_TRY(ensure(c->bk_g, 8 * qk));
+    const int64_t kmax = n > k ? n : k;
+    CGGM_TRY(ensure(c->cg_w, 8 * cg_work_doubles(q, kmax)));
+    const CgWork w = cg_work_at(P<double>(c->cg_w), P<int>(c->err), q, kmax);
+    const int64_t *rp = P<int64_t>(c->cg_rp);
+    const int32_t *ci = P<int32_t>(c->cg_ci);
+    const double *va = P<double>(c->cg_v);
+    const double inv = 1.0 / (double)n;
+    // R^T = Theta^T X^T (q x n); P^T = Sigma R^T from Lambda P^T = R^T; Sigma[:, C]
+    gemm<double>(true, false, q, n, p, 1.0, P<double>(c->bk_th), q, P<double>(c->Xt), n, 0.0,
+                 P<double>(c->bk_rt), n, st);
+    int it1 = 0, it2 = 0;
+    double res = 0.0;
+    cggm_status s = pcg_solve(q, rp, ci, va, n, P<double>(c->bk_rt), 0, tol, max_iter,
+                              P<double>(c->bk_pt), w, &it1, &res, st);
+    if (s != CGGM_OK) return s;
+    s = pcg_solve(q, rp, ci, va, k, nullptr, c0, tol, max_iter, P<double>(c->bk_sig), w, &it2,
+                  &res, st);
+    if (s != CGGM_OK) return s;
+    // Psi[:, C] = P^T P_C / n and S_yy[:, C] = Y^T Y_C / n (both q x k), then
+    // G_Lambda[:, C] = S_yy[:, C] - Sigma[:, C] - Psi[:, C]  (Eq. 3)
+    gemm<double>(false, true, q, k, n, inv, P<double>(c->bk_pt), n, P<double>(c->bk_pt) + c0 * n,
+                 n, 0.0, P<double>(c->bk_psi), k, st);
+    gemm<double>(false, true, q, k, n, inv, P<double>(c->Yt), n, P<double>(c->Yt) + c0 * n, n,
+                 0.0, P<double>(c->bk_g), k, st);
+    axpby<double>((int64_t)qk, -1.0, P<double>(c->bk_sig), 1.0, P<double>(c->bk_g), st);
+    axpby<double>((int64_t)qk, -1.0, P<double>(c->bk_psi), 1.0, P<double>(c->bk_g), st);
+    CGGM_TRY(store_double(c, G_out, c->bk_g.p, qk));
+    if (iters_out) *iters_out = it1 > it2 ? it1 : it2;
+    return sync_err(c);
 }
 
 cggm_status cggm_contract(cggm_ctx *c, int64_t M, int64_t N, int64_t K, float alpha,

@@ -80,3 +80,21 @@ def test_not_positive_definite_and_malformed(ctx):
     with pytest.raises(cg.CGGMError) as e:
         ctx.cggm_spd_solve(rp, bad, va, c0=0, k=1, tol=1e-12)
     assert e.value.status == cg.CGGM_EINVAL
+
+
+@pytest.mark.parametrize("kind", ["chain", "random4"])
+def test_lambda_gradient_column_block(ctx, kind):
+    """G_Lambda[:, C] from the sparse Lambda by conjugate gradient (Sigma never formed) against
+    the oracle's full gradient of Eq. 3."""
+    pr = synth.make_problem(80, 300, 60, lam_kind=kind, seed=4, theta_nnz=3)
+    Lam = pr.Lambda_true
+    Th = 0.5 * pr.Theta_true.toarray()
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    G_L, _, _, _ = oracle.gradients(Lam.toarray(), Th, Sxx, Sxy, Syy)
+    for c0, k in ((0, 64), (250, 50), (123, 1)):
+        G, iters = ctx.cggm_grad_lambda_block(pr.X, pr.Y, *csr(Lam), Th, c0, k, tol=1e-12,
+                                              max_iter=3000)
+        assert 0 < iters < 3000
+        assert rel(G, G_L[:, c0:c0 + k]) < 1e-9
+    with pytest.raises(cg.CGGMError):
+        ctx.cggm_grad_lambda_block(pr.X, pr.Y, *csr(Lam), Th, 290, 20)
