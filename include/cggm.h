@@ -61,6 +61,9 @@ typedef enum {
  * inputs are genotype counts (Section 5.2). */
 typedef enum { CGGM_F32 = 0, CGGM_F64 = 1, CGGM_BF16 = 2, CGGM_I8_GENO = 3 } cggm_dtype;
 
+/* opts.sweep_batch value that lets the batch-size tuner choose (see cggm_tuned_batch). */
+#define CGGM_SWEEP_BATCH_AUTO (-1)
+
 typedef struct {
     double tol;          /* stopping ratio of Section 5.1: stop when
                             ||grad^S f||_1 < tol (||Lambda||_1 + ||Theta||_1); 0.01      */
@@ -70,8 +73,9 @@ typedef struct {
     double ls_beta;      /* Armijo step shrink factor; 0.5                                */
     int ls_max_trials;   /* Armijo trials before CGGM_ELINESEARCH; 50                     */
     int penalize_diag;   /* include diag(Lambda) in ||Lambda||_1; 1                       */
-    int sweep_batch;     /* coordinates per blocked Gauss-Seidel batch: 32, 64, 128, or   
-                            256 and 512 in the mixed path; 0 = default (128 FP64, 256)  */
+    int sweep_batch;     /* coordinates per blocked Gauss-Seidel batch: 32, 64, 128, or
+                            256 and 512 in the mixed path; 0 = default (128 FP64, 256);
+                            CGGM_SWEEP_BATCH_AUTO = chosen by the tuner (cggm_tuned_batch) */
     double target_f;     /* also stop once f <= target_f (time-to-gap runs); -inf = off  */
     int verbose;         /* per-iteration line on stderr                                  */
 } cggm_opts;
@@ -245,6 +249,15 @@ void cggm_server_destroy(cggm_server *srv);
 /* Device bytes a request of this size is accounted for (workspace of cggm_solve plus the
  * request's own device copies); -1 for invalid sizes. */
 int64_t cggm_footprint(int64_t n, int64_t p, int64_t q, int precision);
+
+/* The batch size (the tile shape of the coordinate-pass kernels) that the tuner chose for a
+ * size class: precision (cggm_precision), q and the Lambda active-set size m, each rounded up
+ * to a power of two.  A solve with opts.sweep_batch = CGGM_SWEEP_BATCH_AUTO times the Lambda
+ * pass at every candidate batch size in its first Newton iteration of a class it has not
+ * seen, keeps the fastest for the process (shared by all contexts and threads), and uses it
+ * for both passes.  Returns the chosen size, 0 if the class has not been tuned yet, -1 for
+ * bad arguments.  The paper has no counterpart (its passes visit one coordinate at a time). */
+int cggm_tuned_batch(int64_t q, int64_t m, int precision);
 
 /* Dense contraction on the tensor cores, the form every product from X takes in the mixed
  * path (R = X Theta, P = R Sigma, Psi = P^T P / n, X^T (Y + P); Section 2.3 lists them):

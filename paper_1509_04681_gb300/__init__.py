@@ -20,6 +20,8 @@ from .cggm import (  # noqa: F401
     CGGM_F64,
     CGGM_BF16,
     CGGM_I8_GENO,
+    CGGM_SWEEP_BATCH_AUTO,
+    tuned_batch,
     CGGM_MIXED,
     CGGM_OK,
     CGGM_EMAXITER,

@@ -23,13 +23,14 @@ CGGM_OK, CGGM_EINVAL, CGGM_ENOTPD, CGGM_ENOMEM, CGGM_EMAXITER = 0, -1, -2, -3, -
 CGGM_ELINESEARCH, CGGM_ECUDA, CGGM_ETIMEDOUT, CGGM_ENONFINITE, CGGM_ECANCELLED = -5, -6, -7, -8, -9
 CGGM_FP64, CGGM_MIXED = 0, 1
 CGGM_F32, CGGM_F64, CGGM_BF16, CGGM_I8_GENO = 0, 1, 2, 3
+CGGM_SWEEP_BATCH_AUTO = -1
 
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
-    "cggm_spd_solve", "cggm_grad_lambda_block",
+    "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch",
 ]
 
 
@@ -118,6 +119,8 @@ def _lib():
         lib.cggm_server_destroy.restype = None
         lib.cggm_footprint.argtypes = [i64, i64, i64, ip]
         lib.cggm_footprint.restype = i64
+        lib.cggm_tuned_batch.argtypes = [i64, i64, ip]
+        lib.cggm_tuned_batch.restype = ip
         lib.cggm_lambda_sweep_noalloc.argtypes = [i64, vp, vp, vp, vp, i64, vp, vp, dbl, ip, vp,
                                                   vp]
         lib.cggm_spd_solve.argtypes = [vp, i64, vp, vp, vp, i64, vp, i64, dbl, ip, vp,
@@ -375,6 +378,11 @@ class Context:
                                        lj.ctypes.data, ctypes.byref(mL), ti.ctypes.data,
                                        tj.ctypes.data, ctypes.byref(mT)), "cggm_active_sets")
         return li[:mL.value], lj[:mL.value], ti[:mT.value], tj[:mT.value]
+
+
+def tuned_batch(q: int, m: int, precision: int) -> int:
+    """Batch size the tuner chose for the size class of (q, m, precision); 0 if not tuned yet."""
+    return _lib().cggm_tuned_batch(int(q), int(m), int(precision))
 
 
 def make_opts(**kw) -> cggm_opts:

@@ -8,6 +8,10 @@
 
 #include "cg.cuh"
 #include "chol.cuh"
+
+#include <map>
+#include <mutex>
+#include <tuple>
 #include "common.cuh"
 #include "dense.cuh"
 #include "gemm_tc.cuh"
@@ -53,6 +57,37 @@ bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------------------------
+// Batch-size tuner of the coordinate passes.  The batch size B is the tile shape of the
+// sweep kernels: larger batches amortise the per-batch barriers over more coordinates but
+// lengthen the serial phase and the coefficient work.  For opts.sweep_batch = -1, the first
+// Newton iteration of a size class (precision, q and the Lambda active-set size, each rounded
+// up to a power of two) times the Lambda pass at every candidate B and keeps the fastest for
+// the process; later solves of the class reuse it.
+// ---------------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int>, int> g_tuned;
+
+int log2_ceil(int64_t v) {
+    int r = 0;
+    while (((int64_t)1 << r) < v) r++;
+    return r;
+}
+std::tuple<int, int, int> tune_key(int precision, int64_t q, int64_t m) {
+    return std::make_tuple(precision, log2_ceil(q < 1 ? 1 : q), log2_ceil(m < 1 ? 1 : m));
+}
+int tuned_lookup(int precision, int64_t q, int64_t m) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    const auto it = g_tuned.find(tune_key(precision, q, m));
+    return it == g_tuned.end() ? 0 : it->second;
+}
+void tuned_store(int precision, int64_t q, int64_t m, int B) {
+    std::lock_guard<std::mutex> lk(g_tune_mutex);
+    g_tuned[tune_key(precision, q, m)] = B;
+}
 }  // namespace
 
 struct cggm_ctx {
@@ -460,7 +495,10 @@ struct Solver {
         CGGM_TRY(factor(c->Lam, c->Lch, c->logd, S_LOGDET));
         sigma_from_factor();
 
-        const int B = o.sweep_batch > 0 ? o.sweep_batch : (sizeof(T) == 8 ? 128 : 256);
+        const int B_default = sizeof(T) == 8 ? 128 : 256;
+        int B = o.sweep_batch > 0 ? o.sweep_batch : B_default;
+        const bool autotune = o.sweep_batch == CGGM_SWEEP_BATCH_AUTO;
+        const int prec_key = sizeof(T) == 8 ? CGGM_FP64 : CGGM_MIXED;
         double h[S_COUNT];
         int64_t hc[2];
         bool converged = false;
@@ -533,13 +571,41 @@ struct Solver {
             // ---- Lambda direction (Section 3.1) ----
             coords_l += hc[0];
             coords_t += hc[1];
+            auto lambda_pass = [&](int Bp) -> cggm_status {
+                CGGM_CUDA_TRY(cudaMemsetAsync(c->D.p, 0, 8 * qq, st));
+                CGGM_CUDA_TRY(cudaMemsetAsync(c->U.p, 0, sizeof(T) * qq, st));
+                return lambda_sweep<T>(q, SigT(), (const T *)c->Psi.p, P<double>(c->Sd),
+                                       P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam),
+                                       hc[0], P<int32_t>(c->li), P<int32_t>(c->lj), lamL, lamLd,
+                                       P<double>(c->D), (T *)c->U.p, Bp, c->scr, st);
+            };
+            if (autotune) {
+                const int tb = tuned_lookup(prec_key, q, hc[0]);
+                if (tb > 0) {
+                    B = tb;
+                } else if (hc[0] > 0) {
+                    // time the pass at each candidate (each run recomputes D from zero)
+                    const int cands_f[] = {64, 128, 256, 512}, cands_d[] = {32, 64, 128};
+                    const int *cands = sizeof(T) == 8 ? cands_d : cands_f;
+                    const int nc = sizeof(T) == 8 ? 3 : 4;
+                    float best = -1.0f;
+                    for (int ci = 0; ci < nc; ci++) {
+                        cudaEventRecord(ev[3], st);
+                        CGGM_TRY(lambda_pass(cands[ci]));
+                        cudaEventRecord(ev[4], st);
+                        CGGM_CUDA_TRY(cudaEventSynchronize(ev[4]));
+                        float ms = 0.0f;
+                        cudaEventElapsedTime(&ms, ev[3], ev[4]);
+                        if (best < 0.0f || ms < best) {
+                            best = ms;
+                            B = cands[ci];
+                        }
+                    }
+                    tuned_store(prec_key, q, hc[0], B);
+                }
+            }
             cudaEventRecord(ev[3], st);
-            CGGM_CUDA_TRY(cudaMemsetAsync(c->D.p, 0, 8 * qq, st));
-            CGGM_CUDA_TRY(cudaMemsetAsync(c->U.p, 0, sizeof(T) * qq, st));
-            CGGM_TRY(lambda_sweep<T>(q, SigT(), (const T *)c->Psi.p, P<double>(c->Sd),
-                                     P<double>(c->Pd), P<double>(c->GL), P<double>(c->Lam), hc[0],
-                                     P<int32_t>(c->li), P<int32_t>(c->lj), lamL, lamLd,
-                                     P<double>(c->D), (T *)c->U.p, B, c->scr, st));
+            CGGM_TRY(lambda_pass(B));
             cudaEventRecord(ev[4], st);
             // ---- Armijo (Algorithm 1) ----
             // delta = tr(G D) + lamL (||Lam + D||_1 - ||Lam||_1)
@@ -744,7 +810,8 @@ cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, in
     if (tol > 0.0) o.tol = tol;
     if (!(o.tol > 0.0) || o.max_iter < 0 || o.ls_max_trials < 1 || !(o.ls_beta > 0.0 && o.ls_beta < 1.0))
         return CGGM_EINVAL;
-    if (o.sweep_batch != 0 && o.sweep_batch != 32 && o.sweep_batch != 64 && o.sweep_batch != 128 &&
+    if (o.sweep_batch != 0 && o.sweep_batch != CGGM_SWEEP_BATCH_AUTO && o.sweep_batch != 32 &&
+        o.sweep_batch != 64 && o.sweep_batch != 128 &&
         !((o.sweep_batch == 256 || o.sweep_batch == 512) && o.precision == CGGM_MIXED))
         return CGGM_EINVAL;
     if (info) memset(info, 0, sizeof(*info));
@@ -1140,6 +1207,11 @@ cggm_status cggm_grad_lambda_block(cggm_ctx *c, const void *X, int xdtype, const
     CGGM_TRY(store_double(c, G_out, c->bk_g.p, qk));
     if (iters_out) *iters_out = it1 > it2 ? it1 : it2;
     return sync_err(c);
+}
+
+int cggm_tuned_batch(int64_t q, int64_t m, int precision) {
+    if (q < 1 || m < 0 || (precision != CGGM_FP64 && precision != CGGM_MIXED)) return -1;
+    return tuned_lookup(precision, q, m);
 }
 
 cggm_status cggm_contract(cggm_ctx *c, int64_t M, int64_t N, int64_t K, float alpha,

@@ -234,6 +234,21 @@ def test_solve_batch_of_512_matches_oracle(ctx):
     check_solution(pr, r, ref, ref.f)
 
 
+def test_solve_with_tuned_batch_size(ctx):
+    """sweep_batch = auto: the first iteration of a new size class times the Lambda pass at
+    every candidate batch size and keeps the fastest; the solve meets the same bar."""
+    pr = synth.workload("chain-gauss-p200-q100-n100")
+    ref = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, max_iter=3000)
+    o = cg.make_opts(precision=cg.CGGM_MIXED, max_iter=3000, sweep_batch=cg.CGGM_SWEEP_BATCH_AUTO)
+    r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, opts=o)
+    check_solution(pr, r, ref, ref.f)
+    assert r.info["m_lambda"] > 0
+    tuned = [cg.tuned_batch(100, m, cg.CGGM_MIXED) for m in (r.info["m_lambda"], 5050)]
+    assert any(b in (64, 128, 256, 512) for b in tuned)
+    assert cg.tuned_batch(100, 10 ** 9, cg.CGGM_MIXED) == 0  # a class never seen
+    assert cg.tuned_batch(0, 10, cg.CGGM_MIXED) == -1
+
+
 def test_solve_first_iterates_track_oracle(ctx):
     """FP64 path: the objective after each of the first iterations equals the oracle's."""
     pr = problem(60, 40, 50, seed=8, lam=0.1)
