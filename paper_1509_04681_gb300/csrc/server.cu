@@ -97,7 +97,6 @@ void cggm_server::run(Job *j, cggm_ctx *ctx) {
     cggm_opts_default(&o);
     o.max_iter = r.max_iter > 0 ? r.max_iter : o.max_iter;
     o.precision = r.precision;
-    o.sweep_batch = CGGM_SWEEP_BATCH_AUTO;  // batch size per size class, tuned once
     int iters = 0;
     double f = 0.0;
     for (size_t k = 0; k < j->lambdas.size() && st == CGGM_OK; k++) {
