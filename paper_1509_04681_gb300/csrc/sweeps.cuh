@@ -57,7 +57,7 @@ constexpr size_t scratch_sub2_bytes(int B, size_t esz) {
     return esz * (2 * (size_t)coef_slots(B) + (size_t)B * B + (size_t)B);
 }
 
-// Allocates the scratch once, for B 512 in float (which also covers B <= 128 in double).
+// Allocates the scratch once, for B 256 in float (which also covers B <= 128 in double).
 cggm_status scratch_reserve(SweepScratch &scr);
 void scratch_free(SweepScratch &scr);
 
