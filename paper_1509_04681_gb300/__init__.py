@@ -22,6 +22,8 @@ from .cggm import (  # noqa: F401
     CGGM_I8_GENO,
     CGGM_SWEEP_BATCH_AUTO,
     tuned_batch,
+    partition_columns,
+    partition_theta_columns,
     CGGM_MIXED,
     CGGM_OK,
     CGGM_EMAXITER,

@@ -23,11 +23,12 @@ def _nvcc() -> str:
 
 
 def sources():
-    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
+    """CUDA sources and the host-only C++ of the library (compiled by nvcc as well)."""
+    return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cpp")))
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every csrc/*.cu for sm_103a (in parallel) and link libcggm.so."""
+    """Compile every csrc/*.cu (sm_103a) and csrc/*.cpp (host) in parallel and link libcggm.so."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + \

@@ -30,7 +30,8 @@ EXPORTED = [
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
-    "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch",
+    "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
+    "cggm_partition_theta_columns",
 ]
 
 
@@ -127,6 +128,10 @@ def _lib():
                                        ctypes.POINTER(ip), ctypes.POINTER(dbl)]
         lib.cggm_grad_lambda_block.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, vp, vp,
                                                i64, i64, dbl, ip, vp, ctypes.POINTER(ip)]
+        lib.cggm_partition_columns.argtypes = [i64, i64, vp, vp, vp, i64, vp,
+                                               ctypes.POINTER(i64), ctypes.POINTER(dbl)]
+        lib.cggm_partition_theta_columns.argtypes = [i64, i64, i64, vp, vp, i64, vp,
+                                                     ctypes.POINTER(i64), ctypes.POINTER(i64)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -136,6 +141,8 @@ def _lib():
                                                      "cggm_lambda_sweep_noalloc",
                                                      "cggm_contract", "cggm_server_create",
                                                      "cggm_spd_solve", "cggm_grad_lambda_block",
+                                                     "cggm_partition_columns",
+                                                     "cggm_partition_theta_columns",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -383,6 +390,56 @@ class Context:
 def tuned_batch(q: int, m: int, precision: int) -> int:
     """Batch size the tuner chose for the size class of (q, m, precision); 0 if not tuned yet."""
     return _lib().cggm_tuned_batch(int(q), int(m), int(precision))
+
+
+def _host_i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def partition_columns(q: int, ei, ej, max_block: int, w=None):
+    """Column blocks for the block coordinate descent of Algorithm 2
+    (cggm_partition_columns): the graph on q columns with edges (ei[t], ej[t]) of weight
+    w[t] (default 1) cut into blocks of at most max_block columns.  Host memory only.
+    Returns (block, nblocks, cut): the block id of every column, the number of blocks and
+    the weight of the edges between blocks."""
+    ei, pi = _host_i32(ei)
+    ej, pj = _host_i32(ej)
+    if ei.shape != ej.shape:
+        raise ValueError("ei and ej differ in length")
+    pw = None
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != ei.shape:
+            raise ValueError("w and ei differ in length")
+        pw = w.ctypes.data_as(ctypes.c_void_p)
+    block = np.empty(max(int(q), 0), dtype=np.int32)
+    k = ctypes.c_int64()
+    cut = ctypes.c_double()
+    _check(_lib().cggm_partition_columns(int(q), int(ei.size), pi, pj, pw, int(max_block),
+                                         block.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k),
+                                         ctypes.byref(cut)), "cggm_partition_columns")
+    return block, int(k.value), float(cut.value)
+
+
+def partition_theta_columns(p: int, q: int, ti, tj, max_block: int):
+    """Column blocks for the blocked Theta pass of Algorithm 2
+    (cggm_partition_theta_columns) from the active coordinates (ti, tj).  Host memory only.
+    Returns (block, nblocks, row_blocks): row_blocks is the number of (row, block) pairs
+    holding an active entry, the cost Section 4.2 minimises."""
+    ti, pi = _host_i32(ti)
+    tj, pj = _host_i32(tj)
+    if ti.shape != tj.shape:
+        raise ValueError("ti and tj differ in length")
+    block = np.empty(max(int(q), 0), dtype=np.int32)
+    k = ctypes.c_int64()
+    rb = ctypes.c_int64()
+    _check(_lib().cggm_partition_theta_columns(int(p), int(q), int(ti.size), pi, pj,
+                                               int(max_block),
+                                               block.ctypes.data_as(ctypes.c_void_p),
+                                               ctypes.byref(k), ctypes.byref(rb)),
+           "cggm_partition_theta_columns")
+    return block, int(k.value), int(rb.value)
 
 
 def make_opts(**kw) -> cggm_opts:
