@@ -225,6 +225,19 @@ def cpu_oracle_rate(pr, budget_s=25.0):
             "seconds_measured": round(time.perf_counter() - t0, 2)}
 
 
+def reference_config(pr):
+    """The workload the reference arm ran: sizes from the generated problem, recipe from
+    the workload table."""
+    import synth
+    w = synth.WORKLOADS[WORKLOAD]
+    x = ("genotype Binomial(2, MAF~U(0.05,0.5)) standardised" if w["x_kind"] == "genotype"
+         else "iid N(0,1) standardised")
+    net = "chain (1.0 / 0.4)" if w["lam_kind"] == "chain" else w["lam_kind"]
+    return {"workload": WORKLOAD, "p": int(pr.X.shape[1]), "q": int(pr.Y.shape[1]),
+            "n": int(pr.X.shape[0]), "lambda": pr.lam_L, "x": x, "network": net,
+            "theta_nnz_per_col": w["theta_nnz"], "seed": w["seed"]}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -242,9 +255,7 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "p": 5000, "q": 5000, "n": 1000, "lambda": 0.05,
-                       "x": "genotype Binomial(2, MAF~U(0.05,0.5)) standardised",
-                       "network": "chain (1.0 / 0.4)", "theta_nnz_per_col": 10, "seed": 0},
+            "config": reference_config(pr),
             "cpu_baseline": {"kind": "oracle", "cores": rates[0]["cores"],
                              "sample": rates[0]["sample"], "value": v,
                              "unit": "Newton iterations/s"},

@@ -29,3 +29,36 @@ def test_traffic_is_null_for_other_kernels_and_changed_sources(tmp_path, monkeyp
     src = root / bench.SWEEP_SOURCES[0]
     src.write_bytes(src.read_bytes() + b" ")
     assert bench.profiled_traffic("lambda_sweep_kernel", 1000) is None
+
+
+def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):
+    """--impl reference times the oracle on the host cores and prints one JSON line with
+    the contract's keys; run here on the small chain workload to stay quick."""
+    import json
+    import types
+    monkeypatch.setattr(bench, "WORKLOAD", "chain-gauss-p200-q100-n100")
+    monkeypatch.delenv("RANK", raising=False)
+    args = types.SimpleNamespace(steps=1, warmup=0, gpus=1)
+    bench.run_reference(args)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-9 * d["ms_per_step"]
+    c = d["config"]
+    assert (c["workload"], c["p"], c["q"], c["n"]) == ("chain-gauss-p200-q100-n100", 200, 100, 100)
+
+
+def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
+    import types
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(types.SimpleNamespace(steps=1, warmup=0, gpus=2))
+    assert capsys.readouterr().out == ""
