@@ -380,12 +380,12 @@ struct Solver {
         return sizeof(T) == 8 ? (const T *)c->Sig.p : (const T *)c->Sig_f.p;
     }
 
-    // Rt = Theta^T X^T (q x n) in double (it enters the double-precision objective);
-    // Pt = Sigma Rt: double, or float on the tensor cores in the mixed path
+    // Rt = Theta^T X^T (q x n) in double (it enters the double-precision objective), over
+    // Theta's nonzeros only; Pt = Sigma Rt: double, or float on the tensor cores in the
+    // mixed path
     cggm_status products_R_P() {
         const int64_t n = z.n, p = z.p, q = z.q;
-        gemm<double>(true, false, q, n, p, 1.0, P<double>(c->Th), q, P<double>(c->Xt), n, 0.0,
-                     P<double>(c->Rt), n, st);
+        theta_t_xt(p, q, n, P<double>(c->Th), P<double>(c->Xt), P<double>(c->Rt), st);
         if (tc()) {
             transpose<double, float>(q, n, P<double>(c->Rt), P<float>(c->R_f), st);
             split_tf32(n, q, q, P<float>(c->R_f), P<float>(c->R_hi), P<float>(c->R_lo), st);
@@ -866,8 +866,7 @@ cggm_status cggm_objective(cggm_ctx *c, const void *X, int xdtype, const void *Y
     CGGM_TRY(load_double(c, Theta, pq, c->Th));
     CGGM_TRY(S.factor(c->Lam, c->Lch, c->logd, S_LOGDET));
     // trace tr(Lambda^-1 Theta^T S_xx Theta) = ||L^-1 (X Theta)^T||_F^2 / n
-    gemm<double>(true, false, q, n, p, 1.0, P<double>(c->Th), q, P<double>(c->Xt), n, 0.0,
-                 P<double>(c->Rt), n, c->st);
+    theta_t_xt(p, q, n, P<double>(c->Th), P<double>(c->Xt), P<double>(c->Rt), c->st);
     CGGM_CUDA_TRY(cudaMemcpyAsync(c->Z.p, c->Rt.p, 8 * (size_t)q * n, cudaMemcpyDeviceToDevice, c->st));
     trsm_lower_inplace(q, P<double>(c->Lch), q, P<double>(c->Z), n, n, false, c->st);
     double *s = P<double>(c->scal);
@@ -1033,7 +1032,7 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
     rowsq_kernel<double><<<(unsigned)p, 256, 0, c->st>>>(p, n, Xt, inv, P<double>(c->Xd));
     diag_to_double<double>(q, P<double>(c->Sig), P<double>(c->Sd), c->st);
     // W = S_xy + S_xx Theta Sigma
-    gemm<double>(true, false, q, n, p, 1.0, P<double>(c->Th), q, Xt, n, 0.0, P<double>(c->Rt), n, c->st);
+    theta_t_xt(p, q, n, P<double>(c->Th), Xt, P<double>(c->Rt), c->st);
     gemm<double>(false, false, q, n, q, 1.0, P<double>(c->Sig), q, P<double>(c->Rt), n, 0.0,
                  P<double>(c->Pt), n, c->st);
     CGGM_CUDA_TRY(cudaMemcpyAsync(c->W.p, c->Sxy.p, 8 * pq, cudaMemcpyDeviceToDevice, c->st));
@@ -1186,8 +1185,7 @@ cggm_status cggm_grad_lambda_block(cggm_ctx *c, const void *X, int xdtype, const
     const double *va = P<double>(c->cg_v);
     const double inv = 1.0 / (double)n;
     // R^T = Theta^T X^T (q x n); P^T = Sigma R^T from Lambda P^T = R^T; Sigma[:, C]
-    gemm<double>(true, false, q, n, p, 1.0, P<double>(c->bk_th), q, P<double>(c->Xt), n, 0.0,
-                 P<double>(c->bk_rt), n, st);
+    theta_t_xt(p, q, n, P<double>(c->bk_th), P<double>(c->Xt), P<double>(c->bk_rt), st);
     int it1 = 0, it2 = 0;
     double res = 0.0;
     cggm_status s = pcg_solve(q, rp, ci, va, n, P<double>(c->bk_rt), 0, tol, max_iter,

@@ -175,6 +175,63 @@ __global__ void diag_kernel(int64_t n, const T *A, double *d) {
          i += (int64_t)gridDim.x * blockDim.x)
         d[i] = (double)A[i * n + i];
 }
+// R^T = Theta^T X^T with a sparse Theta (see theta_t_xt).  One CTA per column j of Theta:
+// the column is scanned in chunks of kSpThreads rows; each chunk's nonzeros are compacted
+// into shared memory in ascending row order (a ballot per warp, an exclusive prefix over
+// the warps), then every thread adds them, in that order, into its entries of row j of
+// R^T, kSpPerThread entries a thread per pass over n.
+constexpr int kSpThreads = 256;
+constexpr int kSpPerThread = 4;
+__global__ void __launch_bounds__(kSpThreads)
+theta_t_xt_kernel(int64_t p, int64_t q, int64_t n, const double *__restrict__ Th,
+                  const double *__restrict__ Xt, double *__restrict__ Rt) {
+    __shared__ int s_off[kSpThreads];
+    __shared__ double s_val[kSpThreads];
+    __shared__ int s_count[kSpThreads / 32];
+    const int64_t j = blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t span = (int64_t)kSpThreads * kSpPerThread;
+    for (int64_t t0 = 0; t0 < n; t0 += span) {
+        double acc[kSpPerThread];
+#pragma unroll
+        for (int k = 0; k < kSpPerThread; k++) acc[k] = 0.0;
+        for (int64_t i0 = 0; i0 < p; i0 += kSpThreads) {
+            const int64_t i = i0 + tid;
+            const double v = i < p ? Th[i * q + j] : 0.0;
+            const unsigned mask = __ballot_sync(0xffffffffu, v != 0.0);
+            if (lane == 0) s_count[warp] = __popc(mask);
+            __syncthreads();
+            int base = 0, total = 0;
+#pragma unroll
+            for (int w = 0; w < kSpThreads / 32; w++) {
+                base += w < warp ? s_count[w] : 0;
+                total += s_count[w];
+            }
+            if (v != 0.0) {
+                const int pos = base + __popc(mask & ((1u << lane) - 1u));
+                s_off[pos] = tid;
+                s_val[pos] = v;
+            }
+            __syncthreads();
+            for (int e = 0; e < total; e++) {
+                const double th = s_val[e];
+                const double *x = Xt + (i0 + s_off[e]) * n + t0;
+#pragma unroll
+                for (int k = 0; k < kSpPerThread; k++) {
+                    const int64_t t = tid + (int64_t)k * kSpThreads;
+                    if (t0 + t < n) acc[k] = fma(th, x[t], acc[k]);
+                }
+            }
+            __syncthreads();  // the next chunk rewrites s_count, s_off, s_val
+        }
+#pragma unroll
+        for (int k = 0; k < kSpPerThread; k++) {
+            const int64_t t = t0 + tid + (int64_t)k * kSpThreads;
+            if (t < n) Rt[j * n + t] = acc[k];
+        }
+    }
+}
+
 inline unsigned grid_for(int64_t len) {
     int64_t g = (len + 255) / 256;
     int64_t cap = (int64_t)sm_count() * 16;
@@ -224,6 +281,14 @@ template void transpose<double, double>(int64_t, int64_t, const double *, double
 template void transpose<double, float>(int64_t, int64_t, const double *, float *, cudaStream_t);
 template void transpose<float, float>(int64_t, int64_t, const float *, float *, cudaStream_t);
 template void transpose<float, double>(int64_t, int64_t, const float *, double *, cudaStream_t);
+
+void theta_t_xt(int64_t p, int64_t q, int64_t n, const double *Th, const double *Xt, double *Rt,
+                cudaStream_t st) {
+    if (q > 0 && n > 0) {
+        note_launch();
+        theta_t_xt_kernel<<<(unsigned)q, kSpThreads, 0, st>>>(p, q, n, Th, Xt, Rt);
+    }
+}
 
 template <typename T>
 void symmetrize_lower(int64_t n, T *A, cudaStream_t st) {

@@ -30,6 +30,14 @@ void convert_f2d(int64_t len, const float *x, double *y, cudaStream_t st);
 template <typename Tin, typename Tout>
 void transpose(int64_t rows, int64_t cols, const Tin *in, Tout *out, cudaStream_t st);
 
+// R^T = Theta^T X^T for a sparse Theta held densely (p x q, row-major) and X^T (p x n,
+// row-major), into R^T (q x n, row-major): R = X Theta costs O(n m_Theta) with Theta's
+// nonzeros (Section 3.2) instead of the O(n p q) of a dense product.  Row j of R^T sums
+// Theta_ij X^T_i over the nonzero Theta_ij in ascending i, one fused multiply-add at a
+// time, so the result does not depend on the launch.
+void theta_t_xt(int64_t p, int64_t q, int64_t n, const double *Th, const double *Xt, double *Rt,
+                cudaStream_t st);
+
 // Mirror the lower triangle of a square matrix into the upper one.
 template <typename T>
 void symmetrize_lower(int64_t n, T *A, cudaStream_t st);

@@ -84,6 +84,31 @@ def test_grad_and_objective(ctx, shape):
         assert abs(f - f_ref) < 1e-11 * abs(f_ref)
 
 
+def test_grad_and_objective_sparse_theta_edges(ctx):
+    """R = X Theta is formed over Theta's nonzeros (scanned in chunks of 256 rows, summed
+    over n in passes of 1024): p = 300 and n = 1300 take two of each with a ragged tail;
+    Theta has an empty column, a dense one, one whose only entry is in the last row, and
+    scattered entries elsewhere; and Theta = 0."""
+    p, q, n = 300, 9, 1300
+    pr = problem(p, q, n, seed=77)
+    rng = np.random.default_rng(77)
+    Th = np.where(rng.random((p, q)) < 0.05, rng.standard_normal((p, q)) * 0.1, 0.0)
+    Th[:, 0] = 0.0
+    Th[:, 1] = rng.standard_normal(p) * 0.05
+    Th[:, 2] = 0.0
+    Th[p - 1, 2] = 0.3
+    Lam = synth.chain_precision(q).toarray()
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    for T in (Th, np.zeros((p, q))):
+        G_L, G_T, _, _ = oracle.gradients(Lam, T, Sxx, Sxy, Syy)
+        gL, gT = ctx.cggm_grad(pr.X, pr.Y, Lam, T)
+        assert rel(gL, G_L) < 1e-10
+        assert rel(gT, G_T) < 1e-10
+        f_ref = oracle.objective(Lam, T, Sxx, Sxy, Syy, 0.1, 0.2)
+        f = ctx.cggm_objective(pr.X, pr.Y, Lam, T, 0.1, 0.2)
+        assert abs(f - f_ref) < 1e-11 * abs(f_ref)
+
+
 # ------------------------------------------------------------------------------------
 # active sets: integer work, bit-exact
 # ------------------------------------------------------------------------------------
