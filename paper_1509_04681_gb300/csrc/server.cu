@@ -47,8 +47,14 @@ struct cggm_server {
     double now() const {
         return std::chrono::duration<double>(Clock::now() - t0).count();
     }
+    struct Outcome {
+        cggm_status status;
+        int iterations;
+        double f_last;
+    };
     void worker_loop();
-    void run(Job *j, cggm_ctx *ctx);
+    // solves the request's path; touches no field of the job (pollers read it under mu)
+    Outcome run(const Job *j, cggm_ctx *ctx);
 };
 
 namespace {
@@ -76,7 +82,7 @@ int64_t footprint_bytes(int64_t n, int64_t p, int64_t q, int precision) {
 
 }  // namespace
 
-void cggm_server::run(Job *j, cggm_ctx *ctx) {
+cggm_server::Outcome cggm_server::run(const Job *j, cggm_ctx *ctx) {
     const cggm_request &r = j->req;
     const int64_t n = r.n, p = r.p, q = r.q;
     const size_t xs = cggm::dtype_size(r.xdtype) * (size_t)(n * p);
@@ -121,9 +127,7 @@ void cggm_server::run(Job *j, cggm_ctx *ctx) {
     cudaFree(dY);
     cudaFree(dL);
     cudaFree(dT);
-    j->res.status = st;
-    j->res.iterations = iters;
-    j->res.f_last = f;
+    return {st, iters, f};
 }
 
 void cggm_server::worker_loop() {
@@ -153,14 +157,16 @@ void cggm_server::worker_loop() {
             j->res.start_s = now();
         }
         cggm_ctx *ctx = nullptr;
-        if (cggm_create(&ctx, device, nullptr) != CGGM_OK) {
-            j->res.status = CGGM_ECUDA;
-        } else {
-            run(j, ctx);
+        Outcome out{CGGM_ECUDA, 0, 0.0};
+        if (cggm_create(&ctx, device, nullptr) == CGGM_OK) {
+            out = run(j, ctx);
             cggm_destroy(ctx);  // return the workspace: the budget accounts for it exactly
         }
         {
             std::lock_guard<std::mutex> lk(mu);
+            j->res.status = out.status;
+            j->res.iterations = out.iterations;
+            j->res.f_last = out.f_last;
             in_use -= j->footprint;
             j->res.finish_s = now();
             j->res.done = 1;
