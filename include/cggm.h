@@ -162,15 +162,23 @@ cggm_status cggm_grad(cggm_ctx *ctx, const void *X, int xdtype, const void *Y, i
 
 /* Cholesky Lambda = L L^T (lower L, row-major q x q, upper part of L_out set to 0),
  * log|Lambda| = 2 sum log L_ii, and Sigma = Lambda^-1 (Section 2.3's Cholesky
- * initialisation of Sigma).  Sigma_out may be NULL.  CGGM_ENOTPD if not positive
- * definite. */
+ * initialisation of Sigma), all in double (`precision` is ignored).  Lambda is read, the
+ * outputs written, in host or device memory owned by the caller; L_out, logdet_out and
+ * Sigma_out may each be NULL.  Errors: CGGM_EINVAL for q <= 0 or a null Lambda;
+ * CGGM_ENOTPD if Lambda is not positive definite (a pivot <= 0 or not finite). */
 cggm_status cggm_cholesky(cggm_ctx *ctx, int64_t q, const double *Lambda, double *L_out,
                           double *logdet_out, double *Sigma_out, int precision);
 
 /* One coordinate-descent pass for the Newton direction of Lambda (Section 3.1, Eq. 7;
  * coordinate step of Appendix A.1 with the curvature of the exact quadratic model).
- * (ai[k], aj[k]), ai <= aj, k < m, are the active coordinates in visiting order.
- * D_out (q x q) receives the symmetric direction. */
+ * Sigma, Psi, Syy, Lambda: q x q row-major double.  (ai[k], aj[k]), ai <= aj, k < m, are
+ * the active coordinates in visiting order.  D_out (q x q) receives the symmetric
+ * direction.  precision: CGGM_FP64 (caches in double, batches of 128) or CGGM_MIXED
+ * (caches in float, batches of 256).  All buffers host or device, owned by the caller.
+ * Errors: CGGM_EINVAL for q <= 0, m < 0, a null pointer, another precision, or an index
+ * pair outside 0 <= ai <= aj < q (checked on the host before any kernel runs);
+ * CGGM_ETIMEDOUT if a device wait of the pass gave up; CGGM_ENONFINITE for a NaN or Inf
+ * met in a step. */
 cggm_status cggm_lambda_sweep(cggm_ctx *ctx, int64_t q, const double *Sigma,
                               const double *Psi, const double *Syy, const double *Lambda,
                               int64_t m, const int32_t *ai, const int32_t *aj, double lam_L,
@@ -178,8 +186,13 @@ cggm_status cggm_lambda_sweep(cggm_ctx *ctx, int64_t q, const double *Sigma,
 
 /* One coordinate-descent pass on Theta with Lambda fixed (Section 3.2, Eq. 8; Appendix
  * A.1 coordinate step with curvature 2 Sigma_jj (S_xx)_ii).  X is n x p (double), S_xy
- * p x q, Sigma q x q; (ti[k], tj[k]) the active coordinates in visiting order.  Theta
- * (p x q) is read from Theta_in and the result written to Theta_out (may alias). */
+ * p x q, Sigma q x q, all row-major; (ti[k], tj[k]), k < m, the active coordinates in
+ * visiting order.  Theta (p x q) is read from Theta_in and the result written to
+ * Theta_out (may alias).  precision as for cggm_lambda_sweep.  All buffers host or
+ * device, owned by the caller.  Errors: CGGM_EINVAL for sizes <= 0, m < 0, a null
+ * pointer, another precision, or an index outside 0 <= ti < p, 0 <= tj < q (checked on
+ * the host before any kernel runs); CGGM_ETIMEDOUT and CGGM_ENONFINITE as for
+ * cggm_lambda_sweep. */
 cggm_status cggm_theta_sweep(cggm_ctx *ctx, int64_t n, int64_t p, int64_t q,
                              const double *X, const double *Sxy, const double *Sigma,
                              const double *Theta_in, int64_t m, const int32_t *ti,
@@ -188,8 +201,11 @@ cggm_status cggm_theta_sweep(cggm_ctx *ctx, int64_t n, int64_t p, int64_t q,
 
 /* Active sets of Section 2.2 from gradients and parameters: Lambda entries (i <= j) with
  * |G_Lambda| > lam_L or Lambda != 0, Theta entries with |G_Theta| > lam_T or Theta != 0,
- * both in row-major order.  The index buffers must hold q(q+1)/2 and p q entries; the
- * counts are returned in *m_lambda and *m_theta. */
+ * both in row-major order (with penalize_diag = 0 every diagonal entry is active).
+ * G_Lambda, Lambda: q x q; G_Theta, Theta: p x q; row-major double, host or device.  The
+ * caller's index buffers must hold q(q+1)/2 (li, lj) and p q (ti, tj) entries; the counts
+ * are returned in *m_lambda and *m_theta.  Errors: CGGM_EINVAL for sizes <= 0 or a null
+ * pointer. */
 cggm_status cggm_active_sets(cggm_ctx *ctx, int64_t p, int64_t q, const double *G_Lambda,
                              const double *G_Theta, const double *Lambda,
                              const double *Theta, double lam_L, double lam_T,
@@ -361,7 +377,10 @@ cggm_status cggm_partition_theta_columns(int64_t p, int64_t q, int64_t m, const 
  *    CGGM_EINVAL without touching the GPU.
  *  - Every pointer must be device memory of the current device (CGGM_EINVAL otherwise):
  *    Sigma, Psi, Syy, Lambda (q x q double), ai, aj (m int32, ai <= aj, visiting order),
- *    D_out (q x q double, overwritten).  The call runs on cuda_stream (a cudaStream_t;
+ *    D_out (q x q double, overwritten).  The indices are not checked (that would take
+ *    the device-to-host copy and synchronisation this entry point avoids): the caller
+ *    guarantees 0 <= ai <= aj < q, as cggm_active_sets produces them; cggm_lambda_sweep
+ *    checks them.  The call runs on cuda_stream (a cudaStream_t;
  *    NULL = the legacy default stream) and returns after the pass has finished.
  *  - The first call on a device looks up the device address of the array (once per
  *    device, with that device current); make that first call before any stream capture.

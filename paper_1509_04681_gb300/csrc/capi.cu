@@ -952,6 +952,28 @@ cggm_status cggm_cholesky(cggm_ctx *c, int64_t q, const double *Lambda, double *
     return sync_err(c);
 }
 
+// Caller-given coordinate lists (host or device memory) are checked on the host before
+// any kernel reads them: 0 <= a[k] < rows, 0 <= b[k] < cols, and a[k] <= b[k] when
+// `upper`.  The coordinate passes index their matrices with these values unchecked.
+static cggm_status check_pairs(cggm_ctx *c, const int32_t *a, const int32_t *b, int64_t m,
+                               int64_t rows, int64_t cols, bool upper) {
+    if (m <= 0) return CGGM_OK;
+    std::vector<int32_t> ha, hb;
+    if (is_device_ptr(a) || is_device_ptr(b)) {
+        ha.resize((size_t)m);
+        hb.resize((size_t)m);
+        CGGM_CUDA_TRY(cudaMemcpyAsync(ha.data(), a, 4 * (size_t)m, cudaMemcpyDefault, c->st));
+        CGGM_CUDA_TRY(cudaMemcpyAsync(hb.data(), b, 4 * (size_t)m, cudaMemcpyDefault, c->st));
+        CGGM_CUDA_TRY(cudaStreamSynchronize(c->st));
+        a = ha.data();
+        b = hb.data();
+    }
+    for (int64_t k = 0; k < m; k++)
+        if (a[k] < 0 || a[k] >= rows || b[k] < 0 || b[k] >= cols || (upper && a[k] > b[k]))
+            return CGGM_EINVAL;
+    return CGGM_OK;
+}
+
 static cggm_status load_index(cggm_ctx *c, const int32_t *src, int64_t m, Buf &dst) {
     CGGM_TRY(ensure(dst, 4 * (size_t)(m > 0 ? m : 1)));
     if (m > 0) CGGM_CUDA_TRY(cudaMemcpyAsync(dst.p, src, 4 * (size_t)m, cudaMemcpyDefault, c->st));
@@ -964,7 +986,9 @@ cggm_status cggm_lambda_sweep(cggm_ctx *c, int64_t q, const double *Sigma, const
                               int penalize_diag, int precision, double *D_out) {
     if (!c || q <= 0 || m < 0 || !Sigma || !Psi || !Syy || !Lambda || !D_out) return CGGM_EINVAL;
     if (m > 0 && (!ai || !aj)) return CGGM_EINVAL;
+    if (precision != CGGM_FP64 && precision != CGGM_MIXED) return CGGM_EINVAL;
     CGGM_TRY(set_device(c));
+    CGGM_TRY(check_pairs(c, ai, aj, m, q, q, true));
     const size_t qq = (size_t)q * q;
     CGGM_TRY(load_double(c, Sigma, qq, c->Sig));
     CGGM_TRY(load_double(c, Psi, qq, c->work));
@@ -1011,8 +1035,10 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
                              int precision, double *Theta_out) {
     if (!c || !X || !Sxy || !Sigma || !Theta_in || !Theta_out || m < 0) return CGGM_EINVAL;
     if (m > 0 && (!ti || !tj)) return CGGM_EINVAL;
+    if (precision != CGGM_FP64 && precision != CGGM_MIXED) return CGGM_EINVAL;
     CGGM_TRY(check_sizes(n, p, q));
     CGGM_TRY(set_device(c));
+    CGGM_TRY(check_pairs(c, ti, tj, m, p, q, false));
     const size_t qq = (size_t)q * q, pq = (size_t)p * q;
     CGGM_TRY(load_transposed(c, X, CGGM_F64, n, p, c->Xt, nullptr));
     CGGM_TRY(ensure(c->Sxx, 8 * (size_t)p * p));
