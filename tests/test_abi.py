@@ -59,3 +59,28 @@ def test_sm103a_only_sources():
         s = open(src).read()
         assert "triton" not in s.lower()
         assert "__CUDA_ARCH__ <" not in s
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the compiled library every entry point raises: there is no fallback."""
+    import paper_1509_04681_gb300.cggm as m
+    monkeypatch.setattr(m, "_LIB", None)
+    monkeypatch.setattr(m, "LIB_PATH", str(tmp_path / "libcggm.so"))
+    with pytest.raises(ImportError):
+        m.opts_default()
+    with pytest.raises(ImportError):
+        m.Context(0)
+    with pytest.raises(ImportError):
+        m.partition_columns(3, [0], [1], 2)
+
+
+def test_no_cpu_fallback_in_the_package():
+    """The package never imports the oracle or computes on the host in place of the
+    library: its modules name neither the oracle nor numpy linear algebra."""
+    import paper_1509_04681_gb300 as pkg
+    pkg_dir = os.path.dirname(pkg.__file__)
+    for f in os.listdir(pkg_dir):
+        if f.endswith(".py"):
+            src = open(os.path.join(pkg_dir, f)).read()
+            assert "oracle" not in src, f
+            assert "np.linalg" not in src and "scipy" not in src, f
