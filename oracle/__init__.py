@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE: a plain, slow, double-precision CPU restatement of what the CUDA
 solver computes, written from the paper (Eq. 1, Eq. 3, Eq. 4, Algorithm 1, Sections 3.1
 and 3.2, Appendix A.1, the stopping rule of Section 5.1; ``oracle.blocks``: the block
-coordinate descent of Algorithm 2 and Section 4).  Only the tests, the smoke
+coordinate descent of Algorithm 2 and Section 4; ``oracle.symbolic``: the symbolic
+Cholesky of a sparse Lambda by the elimination game).  Only the tests, the smoke
 check and the CPU-baseline leg of the benchmark may import it.  It shares no code
 with the CUDA path; both take inputs from the ``synth`` generators only.
 
@@ -13,7 +14,8 @@ proximal solver of the diagonal-penalised graphical lasso, KKT conditions, finit
 differences of the objective, one-dimensional brute force for every coordinate step,
 monotone decrease, and a brute-force proximal-gradient solve on tiny inputs; for the
 blocked passes, equality with the pinned sequential passes in the blocked order, the
-cache counts of Section 4, the lambda = 0 closed form and Algorithm 1's optimum.
+cache counts of Section 4, the lambda = 0 closed form and Algorithm 1's optimum; for the
+symbolic Cholesky, the nonzero pattern of LAPACK's numeric factor and closed forms.
 """
 from .cggm_oracle import (  # noqa: F401
     OracleError,
@@ -33,3 +35,4 @@ from .cggm_oracle import (  # noqa: F401
     spd_solve,
 )
 from . import blocks  # noqa: F401,E402
+from . import symbolic  # noqa: F401,E402

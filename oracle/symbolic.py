@@ -1,0 +1,71 @@
+"""Symbolic Cholesky of a sparse symmetric pattern: oracle form.
+
+TEST INFRASTRUCTURE (see the package docstring).  Plain numpy on dense boolean matrices,
+for small cases only.
+
+Algorithm 2 keeps Lambda sparse, and its line search needs log det of Lambda + alpha D
+(Section 4; Section 2.3 computes log det from a Cholesky factor).  For a sparse Lambda that
+factor is a sparse Cholesky, whose structure depends only on the pattern and the pivot
+order.  The definition used here is the elimination game: with the pattern permuted to
+the pivot order, eliminating pivot k joins every pair of rows r, s > k that have an entry
+in column k; the pattern of L is the lower triangle at the end.  From it:
+
+  * the elimination tree: parent(k) = min { r > k : L_rk != 0 }, or -1;
+  * column counts: the entries of column k of L, the diagonal included;
+  * fill: entries of L that were not in the lower triangle of the permuted pattern.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def pattern_from_csr(q, row_ptr, col) -> np.ndarray:
+    """Dense boolean symmetric pattern with a full diagonal from CSR entries (either or
+    both triangles given)."""
+    A = np.zeros((q, q), dtype=bool)
+    row_ptr = np.asarray(row_ptr)
+    col = np.asarray(col)
+    for i in range(q):
+        for t in range(row_ptr[i], row_ptr[i + 1]):
+            A[i, col[t]] = True
+            A[col[t], i] = True
+    np.fill_diagonal(A, True)
+    return A
+
+
+def cholesky_pattern(A: np.ndarray, perm) -> np.ndarray:
+    """Pattern of L for the pivot order perm (perm[k] = original index of pivot k), by
+    the elimination game."""
+    perm = np.asarray(perm)
+    B = A[np.ix_(perm, perm)].copy()
+    q = B.shape[0]
+    for k in range(q):
+        rows = np.flatnonzero(B[k + 1:, k]) + k + 1
+        if rows.size:
+            B[np.ix_(rows, rows)] = True
+    return np.tril(B)
+
+
+def etree(L: np.ndarray) -> np.ndarray:
+    """parent(k) = the first row below the diagonal with an entry in column k, or -1."""
+    q = L.shape[0]
+    parent = np.full(q, -1, dtype=np.int64)
+    for k in range(q):
+        below = np.flatnonzero(L[k + 1:, k])
+        if below.size:
+            parent[k] = k + 1 + below[0]
+    return parent
+
+
+def column_counts(L: np.ndarray) -> np.ndarray:
+    return L.sum(axis=0).astype(np.int64)
+
+
+def analyse(q, row_ptr, col, perm):
+    """(parent, colcount, nnz_L, fill) for the pivot order perm."""
+    A = pattern_from_csr(q, row_ptr, col)
+    L = cholesky_pattern(A, perm)
+    cc = column_counts(L)
+    perm = np.asarray(perm)
+    fill = int(L.sum()) - int(np.tril(A[np.ix_(perm, perm)]).sum())
+    return etree(L), cc, int(cc.sum()), fill

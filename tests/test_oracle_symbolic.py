@@ -1,0 +1,75 @@
+"""Pins of the oracle's symbolic Cholesky (CPU): the elimination game's pattern equals the
+nonzero pattern of a numeric Cholesky factor (LAPACK through numpy) of a matrix with that
+sparsity and generic values, and closed forms on a path, an arrow and a dense pattern."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import symbolic
+
+
+def csr_of(A):
+    m = sp.csr_matrix(A)
+    return m.indptr, m.indices
+
+
+def random_pattern(q, m, seed):
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, q, m)
+    j = rng.integers(0, q, m)
+    A = np.zeros((q, q), dtype=bool)
+    A[i, j] = True
+    A[j, i] = True
+    np.fill_diagonal(A, True)
+    return A
+
+
+@pytest.mark.parametrize("q,m,seed", [(30, 40, 1), (60, 90, 2), (45, 300, 3), (1, 0, 4)])
+def test_pattern_equals_numeric_cholesky(q, m, seed):
+    """Generic values on the pattern, made diagonally dominant: every structurally nonzero
+    entry of L is nonzero, and every structural zero is computed as an exact zero."""
+    rng = np.random.default_rng(seed + 100)
+    A = random_pattern(q, m, seed)
+    V = np.where(A, rng.uniform(0.1, 1.0, (q, q)), 0.0)
+    V = np.triu(V, 1)
+    V = V + V.T
+    V += np.diag(np.abs(V).sum(axis=1) + 1.0)
+    for perm in (np.arange(q), rng.permutation(q)):
+        Lnum = np.linalg.cholesky(V[np.ix_(perm, perm)])
+        rp, ci = csr_of(A)
+        L = symbolic.cholesky_pattern(symbolic.pattern_from_csr(q, rp, ci), perm)
+        assert np.array_equal(L, Lnum != 0.0)
+
+
+def test_path_has_no_fill():
+    q = 10
+    A = np.eye(q, dtype=bool) | np.eye(q, k=1, dtype=bool) | np.eye(q, k=-1, dtype=bool)
+    rp, ci = csr_of(A)
+    parent, cc, nnz, fill = symbolic.analyse(q, rp, ci, np.arange(q))
+    assert parent.tolist() == list(range(1, q)) + [-1]
+    assert cc.tolist() == [2] * (q - 1) + [1]
+    assert nnz == 2 * q - 1 and fill == 0
+
+
+def test_arrow_order_decides_fill():
+    """A hub joined to every other column: eliminated first it fills the whole factor,
+    eliminated last it fills nothing."""
+    q = 8
+    A = np.eye(q, dtype=bool)
+    A[0, :] = A[:, 0] = True
+    rp, ci = csr_of(A)
+    _, cc, nnz, fill = symbolic.analyse(q, rp, ci, np.arange(q))
+    assert nnz == q * (q + 1) // 2 and fill == (q - 1) * (q - 2) // 2
+    hub_last = np.r_[np.arange(1, q), 0]
+    parent, cc, nnz, fill = symbolic.analyse(q, rp, ci, hub_last)
+    assert nnz == 2 * q - 1 and fill == 0
+    assert parent.tolist() == [q - 1] * (q - 1) + [-1]
+
+
+def test_dense_pattern():
+    q = 6
+    A = np.ones((q, q), dtype=bool)
+    rp, ci = csr_of(A)
+    parent, cc, nnz, fill = symbolic.analyse(q, rp, ci, np.arange(q))
+    assert cc.tolist() == list(range(q, 0, -1)) and fill == 0
+    assert parent.tolist() == list(range(1, q)) + [-1]
