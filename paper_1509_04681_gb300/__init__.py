@@ -24,6 +24,11 @@ from .cggm import (  # noqa: F401
     tuned_batch,
     partition_columns,
     partition_theta_columns,
+    chol_symbolic,
+    CGGM_ORDER_NATURAL,
+    CGGM_ORDER_RCM,
+    CGGM_ORDER_GIVEN,
+    CGGM_ORDER_MINDEG,
     CGGM_MIXED,
     CGGM_OK,
     CGGM_EMAXITER,

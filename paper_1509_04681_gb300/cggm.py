@@ -24,6 +24,7 @@ CGGM_ELINESEARCH, CGGM_ECUDA, CGGM_ETIMEDOUT, CGGM_ENONFINITE, CGGM_ECANCELLED =
 CGGM_FP64, CGGM_MIXED = 0, 1
 CGGM_F32, CGGM_F64, CGGM_BF16, CGGM_I8_GENO = 0, 1, 2, 3
 CGGM_SWEEP_BATCH_AUTO = -1
+CGGM_ORDER_NATURAL, CGGM_ORDER_RCM, CGGM_ORDER_GIVEN, CGGM_ORDER_MINDEG = 0, 1, 2, 3
 
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
@@ -31,7 +32,7 @@ EXPORTED = [
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
-    "cggm_partition_theta_columns",
+    "cggm_partition_theta_columns", "cggm_chol_symbolic",
 ]
 
 
@@ -132,6 +133,7 @@ def _lib():
                                                ctypes.POINTER(i64), ctypes.POINTER(dbl)]
         lib.cggm_partition_theta_columns.argtypes = [i64, i64, i64, vp, vp, i64, vp,
                                                      ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.cggm_chol_symbolic.argtypes = [i64, vp, vp, ip, vp, vp, vp, vp, ctypes.POINTER(i64)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -143,6 +145,7 @@ def _lib():
                                                      "cggm_spd_solve", "cggm_grad_lambda_block",
                                                      "cggm_partition_columns",
                                                      "cggm_partition_theta_columns",
+                                                     "cggm_chol_symbolic",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -440,6 +443,34 @@ def partition_theta_columns(p: int, q: int, ti, tj, max_block: int):
                                                ctypes.byref(k), ctypes.byref(rb)),
            "cggm_partition_theta_columns")
     return block, int(k.value), int(rb.value)
+
+
+def chol_symbolic(q: int, row_ptr, col, ordering: int = CGGM_ORDER_MINDEG, perm=None):
+    """Symbolic analysis of the sparse Cholesky factor of a q x q pattern in CSR
+    (cggm_chol_symbolic).  Host memory only.  Returns (perm, parent, colcount, nnz_L):
+    the pivot order (new -> old), the elimination tree of the permuted pattern, the
+    entries of each column of L (diagonal included) and their sum."""
+    q = int(q)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci, pci = _host_i32(col)
+    if rp.shape != (q + 1,) and q > 0:
+        raise ValueError("row_ptr must hold q + 1 entries")
+    ppi = None
+    if perm is not None:
+        perm, ppi = _host_i32(perm)
+        if perm.shape != (q,):
+            raise ValueError("perm must hold q entries")
+    n = max(q, 0)
+    perm_out = np.empty(n, dtype=np.int32)
+    parent = np.empty(n, dtype=np.int32)
+    count = np.empty(n, dtype=np.int64)
+    nnz = ctypes.c_int64()
+    _check(_lib().cggm_chol_symbolic(q, rp.ctypes.data_as(ctypes.c_void_p), pci, int(ordering),
+                                     ppi, perm_out.ctypes.data_as(ctypes.c_void_p),
+                                     parent.ctypes.data_as(ctypes.c_void_p),
+                                     count.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nnz)),
+           "cggm_chol_symbolic")
+    return perm_out, parent, count, int(nnz.value)
 
 
 def make_opts(**kw) -> cggm_opts:

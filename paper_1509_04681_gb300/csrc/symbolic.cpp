@@ -1,0 +1,256 @@
+// Symbolic analysis of the sparse Cholesky factor of Lambda (host code).
+//
+// Algorithm 2 keeps Lambda sparse; its Armijo step needs log det(Lambda + alpha D) (Section
+// 4), which for a sparse Lambda comes from a sparse Cholesky factor.  The structure of
+// that factor depends only on the pattern and the pivot order, and is found once per
+// pattern before any numeric work:
+//
+//  1. the pivot order: natural; reverse Cuthill-McKee (breadth-first from a
+//     pseudo-peripheral vertex of each component, neighbours by ascending degree, the whole
+//     order reversed: a small profile for banded patterns); minimum degree (always
+//     eliminate a vertex of least current degree in the elimination graph, whose
+//     neighbours then become a clique: no fill at all on a forest, little on a chain with
+//     few extra links; once the remaining graph is at least 90 % dense the rest is taken
+//     as it stands, order no longer mattering there); or given;
+//  2. the elimination tree, by path compression over the ancestors found so far: for each
+//     pivot k and each earlier neighbour i, climb from i to the root of its current
+//     subtree and hang that root under k;
+//  3. column counts from row subtrees: row k of L holds exactly the nodes on the tree
+//     paths from each earlier neighbour of k up to k, so marking those paths row by row
+//     counts every entry of L once (O(nnz(L)) in all).
+//
+// Deterministic; no GPU is used.
+#include <algorithm>
+#include <cstdint>
+#include <iterator>
+#include <set>
+#include <vector>
+
+#include "../../include/cggm.h"
+
+namespace {
+
+// Symmetric adjacency of the pattern without the diagonal, neighbours ascending, no repeats.
+struct Adjacency {
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> adj;
+    int64_t degree(int64_t v) const { return ptr[v + 1] - ptr[v]; }
+};
+
+Adjacency symmetrise(int64_t q, const int64_t *row_ptr, const int32_t *col)
+{
+    std::vector<int64_t> deg(q + 1, 0);
+    for (int64_t i = 0; i < q; i++)
+        for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; t++)
+            if (col[t] != i) {
+                deg[i]++;
+                deg[col[t]]++;
+            }
+    std::vector<int64_t> start(q + 1, 0);
+    for (int64_t v = 0; v < q; v++) start[v + 1] = start[v] + deg[v];
+    std::vector<int32_t> raw(start[q]);
+    std::vector<int64_t> fill(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < q; i++)
+        for (int64_t t = row_ptr[i]; t < row_ptr[i + 1]; t++)
+            if (col[t] != i) {
+                raw[fill[i]++] = col[t];
+                raw[fill[col[t]]++] = (int32_t)i;
+            }
+    Adjacency a;
+    a.ptr.assign(q + 1, 0);
+    a.adj.reserve(raw.size());
+    for (int64_t v = 0; v < q; v++) {
+        auto b = raw.begin() + start[v], e = raw.begin() + start[v + 1];
+        std::sort(b, e);
+        e = std::unique(b, e);
+        a.adj.insert(a.adj.end(), b, e);
+        a.ptr[v + 1] = (int64_t)a.adj.size();
+    }
+    return a;
+}
+
+// Breadth-first visit of the component of `root` into `order`; levels in `level`.
+void bfs(const Adjacency &a, int32_t root, std::vector<int32_t> &order,
+         std::vector<int32_t> &level, bool by_degree)
+{
+    order.clear();
+    order.push_back(root);
+    level[root] = 0;
+    std::vector<int32_t> nb;
+    for (size_t h = 0; h < order.size(); h++) {
+        const int32_t v = order[h];
+        nb.clear();
+        for (int64_t t = a.ptr[v]; t < a.ptr[v + 1]; t++)
+            if (level[a.adj[t]] < 0) nb.push_back(a.adj[t]);
+        if (by_degree)
+            std::sort(nb.begin(), nb.end(), [&](int32_t x, int32_t y) {
+                return a.degree(x) != a.degree(y) ? a.degree(x) < a.degree(y) : x < y;
+            });
+        for (int32_t u : nb)
+            if (level[u] < 0) {
+                level[u] = level[v] + 1;
+                order.push_back(u);
+            }
+    }
+}
+
+// Reverse Cuthill-McKee order (new -> old): each component from a pseudo-peripheral
+// vertex (the least-degree vertex of the last level, while that deepens the search).
+std::vector<int32_t> rcm_order(const Adjacency &a, int64_t q)
+{
+    std::vector<int32_t> level(q, -1), order, comp, perm;
+    perm.reserve(q);
+    for (int32_t s = 0; s < q; s++) {
+        if (level[s] >= 0) continue;
+        bfs(a, s, comp, level, false);
+        int32_t root = s;
+        for (int32_t v : comp)
+            if (a.degree(v) < a.degree(root) || (a.degree(v) == a.degree(root) && v < root))
+                root = v;
+        int32_t depth = -1;
+        for (int sweep = 0; sweep < 4; sweep++) {
+            for (int32_t v : comp) level[v] = -1;
+            bfs(a, root, comp, level, false);
+            const int32_t d = level[comp.back()];
+            if (d <= depth) break;
+            depth = d;
+            int32_t next = comp.back();
+            for (int32_t v : comp)
+                if (level[v] == d && (a.degree(v) < a.degree(next) ||
+                                      (a.degree(v) == a.degree(next) && v < next)))
+                    next = v;
+            root = next;
+        }
+        for (int32_t v : comp) level[v] = -1;
+        bfs(a, root, order, level, true);
+        perm.insert(perm.end(), order.begin(), order.end());
+    }
+    std::reverse(perm.begin(), perm.end());
+    return perm;
+}
+
+// Minimum-degree order (new -> old) on the explicit elimination graph.  Ties go to the
+// lower index.  Eliminating v joins its current neighbours into a clique.
+std::vector<int32_t> min_degree_order(const Adjacency &a, int64_t q)
+{
+    constexpr double kDenseRest = 0.9;
+    std::vector<std::vector<int32_t>> adj(q);
+    for (int64_t v = 0; v < q; v++) adj[v].assign(a.adj.begin() + a.ptr[v], a.adj.begin() + a.ptr[v + 1]);
+    std::set<std::pair<int64_t, int32_t>> by_degree;
+    for (int32_t v = 0; v < q; v++) by_degree.insert({(int64_t)adj[v].size(), v});
+    std::vector<int32_t> perm, merged;
+    perm.reserve(q);
+    while (!by_degree.empty()) {
+        const auto first = *by_degree.begin();
+        const int64_t remaining = q - (int64_t)perm.size();
+        if (remaining > 64 && (double)(first.first + 1) >= kDenseRest * (double)remaining) {
+            for (const auto &e : by_degree) perm.push_back(e.second);
+            break;
+        }
+        by_degree.erase(by_degree.begin());
+        const int32_t v = first.second;
+        perm.push_back(v);
+        const std::vector<int32_t> nb = std::move(adj[v]);
+        adj[v].clear();
+        for (int32_t u : nb) {
+            by_degree.erase({(int64_t)adj[u].size(), u});
+            merged.clear();
+            std::set_union(adj[u].begin(), adj[u].end(), nb.begin(), nb.end(),
+                           std::back_inserter(merged));
+            merged.erase(std::remove_if(merged.begin(), merged.end(),
+                                        [&](int32_t x) { return x == u || x == v; }),
+                         merged.end());
+            adj[u].swap(merged);
+            by_degree.insert({(int64_t)adj[u].size(), u});
+        }
+    }
+    return perm;
+}
+
+}  // namespace
+
+extern "C" cggm_status cggm_chol_symbolic(int64_t q, const int64_t *row_ptr, const int32_t *col,
+                                          int ordering, const int32_t *perm_in,
+                                          int32_t *perm_out, int32_t *parent_out,
+                                          int64_t *colcount_out, int64_t *nnz_L_out)
+{
+    if (q < 0 || q > INT32_MAX) return CGGM_EINVAL;
+    if (q > 0 && (!row_ptr || !col || !perm_out || !parent_out || !colcount_out))
+        return CGGM_EINVAL;
+    if (ordering != CGGM_ORDER_NATURAL && ordering != CGGM_ORDER_RCM &&
+        ordering != CGGM_ORDER_GIVEN && ordering != CGGM_ORDER_MINDEG)
+        return CGGM_EINVAL;
+    if (q == 0) {
+        if (nnz_L_out) *nnz_L_out = 0;
+        return CGGM_OK;
+    }
+    if (row_ptr[0] != 0) return CGGM_EINVAL;
+    for (int64_t i = 0; i < q; i++)
+        if (row_ptr[i + 1] < row_ptr[i]) return CGGM_EINVAL;
+    for (int64_t t = 0; t < row_ptr[q]; t++)
+        if (col[t] < 0 || col[t] >= q) return CGGM_EINVAL;
+    const Adjacency a = symmetrise(q, row_ptr, col);
+
+    // 1. pivot order (new -> old) and its inverse
+    std::vector<int32_t> perm(q), iperm(q, -1);
+    if (ordering == CGGM_ORDER_NATURAL) {
+        for (int32_t k = 0; k < q; k++) perm[k] = k;
+    } else if (ordering == CGGM_ORDER_RCM) {
+        perm = rcm_order(a, q);
+    } else if (ordering == CGGM_ORDER_MINDEG) {
+        perm = min_degree_order(a, q);
+    } else {
+        if (!perm_in) return CGGM_EINVAL;
+        for (int64_t k = 0; k < q; k++) perm[k] = perm_in[k];
+    }
+    for (int32_t k = 0; k < q; k++) {
+        const int32_t v = perm[k];
+        if (v < 0 || v >= q || iperm[v] >= 0) return CGGM_EINVAL;  // not a permutation
+        iperm[v] = k;
+    }
+
+    // 2. elimination tree of the permuted pattern
+    std::vector<int32_t> parent(q, -1), ancestor(q, -1);
+    for (int32_t k = 0; k < q; k++) {
+        const int32_t v = perm[k];
+        for (int64_t t = a.ptr[v]; t < a.ptr[v + 1]; t++) {
+            int32_t r = iperm[a.adj[t]];
+            if (r >= k) continue;
+            while (ancestor[r] != -1 && ancestor[r] != k) {
+                const int32_t up = ancestor[r];
+                ancestor[r] = k;
+                r = up;
+            }
+            if (ancestor[r] == -1) {
+                ancestor[r] = k;
+                parent[r] = k;
+            }
+        }
+    }
+
+    // 3. column counts from the row subtrees
+    std::vector<int64_t> count(q, 1);  // the diagonal
+    std::vector<int32_t> mark(q, -1);
+    for (int32_t k = 0; k < q; k++) {
+        mark[k] = k;
+        const int32_t v = perm[k];
+        for (int64_t t = a.ptr[v]; t < a.ptr[v + 1]; t++) {
+            int32_t r = iperm[a.adj[t]];
+            if (r >= k) continue;
+            while (mark[r] != k) {  // k is an ancestor of r: the walk ends at k
+                count[r]++;         // L(k, r) is an entry
+                mark[r] = k;
+                r = parent[r];
+            }
+        }
+    }
+    int64_t nnz = 0;
+    for (int32_t k = 0; k < q; k++) {
+        perm_out[k] = perm[k];
+        parent_out[k] = parent[k];
+        colcount_out[k] = count[k];
+        nnz += count[k];
+    }
+    if (nnz_L_out) *nnz_L_out = nnz;
+    return CGGM_OK;
+}

@@ -1,0 +1,164 @@
+"""Symbolic sparse Cholesky (cggm_chol_symbolic, host code of the library; no GPU) against
+the oracle's elimination game.  Integer work, so bit-exact: for caller-given pivot orders
+the elimination tree, the column counts and nnz(L) equal the oracle's.  The orders the
+library computes are checked by what they must achieve: valid permutations; no fill on a
+relabelled path (reverse Cuthill-McKee, minimum degree) or forest (minimum degree); fill
+inside the band of a relabelled banded pattern (reverse Cuthill-McKee); far less fill than
+the other orders on a chain with random links (minimum degree)."""
+import time
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import paper_1509_04681_gb300 as cg
+from oracle import symbolic
+
+
+def random_csr(q, m, seed, upper_only=False):
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, q, m)
+    j = rng.integers(0, q, m)
+    if upper_only:
+        i, j = np.minimum(i, j), np.maximum(i, j)
+    A = sp.csr_matrix((np.ones(m), (i, j)), shape=(q, q))
+    A.sum_duplicates()
+    return A.indptr, A.indices
+
+
+@pytest.mark.parametrize("q,m,seed", [(1, 0, 1), (12, 10, 2), (40, 60, 3), (80, 160, 4),
+                                      (120, 130, 5), (60, 900, 6)])
+def test_given_orders_match_the_oracle(q, m, seed):
+    rp, ci = random_csr(q, m, seed)
+    rng = np.random.default_rng(seed)
+    for perm in (np.arange(q), rng.permutation(q), rng.permutation(q)[::-1].copy()):
+        p_out, parent, cc, nnz = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_GIVEN, perm)
+        r_parent, r_cc, r_nnz, _ = symbolic.analyse(q, rp, ci, perm)
+        assert np.array_equal(p_out, perm)
+        assert np.array_equal(parent, r_parent)
+        assert np.array_equal(cc, r_cc)
+        assert nnz == r_nnz
+    # the natural order is the identity permutation
+    _, parent, cc, nnz = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_NATURAL)
+    r_parent, r_cc, r_nnz, _ = symbolic.analyse(q, rp, ci, np.arange(q))
+    assert np.array_equal(parent, r_parent) and np.array_equal(cc, r_cc) and nnz == r_nnz
+
+
+def test_one_triangle_is_enough():
+    q = 50
+    rp_u, ci_u = random_csr(q, 120, 7, upper_only=True)
+    U = sp.csr_matrix((np.ones(len(ci_u)), ci_u, rp_u), shape=(q, q))
+    F = (U + U.T).tocsr()
+    a = cg.chol_symbolic(q, rp_u, ci_u, cg.CGGM_ORDER_NATURAL)
+    b = cg.chol_symbolic(q, F.indptr, F.indices, cg.CGGM_ORDER_NATURAL)
+    assert all(np.array_equal(x, y) for x, y in zip(a[:3], b[:3])) and a[3] == b[3]
+
+
+def relabelled(A, seed):
+    q = A.shape[0]
+    lab = np.random.default_rng(seed).permutation(q)
+    P = sp.csr_matrix((np.ones(q), (lab, np.arange(q))), shape=(q, q))
+    B = (P @ A @ P.T).tocsr()
+    B.sort_indices()
+    return B
+
+
+def test_rcm_and_min_degree_on_a_relabelled_path():
+    """A path has no fill once numbered along itself (reverse Cuthill-McKee does that);
+    minimum degree eliminates an end each time and fills nothing either; any order fills
+    at most one entry per elimination (eliminating a vertex of a path leaves a path)."""
+    q = 500
+    A = sp.diags([np.ones(q - 1), np.ones(q), np.ones(q - 1)], [-1, 0, 1], format="csr")
+    B = relabelled(A, 1)
+    for order in (cg.CGGM_ORDER_RCM, cg.CGGM_ORDER_MINDEG):
+        perm, parent, cc, nnz = cg.chol_symbolic(q, B.indptr, B.indices, order)
+        assert np.array_equal(np.sort(perm), np.arange(q))
+        assert nnz == 2 * q - 1
+    _, _, _, nnz_nat = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_NATURAL)
+    assert 2 * q - 1 <= nnz_nat <= 3 * q
+
+
+def test_min_degree_has_no_fill_on_a_forest():
+    """A forest always has a vertex of degree at most one, whose elimination creates no
+    fill: nnz(L) = q + edges exactly."""
+    rng = np.random.default_rng(10)
+    q = 3000
+    parent = np.array([rng.integers(0, v) if v > 0 and v % 50 else -1 for v in range(q)])
+    child = np.flatnonzero(parent >= 0)
+    A = sp.csr_matrix((np.ones(child.size), (child, parent[child])), shape=(q, q))
+    B = relabelled((A + A.T).tocsr(), 4)
+    perm, par, cc, nnz = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_MINDEG)
+    assert np.array_equal(np.sort(perm), np.arange(q))
+    assert nnz == q + child.size
+
+
+def test_rcm_keeps_a_relabelled_band():
+    """Bandwidth b: a band-preserving order fills only inside the band, at most
+    (b + 1) entries per column."""
+    q, b = 300, 4
+    A = sp.diags([np.ones(q - abs(k)) for k in range(-b, b + 1)], list(range(-b, b + 1)),
+                 format="csr")
+    B = relabelled(A, 2)
+    perm, parent, cc, nnz = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_RCM)
+    assert np.array_equal(np.sort(perm), np.arange(q))
+    assert cc.max() <= b + 1 and nnz <= q * (b + 1)
+
+
+def test_tree_and_counts_are_consistent():
+    """parent > k for every non-root; a column's count is at most its parent's + 1."""
+    q = 400
+    rp, ci = random_csr(q, 800, 8)
+    perm, parent, cc, nnz = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_RCM)
+    k = np.arange(q)
+    nonroot = parent >= 0
+    assert np.all(parent[nonroot] > k[nonroot])
+    assert np.all(cc[nonroot] <= cc[parent[nonroot]] + 1)
+    assert nnz == cc.sum() and np.all(cc >= 1)
+
+
+def test_chain_with_links_at_the_largest_output_count():
+    """q = 20000 outputs, a chain with random links (the block regime's network shape) on
+    relabelled columns: minimum degree keeps the factor far sparser than the natural and
+    the reverse Cuthill-McKee orders (which the long links defeat), within a second."""
+    q = 20000
+    rng = np.random.default_rng(9)
+    for links in (200, 2000):
+        i = np.r_[np.arange(q - 1), rng.integers(0, q, links)]
+        j = np.r_[np.arange(1, q), rng.integers(0, q, links)]
+        A = sp.csr_matrix((np.ones(i.size), (i, j)), shape=(q, q))
+        B = relabelled((A + A.T).tocsr(), 3)
+        t0 = time.perf_counter()
+        _, _, _, nnz_md = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_MINDEG)
+        assert time.perf_counter() - t0 < 5.0
+        _, _, _, nnz_nat = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_NATURAL)
+        _, _, _, nnz_rcm = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_RCM)
+        assert 2 * q - 1 <= nnz_md < 0.5 * min(nnz_nat, nnz_rcm)
+
+
+def test_min_degree_on_a_random_network():
+    """A random network of average degree 4 (q = 2000): a valid order, counts consistent
+    with the elimination tree, and less fill than the natural order."""
+    q = 2000
+    rp, ci = random_csr(q, 4000, 11)
+    perm, parent, cc, nnz = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_MINDEG)
+    assert np.array_equal(np.sort(perm), np.arange(q))
+    nonroot = parent >= 0
+    assert np.all(parent[nonroot] > np.arange(q)[nonroot])
+    assert nnz == cc.sum()
+    assert nnz < cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_NATURAL)[3]
+
+
+def test_empty_and_errors():
+    perm, parent, cc, nnz = cg.chol_symbolic(0, [0], [], cg.CGGM_ORDER_RCM)
+    assert perm.size == 0 and nnz == 0
+    rp, ci = np.array([0, 1, 2]), np.array([1, 0])
+    with pytest.raises(cg.CGGMError):
+        cg.chol_symbolic(2, rp, ci, 7)                                   # no such ordering
+    with pytest.raises(cg.CGGMError):
+        cg.chol_symbolic(2, rp, ci, cg.CGGM_ORDER_GIVEN, [0, 0])         # not a permutation
+    with pytest.raises(cg.CGGMError):
+        cg.chol_symbolic(2, rp, ci, cg.CGGM_ORDER_GIVEN)                 # no permutation given
+    with pytest.raises(cg.CGGMError):
+        cg.chol_symbolic(2, np.array([0, 1, 2]), np.array([1, 2]), cg.CGGM_ORDER_NATURAL)
+    with pytest.raises(cg.CGGMError):
+        cg.chol_symbolic(2, np.array([0, 2, 1]), np.array([1, 0]), cg.CGGM_ORDER_NATURAL)
