@@ -396,6 +396,20 @@ cggm_status cggm_chol_symbolic(int64_t q, const int64_t *row_ptr, const int32_t 
                                int32_t *parent_out, int64_t *colcount_out,
                                int64_t *nnz_L_out);
 
+/* Fundamental supernodes of the factor analysed by cggm_chol_symbolic: maximal runs of
+ * consecutive pivots whose columns share one row pattern below the run (a dense block of
+ * L), the unit of work of a supernodal numeric factorisation.  Pivot k + 1 continues the
+ * run of pivot k when k is its only child in the elimination tree and column k holds
+ * exactly one entry more than column k + 1 (then column k below its diagonal is column
+ * k + 1's pattern).
+ *   parent, colcount (q): as returned by cggm_chol_symbolic.
+ *   start_out (q + 1 entries, caller-owned host memory): start_out[s] is the first pivot of
+ *   supernode s, s < *nsuper_out, and start_out[*nsuper_out] = q.
+ * Errors: CGGM_EINVAL for q < 0, a null pointer, a parent outside (k, q) or -1, or a
+ * count outside [1, q - k]. */
+cggm_status cggm_chol_supernodes(int64_t q, const int32_t *parent, const int64_t *colcount,
+                                 int64_t *start_out, int64_t *nsuper_out);
+
 /*
  * No-allocation variant of cggm_lambda_sweep (the paper has no counterpart: this is an
  * interface for embedding).  Some callers cannot call cudaMalloc: code that runs under

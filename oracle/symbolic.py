@@ -69,3 +69,19 @@ def analyse(q, row_ptr, col, perm):
     perm = np.asarray(perm)
     fill = int(L.sum()) - int(np.tril(A[np.ix_(perm, perm)]).sum())
     return etree(L), cc, int(cc.sum()), fill
+
+
+def fundamental_supernodes(L: np.ndarray) -> np.ndarray:
+    """Start columns of the fundamental supernodes of the factor pattern L (with q as a
+    final sentinel): column k + 1 continues the supernode of column k when the pattern of
+    column k below its diagonal is exactly the pattern of column k + 1 (diagonal included),
+    and k is the only child of k + 1 in the elimination tree."""
+    q = L.shape[0]
+    parent = etree(L)
+    children = np.bincount(parent[parent >= 0], minlength=q) if q else np.zeros(0, int)
+    starts = [0] if q else []
+    for k in range(q - 1):
+        same = np.array_equal(L[k + 1:, k], L[k + 1:, k + 1])
+        if not (same and children[k + 1] == 1):
+            starts.append(k + 1)
+    return np.array(starts + [q], dtype=np.int64)

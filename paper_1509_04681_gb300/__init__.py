@@ -25,6 +25,7 @@ from .cggm import (  # noqa: F401
     partition_columns,
     partition_theta_columns,
     chol_symbolic,
+    chol_supernodes,
     CGGM_ORDER_NATURAL,
     CGGM_ORDER_RCM,
     CGGM_ORDER_GIVEN,

@@ -32,7 +32,7 @@ EXPORTED = [
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
-    "cggm_partition_theta_columns", "cggm_chol_symbolic",
+    "cggm_partition_theta_columns", "cggm_chol_symbolic", "cggm_chol_supernodes",
 ]
 
 
@@ -134,6 +134,7 @@ def _lib():
         lib.cggm_partition_theta_columns.argtypes = [i64, i64, i64, vp, vp, i64, vp,
                                                      ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.cggm_chol_symbolic.argtypes = [i64, vp, vp, ip, vp, vp, vp, vp, ctypes.POINTER(i64)]
+        lib.cggm_chol_supernodes.argtypes = [i64, vp, vp, vp, ctypes.POINTER(i64)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -146,6 +147,7 @@ def _lib():
                                                      "cggm_partition_columns",
                                                      "cggm_partition_theta_columns",
                                                      "cggm_chol_symbolic",
+                                                     "cggm_chol_supernodes",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -471,6 +473,22 @@ def chol_symbolic(q: int, row_ptr, col, ordering: int = CGGM_ORDER_MINDEG, perm=
                                      count.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nnz)),
            "cggm_chol_symbolic")
     return perm_out, parent, count, int(nnz.value)
+
+
+def chol_supernodes(parent, colcount):
+    """Fundamental supernodes (cggm_chol_supernodes) from the elimination tree and column
+    counts of chol_symbolic: the start pivot of each supernode, then q."""
+    parent, pp = _host_i32(parent)
+    cc = np.ascontiguousarray(colcount, dtype=np.int64)
+    q = parent.size
+    if cc.shape != (q,):
+        raise ValueError("parent and colcount differ in length")
+    start = np.empty(q + 1, dtype=np.int64)
+    ns = ctypes.c_int64()
+    _check(_lib().cggm_chol_supernodes(q, pp, cc.ctypes.data_as(ctypes.c_void_p),
+                                       start.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ns)),
+           "cggm_chol_supernodes")
+    return start[:ns.value + 1].copy()
 
 
 def make_opts(**kw) -> cggm_opts:

@@ -254,3 +254,30 @@ extern "C" cggm_status cggm_chol_symbolic(int64_t q, const int64_t *row_ptr, con
     if (nnz_L_out) *nnz_L_out = nnz;
     return CGGM_OK;
 }
+
+extern "C" cggm_status cggm_chol_supernodes(int64_t q, const int32_t *parent,
+                                            const int64_t *colcount, int64_t *start_out,
+                                            int64_t *nsuper_out)
+{
+    if (q < 0 || q > INT32_MAX || !nsuper_out) return CGGM_EINVAL;
+    if (q > 0 && (!parent || !colcount || !start_out)) return CGGM_EINVAL;
+    std::vector<int32_t> children(q, 0);
+    for (int64_t k = 0; k < q; k++) {
+        if (colcount[k] < 1 || colcount[k] > q - k) return CGGM_EINVAL;
+        if (parent[k] == -1) continue;
+        if (parent[k] <= k || parent[k] >= q) return CGGM_EINVAL;
+        children[parent[k]]++;
+    }
+    int64_t ns = 0;
+    if (q > 0) start_out[ns++] = 0;
+    for (int64_t k = 0; k + 1 < q; k++) {
+        // column k + 1 continues k's supernode when k is its only child and column k below
+        // its diagonal holds exactly column k + 1's entries
+        const bool joins = parent[k] == k + 1 && children[k + 1] == 1 &&
+                           colcount[k] == colcount[k + 1] + 1;
+        if (!joins) start_out[ns++] = k + 1;
+    }
+    start_out[ns] = q;
+    *nsuper_out = ns;
+    return CGGM_OK;
+}

@@ -73,3 +73,31 @@ def test_dense_pattern():
     parent, cc, nnz, fill = symbolic.analyse(q, rp, ci, np.arange(q))
     assert cc.tolist() == list(range(q, 0, -1)) and fill == 0
     assert parent.tolist() == list(range(1, q)) + [-1]
+
+
+def test_supernodes_closed_forms():
+    """A dense pattern is one supernode; a path splits into single columns except its last
+    two (column q-2 below its diagonal is {q-1}, the pattern of the last column); with a
+    hub eliminated last every column stands alone (the hub has q-1 children)."""
+    q = 6
+    L = symbolic.cholesky_pattern(np.ones((q, q), dtype=bool), np.arange(q))
+    assert symbolic.fundamental_supernodes(L).tolist() == [0, q]
+    A = np.eye(q, dtype=bool) | np.eye(q, k=1, dtype=bool) | np.eye(q, k=-1, dtype=bool)
+    L = symbolic.cholesky_pattern(A, np.arange(q))
+    assert symbolic.fundamental_supernodes(L).tolist() == [0, 1, 2, 3, 4, q]
+    H = np.eye(q, dtype=bool)
+    H[0, :] = H[:, 0] = True
+    L = symbolic.cholesky_pattern(H, np.r_[np.arange(1, q), 0])
+    assert symbolic.fundamental_supernodes(L).tolist() == list(range(q)) + [q]
+
+
+def test_supernode_columns_share_their_pattern():
+    """Within every supernode each column's pattern below the diagonal is the next
+    column's pattern: the columns form one dense block with a common row set."""
+    A = random_pattern(50, 120, 9)
+    L = symbolic.cholesky_pattern(A, np.arange(50))
+    s = symbolic.fundamental_supernodes(L)
+    assert s[0] == 0 and s[-1] == 50 and np.all(np.diff(s) > 0)
+    for a, b in zip(s[:-1], s[1:]):
+        for k in range(a, b - 1):
+            assert np.array_equal(L[k + 1:, k], L[k + 1:, k + 1])

@@ -162,3 +162,25 @@ def test_empty_and_errors():
         cg.chol_symbolic(2, np.array([0, 1, 2]), np.array([1, 2]), cg.CGGM_ORDER_NATURAL)
     with pytest.raises(cg.CGGMError):
         cg.chol_symbolic(2, np.array([0, 2, 1]), np.array([1, 0]), cg.CGGM_ORDER_NATURAL)
+
+
+@pytest.mark.parametrize("q,m,seed", [(1, 0, 12), (30, 25, 13), (80, 160, 14), (60, 900, 15)])
+def test_supernodes_match_the_oracle(q, m, seed):
+    rp, ci = random_csr(q, m, seed)
+    rng = np.random.default_rng(seed)
+    for perm in (np.arange(q), rng.permutation(q)):
+        _, parent, cc, _ = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_GIVEN, perm)
+        L = symbolic.cholesky_pattern(symbolic.pattern_from_csr(q, rp, ci), perm)
+        assert np.array_equal(cg.chol_supernodes(parent, cc), symbolic.fundamental_supernodes(L))
+
+
+def test_supernodes_of_a_dense_block_and_errors():
+    q = 7
+    A = sp.csr_matrix(np.ones((q, q)))
+    _, parent, cc, _ = cg.chol_symbolic(q, A.indptr, A.indices, cg.CGGM_ORDER_NATURAL)
+    assert cg.chol_supernodes(parent, cc).tolist() == [0, q]
+    assert cg.chol_supernodes(np.zeros(0, np.int32), np.zeros(0, np.int64)).tolist() == [0]
+    with pytest.raises(cg.CGGMError):
+        cg.chol_supernodes([1, 0], [2, 1])          # a parent below its child
+    with pytest.raises(cg.CGGMError):
+        cg.chol_supernodes([1, -1], [3, 1])         # more entries than rows left
