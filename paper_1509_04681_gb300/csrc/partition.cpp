@@ -35,11 +35,13 @@
 #include <vector>
 
 #include "../../include/cggm.h"
+#include "graph_order.hpp"
 
 namespace {
 
+using namespace cggm;
+
 constexpr int kRefinePasses = 8;
-constexpr int kPseudoPeripheralSweeps = 4;
 constexpr int64_t kCliqueMaxRow = 16;  // rows with more active columns are joined as a path
 
 struct Graph {
@@ -93,62 +95,6 @@ Graph build_graph(int64_t n, const std::vector<Edge> &edges)
         g.ptr[v + 1] = (int64_t)g.adj.size();
     }
     return g;
-}
-
-// Breadth-first search over one component from `root`; fills `order` (visit order) and
-// `level`; neighbours are taken by ascending (degree, index) when `by_degree`.
-void bfs(const Graph &g, int32_t root, std::vector<int32_t> &order, std::vector<int32_t> &level,
-         bool by_degree)
-{
-    order.clear();
-    order.push_back(root);
-    level[root] = 0;
-    std::vector<int32_t> nb;
-    for (size_t h = 0; h < order.size(); h++) {
-        const int32_t v = order[h];
-        nb.clear();
-        for (int64_t t = g.ptr[v]; t < g.ptr[v + 1]; t++)
-            if (level[g.adj[t]] < 0) nb.push_back(g.adj[t]);
-        if (by_degree)
-            std::sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) {
-                const int64_t da = g.degree(a), db = g.degree(b);
-                return da != db ? da < db : a < b;
-            });
-        for (int32_t u : nb) {
-            if (level[u] >= 0) continue;
-            level[u] = level[v] + 1;
-            order.push_back(u);
-        }
-    }
-}
-
-// Cuthill-McKee order of the component of `seed`, from a pseudo-peripheral vertex: start
-// at the component's vertex of least degree, and move to the least-degree vertex of the
-// last level while that lengthens the search.
-std::vector<int32_t> component_order(const Graph &g, int32_t seed, std::vector<int32_t> &level)
-{
-    std::vector<int32_t> order;
-    bfs(g, seed, order, level, false);
-    int32_t root = seed;
-    for (int32_t v : order)
-        if (g.degree(v) < g.degree(root) || (g.degree(v) == g.degree(root) && v < root)) root = v;
-    int32_t depth = -1;
-    for (int s = 0; s < kPseudoPeripheralSweeps; s++) {
-        for (int32_t v : order) level[v] = -1;
-        bfs(g, root, order, level, false);
-        const int32_t d = level[order.back()];
-        if (d <= depth) break;
-        depth = d;
-        int32_t next = order.back();
-        for (int32_t v : order)
-            if (level[v] == d &&
-                (g.degree(v) < g.degree(next) || (g.degree(v) == g.degree(next) && v < next)))
-                next = v;
-        root = next;
-    }
-    for (int32_t v : order) level[v] = -1;
-    bfs(g, root, order, level, true);
-    return order;
 }
 
 // Pieces (vertex lists of weight at most cap) grouped into blocks: pairs of pieces are
@@ -273,7 +219,7 @@ std::vector<int32_t> initial_blocks(const Graph &g, int64_t cap)
     std::vector<int64_t> piece_w;
     for (int32_t v = 0; v < n; v++) {
         if (level[v] >= 0) continue;
-        std::vector<int32_t> ord = component_order(g, v, level);
+        std::vector<int32_t> ord = graph::cuthill_mckee(g, v, level);
         const int64_t size = (int64_t)ord.size();
         const int64_t parts = (size + cap - 1) / cap;
         int64_t at = 0;

@@ -27,6 +27,7 @@
 #include <vector>
 
 #include "../../include/cggm.h"
+#include "graph_order.hpp"
 
 namespace {
 
@@ -69,61 +70,16 @@ Adjacency symmetrise(int64_t q, const int64_t *row_ptr, const int32_t *col)
     return a;
 }
 
-// Breadth-first visit of the component of `root` into `order`; levels in `level`.
-void bfs(const Adjacency &a, int32_t root, std::vector<int32_t> &order,
-         std::vector<int32_t> &level, bool by_degree)
-{
-    order.clear();
-    order.push_back(root);
-    level[root] = 0;
-    std::vector<int32_t> nb;
-    for (size_t h = 0; h < order.size(); h++) {
-        const int32_t v = order[h];
-        nb.clear();
-        for (int64_t t = a.ptr[v]; t < a.ptr[v + 1]; t++)
-            if (level[a.adj[t]] < 0) nb.push_back(a.adj[t]);
-        if (by_degree)
-            std::sort(nb.begin(), nb.end(), [&](int32_t x, int32_t y) {
-                return a.degree(x) != a.degree(y) ? a.degree(x) < a.degree(y) : x < y;
-            });
-        for (int32_t u : nb)
-            if (level[u] < 0) {
-                level[u] = level[v] + 1;
-                order.push_back(u);
-            }
-    }
-}
-
-// Reverse Cuthill-McKee order (new -> old): each component from a pseudo-peripheral
-// vertex (the least-degree vertex of the last level, while that deepens the search).
+// Reverse Cuthill-McKee order (new -> old): the Cuthill-McKee orders of the components, in
+// the order of their lowest vertex, concatenated and reversed.
 std::vector<int32_t> rcm_order(const Adjacency &a, int64_t q)
 {
-    std::vector<int32_t> level(q, -1), order, comp, perm;
+    std::vector<int32_t> level(q, -1), perm;
     perm.reserve(q);
     for (int32_t s = 0; s < q; s++) {
         if (level[s] >= 0) continue;
-        bfs(a, s, comp, level, false);
-        int32_t root = s;
-        for (int32_t v : comp)
-            if (a.degree(v) < a.degree(root) || (a.degree(v) == a.degree(root) && v < root))
-                root = v;
-        int32_t depth = -1;
-        for (int sweep = 0; sweep < 4; sweep++) {
-            for (int32_t v : comp) level[v] = -1;
-            bfs(a, root, comp, level, false);
-            const int32_t d = level[comp.back()];
-            if (d <= depth) break;
-            depth = d;
-            int32_t next = comp.back();
-            for (int32_t v : comp)
-                if (level[v] == d && (a.degree(v) < a.degree(next) ||
-                                      (a.degree(v) == a.degree(next) && v < next)))
-                    next = v;
-            root = next;
-        }
-        for (int32_t v : comp) level[v] = -1;
-        bfs(a, root, order, level, true);
-        perm.insert(perm.end(), order.begin(), order.end());
+        const std::vector<int32_t> comp = cggm::graph::cuthill_mckee(a, s, level);
+        perm.insert(perm.end(), comp.begin(), comp.end());
     }
     std::reverse(perm.begin(), perm.end());
     return perm;
