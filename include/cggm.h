@@ -362,6 +362,24 @@ cggm_status cggm_partition_theta_columns(int64_t p, int64_t q, int64_t m, const 
                                          int32_t *block_out, int64_t *nblocks_out,
                                          int64_t *row_blocks_out);
 
+/* Visiting order of the blocked coordinate passes of Algorithm 2 for a column partition
+ * (one block id per column, ids 0..k-1, none empty), and the cache counts of Section 4.
+ *   kind 0 (Lambda): (ci[t], cj[t]) with 0 <= ci <= cj < q; a coordinate belongs to the
+ *   block pair (z, r), z <= r, of its indices' blocks, a being the index in block z; the
+ *   pass runs by z, then r, then a, then b.  It forms Sigma (and Psi) columns for every
+ *   block once and again for block r at each off-diagonal pair holding a coordinate:
+ *   *columns_out = q + the sizes of those blocks, *misses_out = the number of such pairs.
+ *   kind 1 (Theta): (ci[t], cj[t]) = (i, j) with i >= 0, 0 <= j < q; the pass runs by the
+ *   block of j, then i, then j; *columns_out = q (Sigma once), *misses_out = the number of
+ *   non-empty (i, block) pairs, each one row of S_xx formed.
+ *   order_out (m, caller-owned host): positions into the input list in visiting order.
+ *   columns_out, misses_out: optional.  Host code, no GPU use.
+ * Errors: CGGM_EINVAL for another kind, negative sizes, a null pointer the sizes need, a
+ * block id outside [0, q) or an empty block, or an index out of range. */
+cggm_status cggm_block_order(int kind, int64_t q, int64_t m, const int32_t *ci,
+                             const int32_t *cj, const int32_t *block, int32_t *order_out,
+                             int64_t *columns_out, int64_t *misses_out);
+
 /* Pivot orders for cggm_chol_symbolic. */
 typedef enum {
     CGGM_ORDER_NATURAL = 0, /* columns as numbered                                        */

@@ -26,6 +26,7 @@ from .cggm import (  # noqa: F401
     partition_theta_columns,
     chol_symbolic,
     chol_supernodes,
+    block_order,
     CGGM_ORDER_NATURAL,
     CGGM_ORDER_RCM,
     CGGM_ORDER_GIVEN,

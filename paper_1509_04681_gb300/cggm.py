@@ -33,6 +33,7 @@ EXPORTED = [
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
     "cggm_partition_theta_columns", "cggm_chol_symbolic", "cggm_chol_supernodes",
+    "cggm_block_order",
 ]
 
 
@@ -135,6 +136,8 @@ def _lib():
                                                      ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.cggm_chol_symbolic.argtypes = [i64, vp, vp, ip, vp, vp, vp, vp, ctypes.POINTER(i64)]
         lib.cggm_chol_supernodes.argtypes = [i64, vp, vp, vp, ctypes.POINTER(i64)]
+        lib.cggm_block_order.argtypes = [ip, i64, i64, vp, vp, vp, vp, ctypes.POINTER(i64),
+                                         ctypes.POINTER(i64)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -148,6 +151,7 @@ def _lib():
                                                      "cggm_partition_theta_columns",
                                                      "cggm_chol_symbolic",
                                                      "cggm_chol_supernodes",
+                                                     "cggm_block_order",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -489,6 +493,28 @@ def chol_supernodes(parent, colcount):
                                        start.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ns)),
            "cggm_chol_supernodes")
     return start[:ns.value + 1].copy()
+
+
+def block_order(kind: str, q: int, ci, cj, block):
+    """Visiting order of a blocked pass of Algorithm 2 (cggm_block_order); kind "lambda"
+    or "theta".  Host memory only.  Returns (order, columns, misses): positions into the
+    coordinate list in visiting order, the Sigma columns the pass forms, and its misses
+    (off-diagonal block pairs loaded for Lambda, rows of S_xx formed for Theta)."""
+    k = {"lambda": 0, "theta": 1}[kind]
+    ci, pi = _host_i32(ci)
+    cj, pj = _host_i32(cj)
+    block, pb = _host_i32(block)
+    if ci.shape != cj.shape:
+        raise ValueError("ci and cj differ in length")
+    if block.shape != (int(q),):
+        raise ValueError("block must hold q entries")
+    order = np.empty(ci.size, dtype=np.int32)
+    cols = ctypes.c_int64()
+    miss = ctypes.c_int64()
+    _check(_lib().cggm_block_order(k, int(q), int(ci.size), pi, pj, pb,
+                                   order.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cols),
+                                   ctypes.byref(miss)), "cggm_block_order")
+    return order, int(cols.value), int(miss.value)
 
 
 def make_opts(**kw) -> cggm_opts:

@@ -526,3 +526,74 @@ extern "C" cggm_status cggm_partition_theta_columns(int64_t p, int64_t q, int64_
     }
     return CGGM_OK;
 }
+
+// Visiting order of the blocked passes of Algorithm 2 and the cache counts of Section 4.
+// Lambda: each coordinate (i, j), i <= j, belongs to the block pair (z, r) of its indices'
+// blocks, z <= r, with a the index in block z and b the other; the pass runs by (z, r),
+// then a, then b.  It forms the Sigma columns of every block once (as block z) and those
+// of block r again for each off-diagonal pair (z, r) holding a coordinate (a miss).
+// Theta: by the block r of j, then row i, then j; Sigma is formed once (q columns) and a
+// row of S_xx for each non-empty (i, C_r) (a miss).
+extern "C" cggm_status cggm_block_order(int kind, int64_t q, int64_t m, const int32_t *ci,
+                                        const int32_t *cj, const int32_t *block,
+                                        int32_t *order_out, int64_t *columns_out,
+                                        int64_t *misses_out)
+{
+    if ((kind != 0 && kind != 1) || q < 0 || q > INT32_MAX || m < 0 || m > INT32_MAX)
+        return CGGM_EINVAL;
+    if ((q > 0 && !block) || (m > 0 && (!ci || !cj || !order_out))) return CGGM_EINVAL;
+    int32_t nb = 0;
+    for (int64_t v = 0; v < q; v++) {
+        if (block[v] < 0 || block[v] >= q) return CGGM_EINVAL;
+        nb = std::max(nb, block[v] + 1);
+    }
+    std::vector<int64_t> size(nb, 0);
+    for (int64_t v = 0; v < q; v++) size[block[v]]++;
+    for (int32_t z = 0; z < nb; z++)
+        if (size[z] == 0) return CGGM_EINVAL;  // ids must be 0..k-1 with no empty block
+    struct Key {
+        int32_t k0, k1, k2, k3;
+        int32_t pos;
+    };
+    std::vector<Key> keys((size_t)m);
+    for (int64_t t = 0; t < m; t++) {
+        const int32_t i = ci[t], j = cj[t];
+        if (kind == 0) {
+            if (i < 0 || j < i || j >= q) return CGGM_EINVAL;
+            const bool swap = block[i] > block[j];
+            const int32_t a = swap ? j : i, b = swap ? i : j;
+            keys[t] = {block[a], block[b], a, b, (int32_t)t};
+        } else {
+            if (i < 0 || j < 0 || j >= q) return CGGM_EINVAL;
+            keys[t] = {block[j], i, j, 0, (int32_t)t};
+        }
+    }
+    std::stable_sort(keys.begin(), keys.end(), [](const Key &x, const Key &y) {
+        if (x.k0 != y.k0) return x.k0 < y.k0;
+        if (x.k1 != y.k1) return x.k1 < y.k1;
+        if (x.k2 != y.k2) return x.k2 < y.k2;
+        return x.k3 < y.k3;
+    });
+    int64_t columns = 0, misses = 0;
+    if (kind == 0) {
+        columns = q;  // every block once, as block z
+        for (int64_t t = 0; t < m; t++) {
+            const Key &k = keys[t];
+            const bool first = t == 0 || keys[t - 1].k0 != k.k0 || keys[t - 1].k1 != k.k1;
+            if (first && k.k0 != k.k1) {
+                misses++;
+                columns += size[k.k1];
+            }
+        }
+    } else {
+        columns = q;
+        for (int64_t t = 0; t < m; t++) {
+            const Key &k = keys[t];
+            if (t == 0 || keys[t - 1].k0 != k.k0 || keys[t - 1].k1 != k.k1) misses++;
+        }
+    }
+    for (int64_t t = 0; t < m; t++) order_out[t] = keys[t].pos;
+    if (columns_out) *columns_out = columns;
+    if (misses_out) *misses_out = misses;
+    return CGGM_OK;
+}
