@@ -414,6 +414,20 @@ cggm_status cggm_chol_symbolic(int64_t q, const int64_t *row_ptr, const int32_t 
                                int32_t *parent_out, int64_t *colcount_out,
                                int64_t *nnz_L_out);
 
+/* Symmetric permutation of a q x q CSR matrix, B = P A P^T with B[k][l] = A[perm[k]][perm[l]]
+ * (perm[k] = the original index of new index k): with the order of a column partition's
+ * blocks it makes every block a contiguous range of columns, the layout the blocked passes
+ * of Algorithm 2 and a sparse factorisation work on.  Host code, no GPU use.
+ *   row_ptr (q + 1), col, val (nnz = row_ptr[q]; val and out_val may be NULL for a pattern
+ *   only): the input; out_row_ptr (q + 1), out_col, out_val (nnz): caller-owned host
+ *   output, columns ascending within each row (entries repeated in the input stay
+ *   repeated, in their input order).
+ * Errors: CGGM_EINVAL for q < 0, a null pointer the sizes need, a malformed CSR, or a
+ * perm that is not a permutation of 0..q-1. */
+cggm_status cggm_permute_csr(int64_t q, const int64_t *row_ptr, const int32_t *col,
+                             const double *val, const int32_t *perm, int64_t *out_row_ptr,
+                             int32_t *out_col, double *out_val);
+
 /* Fundamental supernodes of the factor analysed by cggm_chol_symbolic: maximal runs of
  * consecutive pivots whose columns share one row pattern below the run (a dense block of
  * L), the unit of work of a supernodal numeric factorisation.  Pivot k + 1 continues the

@@ -27,6 +27,7 @@ from .cggm import (  # noqa: F401
     chol_symbolic,
     chol_supernodes,
     block_order,
+    permute_csr,
     CGGM_ORDER_NATURAL,
     CGGM_ORDER_RCM,
     CGGM_ORDER_GIVEN,

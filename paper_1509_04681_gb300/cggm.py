@@ -33,7 +33,7 @@ EXPORTED = [
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
     "cggm_partition_theta_columns", "cggm_chol_symbolic", "cggm_chol_supernodes",
-    "cggm_block_order",
+    "cggm_block_order", "cggm_permute_csr",
 ]
 
 
@@ -138,6 +138,7 @@ def _lib():
         lib.cggm_chol_supernodes.argtypes = [i64, vp, vp, vp, ctypes.POINTER(i64)]
         lib.cggm_block_order.argtypes = [ip, i64, i64, vp, vp, vp, vp, ctypes.POINTER(i64),
                                          ctypes.POINTER(i64)]
+        lib.cggm_permute_csr.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -152,6 +153,7 @@ def _lib():
                                                      "cggm_chol_symbolic",
                                                      "cggm_chol_supernodes",
                                                      "cggm_block_order",
+                                                     "cggm_permute_csr",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -515,6 +517,36 @@ def block_order(kind: str, q: int, ci, cj, block):
                                    order.ctypes.data_as(ctypes.c_void_p), ctypes.byref(cols),
                                    ctypes.byref(miss)), "cggm_block_order")
     return order, int(cols.value), int(miss.value)
+
+
+def permute_csr(q: int, row_ptr, col, val, perm):
+    """B = P A P^T of a q x q CSR matrix (cggm_permute_csr), B[k][l] = A[perm[k]][perm[l]].
+    Host memory only; val may be None for a pattern.  Returns (row_ptr, col, val)."""
+    q = int(q)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci, pci = _host_i32(col)
+    perm, pp = _host_i32(perm)
+    if rp.shape != (q + 1,) or perm.shape != (q,):
+        raise ValueError("row_ptr must hold q + 1 entries and perm q")
+    nnz = int(rp[-1]) if q > 0 else 0
+    if ci.size != nnz:
+        raise ValueError("col must hold row_ptr[q] entries")
+    pv = None
+    out_val = None
+    if val is not None:
+        val = np.ascontiguousarray(val, dtype=np.float64)
+        if val.shape != (nnz,):
+            raise ValueError("val must hold row_ptr[q] entries")
+        pv = val.ctypes.data_as(ctypes.c_void_p)
+        out_val = np.empty(nnz, dtype=np.float64)
+    out_rp = np.empty(q + 1, dtype=np.int64)
+    out_ci = np.empty(nnz, dtype=np.int32)
+    _check(_lib().cggm_permute_csr(q, rp.ctypes.data_as(ctypes.c_void_p), pci, pv, pp,
+                                   out_rp.ctypes.data_as(ctypes.c_void_p),
+                                   out_ci.ctypes.data_as(ctypes.c_void_p),
+                                   out_val.ctypes.data_as(ctypes.c_void_p)
+                                   if out_val is not None else None), "cggm_permute_csr")
+    return out_rp, out_ci, out_val
 
 
 def make_opts(**kw) -> cggm_opts:

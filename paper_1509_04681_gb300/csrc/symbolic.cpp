@@ -237,3 +237,46 @@ extern "C" cggm_status cggm_chol_supernodes(int64_t q, const int32_t *parent,
     *nsuper_out = ns;
     return CGGM_OK;
 }
+
+extern "C" cggm_status cggm_permute_csr(int64_t q, const int64_t *row_ptr, const int32_t *col,
+                                        const double *val, const int32_t *perm,
+                                        int64_t *out_row_ptr, int32_t *out_col,
+                                        double *out_val)
+{
+    if (q < 0 || q > INT32_MAX) return CGGM_EINVAL;
+    if (q > 0 && (!row_ptr || !perm || !out_row_ptr)) return CGGM_EINVAL;
+    if (q == 0) {
+        if (out_row_ptr) out_row_ptr[0] = 0;
+        return CGGM_OK;
+    }
+    if (row_ptr[0] != 0) return CGGM_EINVAL;
+    for (int64_t i = 0; i < q; i++)
+        if (row_ptr[i + 1] < row_ptr[i]) return CGGM_EINVAL;
+    const int64_t nnz = row_ptr[q];
+    if (nnz > 0 && (!col || !out_col)) return CGGM_EINVAL;
+    std::vector<int32_t> iperm(q, -1);
+    for (int32_t k = 0; k < q; k++) {
+        if (perm[k] < 0 || perm[k] >= q || iperm[perm[k]] >= 0) return CGGM_EINVAL;
+        iperm[perm[k]] = k;
+    }
+    for (int64_t t = 0; t < nnz; t++)
+        if (col[t] < 0 || col[t] >= q) return CGGM_EINVAL;
+    // row k of the result is row perm[k] of the input with its columns renamed, sorted
+    std::vector<std::pair<int32_t, int64_t>> row;  // (new column, source position)
+    int64_t at = 0;
+    out_row_ptr[0] = 0;
+    for (int32_t k = 0; k < q; k++) {
+        const int32_t src = perm[k];
+        row.clear();
+        for (int64_t t = row_ptr[src]; t < row_ptr[src + 1]; t++) row.push_back({iperm[col[t]], t});
+        std::stable_sort(row.begin(), row.end(),
+                         [](const auto &x, const auto &y) { return x.first < y.first; });
+        for (const auto &e : row) {
+            out_col[at] = e.first;
+            if (val && out_val) out_val[at] = val[e.second];
+            at++;
+        }
+        out_row_ptr[k + 1] = at;
+    }
+    return CGGM_OK;
+}

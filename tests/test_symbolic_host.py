@@ -184,3 +184,32 @@ def test_supernodes_of_a_dense_block_and_errors():
         cg.chol_supernodes([1, 0], [2, 1])          # a parent below its child
     with pytest.raises(cg.CGGMError):
         cg.chol_supernodes([1, -1], [3, 1])         # more entries than rows left
+
+
+@pytest.mark.parametrize("q,m,seed", [(1, 1, 16), (25, 60, 17), (200, 900, 18)])
+def test_permute_csr_is_the_definition(q, m, seed):
+    """B[k][l] = A[perm[k]][perm[l]] entry for entry, columns ascending in every row."""
+    rng = np.random.default_rng(seed)
+    i = rng.integers(0, q, m)
+    j = rng.integers(0, q, m)
+    A = sp.csr_matrix((rng.standard_normal(m), (i, j)), shape=(q, q))
+    A.sum_duplicates()
+    perm = rng.permutation(q)
+    rp, ci, v = cg.permute_csr(q, A.indptr, A.indices, A.data, perm)
+    B = sp.csr_matrix((v, ci, rp), shape=(q, q))
+    assert np.array_equal(B.toarray(), A.toarray()[np.ix_(perm, perm)])
+    assert all(np.all(np.diff(ci[rp[k]:rp[k + 1]]) > 0) for k in range(q))
+    # pattern only, and the inverse permutation restores A
+    rp2, ci2, v2 = cg.permute_csr(q, A.indptr, A.indices, None, perm)
+    assert v2 is None and np.array_equal(rp2, rp) and np.array_equal(ci2, ci)
+    back = cg.permute_csr(q, rp, ci, v, np.argsort(perm))
+    assert np.array_equal(back[0], A.indptr) and np.array_equal(back[1], A.indices)
+    assert np.array_equal(back[2], A.data)
+
+
+def test_permute_csr_errors():
+    rp, ci, v = np.array([0, 1, 2]), np.array([1, 0]), np.array([1.0, 2.0])
+    with pytest.raises(cg.CGGMError):
+        cg.permute_csr(2, rp, ci, v, [1, 1])                  # not a permutation
+    with pytest.raises(cg.CGGMError):
+        cg.permute_csr(2, rp, np.array([1, 2]), v, [1, 0])    # column out of range
