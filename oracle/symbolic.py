@@ -85,3 +85,35 @@ def fundamental_supernodes(L: np.ndarray) -> np.ndarray:
         if not (same and children[k + 1] == 1):
             starts.append(k + 1)
     return np.array(starts + [q], dtype=np.int64)
+
+
+def minimum_degree_order(A: np.ndarray, dense_rest: float = 0.9) -> np.ndarray:
+    """Minimum-degree pivot order by the elimination game on the pattern A (dense boolean,
+    symmetric): repeatedly take the remaining vertex of least degree in the elimination
+    graph (ties: lower index), join its neighbours into a clique and remove it.  Once more
+    than 64 vertices remain and the least degree plus one reaches ``dense_rest`` times their
+    number, the remaining graph is nearly complete and the rest follow in (degree, index)
+    order."""
+    q = A.shape[0]
+    G = A.copy()
+    np.fill_diagonal(G, False)
+    alive = np.ones(q, dtype=bool)
+    order = []
+    while len(order) < q:
+        idx = np.flatnonzero(alive)
+        deg = G[np.ix_(idx, idx)].sum(axis=1)
+        remaining = idx.size
+        best = int(np.lexsort((idx, deg))[0])
+        if remaining > 64 and deg[best] + 1 >= dense_rest * remaining:
+            rest = idx[np.lexsort((idx, deg))]
+            order.extend(int(v) for v in rest)
+            break
+        v = int(idx[best])
+        nb = np.flatnonzero(G[v] & alive)
+        G[np.ix_(nb, nb)] = True
+        G[nb, nb] = False
+        alive[v] = False
+        G[v, :] = False
+        G[:, v] = False
+        order.append(v)
+    return np.array(order, dtype=np.int64)

@@ -101,3 +101,35 @@ def test_supernode_columns_share_their_pattern():
     for a, b in zip(s[:-1], s[1:]):
         for k in range(a, b - 1):
             assert np.array_equal(L[k + 1:, k], L[k + 1:, k + 1])
+
+
+def test_minimum_degree_closed_forms():
+    """On a forest every step takes a vertex of degree at most one (no fill); a star's
+    leaves go first, the hub once it is down to one leaf (the tie goes to its lower index);
+    a complete graph is taken in index order; a path from an end."""
+    q = 7
+    star = np.eye(q, dtype=bool)
+    star[3, :] = star[:, 3] = True
+    assert symbolic.minimum_degree_order(star).tolist() == [0, 1, 2, 4, 5, 3, 6]
+    assert symbolic.minimum_degree_order(np.ones((q, q), dtype=bool)).tolist() == list(range(q))
+    A = np.eye(q, dtype=bool) | np.eye(q, k=1, dtype=bool) | np.eye(q, k=-1, dtype=bool)
+    assert symbolic.minimum_degree_order(A).tolist() == list(range(q))
+    rng = np.random.default_rng(3)
+    q = 60
+    F = np.eye(q, dtype=bool)
+    for v in range(1, q):
+        if v % 7:
+            u = rng.integers(0, v)
+            F[u, v] = F[v, u] = True
+    L = symbolic.cholesky_pattern(F, symbolic.minimum_degree_order(F))
+    assert L.sum() == q + (F.sum() - q) // 2            # no fill
+
+
+def test_minimum_degree_dense_rest():
+    """More than 64 vertices left, least degree + 1 >= 0.9 x remaining: the rest in (degree,
+    index) order, which on a complete graph is the index order from the first step."""
+    q = 80
+    A = np.ones((q, q), dtype=bool)
+    A[0, 1] = A[1, 0] = False                           # degrees 78, 78, then 79 ...
+    order = symbolic.minimum_degree_order(A)
+    assert order.tolist() == list(range(q))

@@ -213,3 +213,14 @@ def test_permute_csr_errors():
         cg.permute_csr(2, rp, ci, v, [1, 1])                  # not a permutation
     with pytest.raises(cg.CGGMError):
         cg.permute_csr(2, rp, np.array([1, 2]), v, [1, 0])    # column out of range
+
+
+@pytest.mark.parametrize("q,m,seed", [(40, 50, 19), (90, 130, 20), (120, 1500, 21),
+                                      (150, 6000, 22), (70, 0, 23)])
+def test_min_degree_order_matches_the_oracle(q, m, seed):
+    """The minimum-degree order is a definition with fixed tie-breaks, so the library's
+    order equals the oracle's elimination game pivot for pivot, dense remainder included."""
+    rp, ci = random_csr(q, m, seed)
+    perm, _, _, _ = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_MINDEG)
+    ref = symbolic.minimum_degree_order(symbolic.pattern_from_csr(q, rp, ci))
+    assert np.array_equal(perm, ref)
