@@ -415,6 +415,24 @@ cggm_status cggm_chol_symbolic(int64_t q, const int64_t *row_ptr, const int32_t 
                                int32_t *parent_out, int64_t *colcount_out,
                                int64_t *nnz_L_out);
 
+/* Row structure of the supernodes (cggm_chol_supernodes) of the sparse Cholesky factor
+ * analysed by cggm_chol_symbolic: for supernode s, the sorted rows (pivot numbering) of its
+ * dense block of L, its own columns first.  A numeric factorisation allocates and
+ * addresses L from it.  Host code, no GPU use.
+ *   row_ptr, col: the pattern as given to cggm_chol_symbolic; perm, parent, colcount: its
+ *   outputs; nsuper, super_start: cggm_chol_supernodes' outputs.
+ *   rows_ptr_out (nsuper + 1): offsets, rows_ptr_out[s + 1] - rows_ptr_out[s] =
+ *   colcount[super_start[s]]; rows_out (rows_ptr_out[nsuper] entries, or NULL to get the
+ *   offsets only).  Caller-owned host memory.
+ * Errors: CGGM_EINVAL for sizes out of range, a null pointer the sizes need, a malformed
+ * CSR, perm not a permutation, a supernode list not increasing from 0 to q, or inputs not
+ * from one analysis (a structure whose size disagrees with the column counts). */
+cggm_status cggm_chol_structure(int64_t q, const int64_t *row_ptr, const int32_t *col,
+                                const int32_t *perm, const int32_t *parent,
+                                const int64_t *colcount, int64_t nsuper,
+                                const int64_t *super_start, int64_t *rows_ptr_out,
+                                int32_t *rows_out);
+
 /* Symmetric permutation of a q x q CSR matrix, B = P A P^T with B[k][l] = A[perm[k]][perm[l]]
  * (perm[k] = the original index of new index k): with the order of a column partition's
  * blocks it makes every block a contiguous range of columns, the layout the blocked passes

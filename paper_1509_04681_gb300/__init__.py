@@ -26,6 +26,7 @@ from .cggm import (  # noqa: F401
     partition_theta_columns,
     chol_symbolic,
     chol_supernodes,
+    chol_structure,
     block_order,
     permute_csr,
     CGGM_ORDER_NATURAL,

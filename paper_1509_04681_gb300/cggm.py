@@ -33,7 +33,7 @@ EXPORTED = [
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
     "cggm_partition_theta_columns", "cggm_chol_symbolic", "cggm_chol_supernodes",
-    "cggm_block_order", "cggm_permute_csr",
+    "cggm_block_order", "cggm_permute_csr", "cggm_chol_structure",
 ]
 
 
@@ -139,6 +139,7 @@ def _lib():
         lib.cggm_block_order.argtypes = [ip, i64, i64, vp, vp, vp, vp, ctypes.POINTER(i64),
                                          ctypes.POINTER(i64)]
         lib.cggm_permute_csr.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
+        lib.cggm_chol_structure.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp, vp, vp]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -154,6 +155,7 @@ def _lib():
                                                      "cggm_chol_supernodes",
                                                      "cggm_block_order",
                                                      "cggm_permute_csr",
+                                                     "cggm_chol_structure",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -547,6 +549,27 @@ def permute_csr(q: int, row_ptr, col, val, perm):
                                    out_val.ctypes.data_as(ctypes.c_void_p)
                                    if out_val is not None else None), "cggm_permute_csr")
     return out_rp, out_ci, out_val
+
+
+def chol_structure(q: int, row_ptr, col, perm, parent, colcount, super_start):
+    """Row structure of each supernode of the factor (cggm_chol_structure) from the outputs
+    of chol_symbolic and chol_supernodes.  Host memory only.  Returns (rows_ptr, rows)."""
+    q = int(q)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    ci, pci = _host_i32(col)
+    perm, pp = _host_i32(perm)
+    parent, ppar = _host_i32(parent)
+    cc = np.ascontiguousarray(colcount, dtype=np.int64)
+    ss = np.ascontiguousarray(super_start, dtype=np.int64)
+    ns = ss.size - 1
+    vp = ctypes.c_void_p
+    rows_ptr = np.empty(ns + 1, dtype=np.int64)
+    args = [q, rp.ctypes.data_as(vp), pci, pp, ppar, cc.ctypes.data_as(vp), ns,
+            ss.ctypes.data_as(vp), rows_ptr.ctypes.data_as(vp)]
+    _check(_lib().cggm_chol_structure(*args, None), "cggm_chol_structure")
+    rows = np.empty(int(rows_ptr[-1]), dtype=np.int32)
+    _check(_lib().cggm_chol_structure(*args, rows.ctypes.data_as(vp)), "cggm_chol_structure")
+    return rows_ptr, rows
 
 
 def make_opts(**kw) -> cggm_opts:

@@ -280,3 +280,84 @@ extern "C" cggm_status cggm_permute_csr(int64_t q, const int64_t *row_ptr, const
     }
     return CGGM_OK;
 }
+
+// Row structure of every supernode (the sorted rows of its dense block of L, in pivot
+// numbering): its own columns, the rows below it where the permuted pattern has an entry
+// in one of its columns, and the rows below it of its child supernodes (a child's rows
+// past its own columns all lie in its parent's structure), merged in supernode order so
+// that every child is done before its parent.
+extern "C" cggm_status cggm_chol_structure(int64_t q, const int64_t *row_ptr, const int32_t *col,
+                                           const int32_t *perm, const int32_t *parent,
+                                           const int64_t *colcount, int64_t nsuper,
+                                           const int64_t *super_start, int64_t *rows_ptr_out,
+                                           int32_t *rows_out)
+{
+    if (q < 0 || q > INT32_MAX || nsuper < 0 || nsuper > q || !rows_ptr_out) return CGGM_EINVAL;
+    if (q > 0 && (!row_ptr || !col || !perm || !parent || !colcount || !super_start))
+        return CGGM_EINVAL;
+    if ((q == 0) != (nsuper == 0)) return CGGM_EINVAL;
+    rows_ptr_out[0] = 0;
+    if (q == 0) return CGGM_OK;
+    if (super_start[0] != 0 || super_start[nsuper] != q) return CGGM_EINVAL;
+    for (int64_t s = 0; s < nsuper; s++)
+        if (super_start[s + 1] <= super_start[s]) return CGGM_EINVAL;
+    for (int64_t s = 0; s < nsuper; s++) {
+        const int64_t c = colcount[super_start[s]];
+        if (c < 1 || c > q - super_start[s]) return CGGM_EINVAL;
+        rows_ptr_out[s + 1] = rows_ptr_out[s] + c;
+    }
+    if (!rows_out) return CGGM_OK;  // sizes only
+    if (row_ptr[0] != 0) return CGGM_EINVAL;
+    for (int64_t i = 0; i < q; i++)
+        if (row_ptr[i + 1] < row_ptr[i]) return CGGM_EINVAL;
+    std::vector<int32_t> iperm(q, -1), snode(q);
+    for (int32_t k = 0; k < q; k++) {
+        if (perm[k] < 0 || perm[k] >= q || iperm[perm[k]] >= 0) return CGGM_EINVAL;
+        iperm[perm[k]] = k;
+    }
+    for (int64_t t = 0; t < row_ptr[q]; t++)
+        if (col[t] < 0 || col[t] >= q) return CGGM_EINVAL;
+    for (int64_t s = 0; s < nsuper; s++)
+        for (int64_t k = super_start[s]; k < super_start[s + 1]; k++) snode[k] = (int32_t)s;
+    const Adjacency a = symmetrise(q, row_ptr, col);
+    // child supernodes of each supernode (the supernode holding the parent of its last column)
+    std::vector<std::vector<int32_t>> kids(nsuper);
+    for (int64_t s = 0; s < nsuper; s++) {
+        const int32_t last = (int32_t)(super_start[s + 1] - 1);
+        if (parent[last] < -1 || parent[last] >= q || (parent[last] >= 0 && parent[last] <= last))
+            return CGGM_EINVAL;
+        if (parent[last] >= 0) kids[snode[parent[last]]].push_back((int32_t)s);
+    }
+    std::vector<int64_t> mark(q, -1);
+    std::vector<int32_t> rows;
+    for (int64_t s = 0; s < nsuper; s++) {
+        const int32_t f = (int32_t)super_start[s], l = (int32_t)super_start[s + 1];
+        rows.clear();
+        for (int32_t k = f; k < l; k++) {
+            rows.push_back(k);
+            mark[k] = s;
+        }
+        for (int32_t k = f; k < l; k++) {
+            const int32_t v = perm[k];
+            for (int64_t t = a.ptr[v]; t < a.ptr[v + 1]; t++) {
+                const int32_t r = iperm[a.adj[t]];
+                if (r >= l && mark[r] != s) {
+                    mark[r] = s;
+                    rows.push_back(r);
+                }
+            }
+        }
+        for (int32_t c : kids[s])
+            for (int64_t t = rows_ptr_out[c]; t < rows_ptr_out[c + 1]; t++) {
+                const int32_t r = rows_out[t];
+                if (r >= l && mark[r] != s) {
+                    mark[r] = s;
+                    rows.push_back(r);
+                }
+            }
+        if ((int64_t)rows.size() != rows_ptr_out[s + 1] - rows_ptr_out[s]) return CGGM_EINVAL;
+        std::sort(rows.begin(), rows.end());
+        std::copy(rows.begin(), rows.end(), rows_out + rows_ptr_out[s]);
+    }
+    return CGGM_OK;
+}

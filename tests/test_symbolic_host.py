@@ -224,3 +224,30 @@ def test_min_degree_order_matches_the_oracle(q, m, seed):
     perm, _, _, _ = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_MINDEG)
     ref = symbolic.minimum_degree_order(symbolic.pattern_from_csr(q, rp, ci))
     assert np.array_equal(perm, ref)
+
+
+@pytest.mark.parametrize("q,m,seed,order", [(1, 0, 24, 3), (30, 40, 25, 3), (80, 200, 26, 1),
+                                            (60, 900, 27, 0), (120, 300, 28, 3)])
+def test_supernode_rows_match_the_oracle(q, m, seed, order):
+    """The rows of supernode s are the pattern of its first column in the oracle's factor."""
+    rp, ci = random_csr(q, m, seed)
+    perm, parent, cc, _ = cg.chol_symbolic(q, rp, ci, order)
+    ss = cg.chol_supernodes(parent, cc)
+    rows_ptr, rows = cg.chol_structure(q, rp, ci, perm, parent, cc, ss)
+    L = symbolic.cholesky_pattern(symbolic.pattern_from_csr(q, rp, ci), perm)
+    assert rows_ptr[-1] == sum(cc[ss[:-1]])
+    for s in range(len(ss) - 1):
+        assert np.array_equal(rows[rows_ptr[s]:rows_ptr[s + 1]], np.flatnonzero(L[:, ss[s]]))
+
+
+def test_supernode_rows_reject_mismatched_inputs():
+    q = 20
+    rp, ci = random_csr(q, 30, 29)
+    perm, parent, cc, _ = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_MINDEG)
+    ss = cg.chol_supernodes(parent, cc)
+    bad = cc.copy()
+    bad[ss[0]] += 1 if bad[ss[0]] < q else -1
+    with pytest.raises(cg.CGGMError):
+        cg.chol_structure(q, rp, ci, perm, parent, bad, ss)
+    with pytest.raises(cg.CGGMError):
+        cg.chol_structure(q, rp, ci, perm, parent, cc, ss[::-1].copy())
