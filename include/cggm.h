@@ -275,6 +275,20 @@ int64_t cggm_footprint(int64_t n, int64_t p, int64_t q, int precision);
  * bad arguments.  The paper has no counterpart (its passes visit one coordinate at a time). */
 int cggm_tuned_batch(int64_t q, int64_t m, int precision);
 
+/* The tuner's table (the batch size chosen per size class) saved to and loaded from a text
+ * file, so that a deployment tunes a size class once and later processes start with the
+ * choice instead of timing their first iteration again.  The choices belong to the GPU
+ * model they were timed on.  Format: '#' comment lines, then "precision log2_q log2_m
+ * batch" per class (log2 rounded up, as cggm_tuned_batch rounds).  Host code.
+ *   cggm_tuner_save writes every class tuned so far; cggm_tuner_load merges a file's
+ *   classes into the table (replacing a class already present).  count_out (optional):
+ *   classes written or read.
+ * Errors: CGGM_EINVAL for a null path, a file that cannot be opened or written, or (load)
+ * a malformed line, an unknown precision or a batch size the precision does not allow;
+ * a load that fails merges nothing. */
+cggm_status cggm_tuner_save(const char *path, int64_t *count_out);
+cggm_status cggm_tuner_load(const char *path, int64_t *count_out);
+
 /* Dense contraction on the tensor cores, the form every product from X takes in the mixed
  * path (R = X Theta, P = R Sigma, Psi = P^T P / n, X^T (Y + P); Section 2.3 lists them):
  *     C = alpha A B^T + beta C,

@@ -22,6 +22,8 @@ from .cggm import (  # noqa: F401
     CGGM_I8_GENO,
     CGGM_SWEEP_BATCH_AUTO,
     tuned_batch,
+    tuner_save,
+    tuner_load,
     partition_columns,
     partition_theta_columns,
     chol_symbolic,

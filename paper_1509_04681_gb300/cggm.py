@@ -33,7 +33,8 @@ EXPORTED = [
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
     "cggm_partition_theta_columns", "cggm_chol_symbolic", "cggm_chol_supernodes",
-    "cggm_block_order", "cggm_permute_csr", "cggm_chol_structure",
+    "cggm_block_order", "cggm_permute_csr", "cggm_chol_structure", "cggm_tuner_save",
+    "cggm_tuner_load",
 ]
 
 
@@ -140,6 +141,8 @@ def _lib():
                                          ctypes.POINTER(i64)]
         lib.cggm_permute_csr.argtypes = [i64, vp, vp, vp, vp, vp, vp, vp]
         lib.cggm_chol_structure.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp, vp, vp]
+        lib.cggm_tuner_save.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
+        lib.cggm_tuner_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -156,6 +159,7 @@ def _lib():
                                                      "cggm_block_order",
                                                      "cggm_permute_csr",
                                                      "cggm_chol_structure",
+                                                     "cggm_tuner_save", "cggm_tuner_load",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -570,6 +574,20 @@ def chol_structure(q: int, row_ptr, col, perm, parent, colcount, super_start):
     rows = np.empty(int(rows_ptr[-1]), dtype=np.int32)
     _check(_lib().cggm_chol_structure(*args, rows.ctypes.data_as(vp)), "cggm_chol_structure")
     return rows_ptr, rows
+
+
+def tuner_save(path) -> int:
+    """Write the batch-size tuner's table to `path` (cggm_tuner_save); returns the classes."""
+    n = ctypes.c_int64()
+    _check(_lib().cggm_tuner_save(os.fsencode(path), ctypes.byref(n)), "cggm_tuner_save")
+    return int(n.value)
+
+
+def tuner_load(path) -> int:
+    """Merge a saved tuner table into this process's (cggm_tuner_load); returns the classes."""
+    n = ctypes.c_int64()
+    _check(_lib().cggm_tuner_load(os.fsencode(path), ctypes.byref(n)), "cggm_tuner_load")
+    return int(n.value)
 
 
 def make_opts(**kw) -> cggm_opts:

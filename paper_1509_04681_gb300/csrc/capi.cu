@@ -2,6 +2,7 @@
 // Algorithm 1, and the step-level entry points.  Host code only issues kernels; every
 // arithmetic step of the solve runs on the device.
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <vector>
@@ -1236,6 +1237,61 @@ cggm_status cggm_grad_lambda_block(cggm_ctx *c, const void *X, int xdtype, const
 int cggm_tuned_batch(int64_t q, int64_t m, int precision) {
     if (q < 1 || m < 0 || (precision != CGGM_FP64 && precision != CGGM_MIXED)) return -1;
     return tuned_lookup(precision, q, m);
+}
+
+// The tuner's table as text: a comment line, then one line per size class,
+// "precision log2_q log2_m batch".
+cggm_status cggm_tuner_save(const char *path, int64_t *count_out) {
+    if (!path) return CGGM_EINVAL;
+    std::vector<std::pair<std::tuple<int, int, int>, int>> rows;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        rows.assign(g_tuned.begin(), g_tuned.end());
+    }
+    FILE *f = std::fopen(path, "w");
+    if (!f) return CGGM_EINVAL;
+    bool ok = std::fprintf(f, "# cggm batch-size tuner table: precision log2_q log2_m batch\n") > 0;
+    for (const auto &r : rows)
+        ok = ok && std::fprintf(f, "%d %d %d %d\n", std::get<0>(r.first), std::get<1>(r.first),
+                                std::get<2>(r.first), r.second) > 0;
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return CGGM_EINVAL;
+    if (count_out) *count_out = (int64_t)rows.size();
+    return CGGM_OK;
+}
+
+cggm_status cggm_tuner_load(const char *path, int64_t *count_out) {
+    if (!path) return CGGM_EINVAL;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return CGGM_EINVAL;
+    std::vector<std::pair<std::tuple<int, int, int>, int>> rows;
+    char line[256];
+    bool ok = true;
+    while (ok && std::fgets(line, sizeof line, f)) {
+        const char *c = line;
+        while (*c == ' ' || *c == '\t') c++;
+        if (*c == '#' || *c == '\n' || *c == '\r' || *c == 0) continue;
+        int prec = -1, lq = -1, lm = -1, B = 0, used = 0;
+        if (std::sscanf(c, "%d %d %d %d %n", &prec, &lq, &lm, &B, &used) != 4 || c[used] != 0) {
+            ok = false;
+            break;
+        }
+        const bool batch_ok = B == 32 || B == 64 || B == 128 ||
+                              (prec == CGGM_MIXED && (B == 256 || B == 512));
+        if ((prec != CGGM_FP64 && prec != CGGM_MIXED) || lq < 0 || lq > 62 || lm < 0 ||
+            lm > 62 || !batch_ok)
+            ok = false;
+        else
+            rows.push_back({std::make_tuple(prec, lq, lm), B});
+    }
+    std::fclose(f);
+    if (!ok) return CGGM_EINVAL;  // nothing merged from a malformed file
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        for (const auto &r : rows) g_tuned[r.first] = r.second;
+    }
+    if (count_out) *count_out = (int64_t)rows.size();
+    return CGGM_OK;
 }
 
 cggm_status cggm_contract(cggm_ctx *c, int64_t M, int64_t N, int64_t K, float alpha,
