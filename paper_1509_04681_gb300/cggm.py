@@ -24,7 +24,8 @@ CGGM_ELINESEARCH, CGGM_ECUDA, CGGM_ETIMEDOUT, CGGM_ENONFINITE, CGGM_ECANCELLED =
 CGGM_FP64, CGGM_MIXED = 0, 1
 CGGM_F32, CGGM_F64, CGGM_BF16, CGGM_I8_GENO = 0, 1, 2, 3
 CGGM_SWEEP_BATCH_AUTO = -1
-CGGM_ORDER_NATURAL, CGGM_ORDER_RCM, CGGM_ORDER_GIVEN, CGGM_ORDER_MINDEG = 0, 1, 2, 3
+CGGM_ORDER_NATURAL, CGGM_ORDER_RCM, CGGM_ORDER_GIVEN, CGGM_ORDER_MINDEG, CGGM_ORDER_AMD = \
+    0, 1, 2, 3, 4
 
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",

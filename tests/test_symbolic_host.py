@@ -251,3 +251,48 @@ def test_supernode_rows_reject_mismatched_inputs():
         cg.chol_structure(q, rp, ci, perm, parent, bad, ss)
     with pytest.raises(cg.CGGMError):
         cg.chol_structure(q, rp, ci, perm, parent, cc, ss[::-1].copy())
+
+
+def chain_with_links(q, links, seed=9):
+    rng = np.random.default_rng(seed)
+    i = np.r_[np.arange(q - 1), rng.integers(0, q, links)]
+    j = np.r_[np.arange(1, q), rng.integers(0, q, links)]
+    A = sp.csr_matrix((np.ones(i.size), (i, j)), shape=(q, q))
+    return relabelled((A + A.T).tocsr(), 3)
+
+
+def test_approximate_degrees_against_the_exact_order():
+    """Approximate degrees bound the exact ones: the order is valid and its fill stays within
+    a few percent of the exact minimum-degree order's on the same patterns (chains with
+    links, a random network)."""
+    cases = [chain_with_links(20000, 200), chain_with_links(20000, 2000)]
+    rp, ci = random_csr(2000, 4000, 11)
+    cases.append(sp.csr_matrix((np.ones(ci.size), ci, rp), shape=(2000, 2000)))
+    for B in cases:
+        q = B.shape[0]
+        perm, parent, cc, nnz_a = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_AMD)
+        assert np.array_equal(np.sort(perm), np.arange(q))
+        assert np.all(parent[parent >= 0] > np.arange(q)[parent >= 0])
+        nnz_m = cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_MINDEG)[3]
+        assert nnz_a <= 1.05 * nnz_m
+
+
+def test_approximate_degrees_keep_a_forest_free_of_fill():
+    rng = np.random.default_rng(10)
+    q = 3000
+    parent = np.array([rng.integers(0, v) if v > 0 and v % 50 else -1 for v in range(q)])
+    child = np.flatnonzero(parent >= 0)
+    A = sp.csr_matrix((np.ones(child.size), (child, parent[child])), shape=(q, q))
+    B = relabelled((A + A.T).tocsr(), 4)
+    assert cg.chol_symbolic(q, B.indptr, B.indices, cg.CGGM_ORDER_AMD)[3] == q + child.size
+
+
+def test_approximate_degrees_at_the_block_regime_scale():
+    """q = 100000 outputs, a chain with 10000 random links: the analysis takes seconds at
+    most, where the exact order takes about 18 s."""
+    B = chain_with_links(100000, 10000)
+    t0 = time.perf_counter()
+    perm, parent, cc, nnz = cg.chol_symbolic(100000, B.indptr, B.indices, cg.CGGM_ORDER_AMD)
+    assert time.perf_counter() - t0 < 10.0
+    assert np.array_equal(np.sort(perm), np.arange(100000))
+    assert nnz == cc.sum()
