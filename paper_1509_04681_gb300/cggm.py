@@ -460,7 +460,7 @@ def partition_theta_columns(p: int, q: int, ti, tj, max_block: int):
     return block, int(k.value), int(rb.value)
 
 
-def chol_symbolic(q: int, row_ptr, col, ordering: int = CGGM_ORDER_MINDEG, perm=None):
+def chol_symbolic(q: int, row_ptr, col, ordering: int = CGGM_ORDER_AMD, perm=None):
     """Symbolic analysis of the sparse Cholesky factor of a q x q pattern in CSR
     (cggm_chol_symbolic).  Host memory only.  Returns (perm, parent, colcount, nnz_L):
     the pivot order (new -> old), the elimination tree of the permuted pattern, the
