@@ -69,3 +69,37 @@ def test_empty_list_and_errors():
         cg.block_order("theta", 3, [0], [3], [0, 0, 1])          # column out of range
     with pytest.raises(KeyError):
         cg.block_order("sigma", 3, [0], [1], [0, 0, 1])
+
+
+def test_block_regime_host_plan_end_to_end():
+    """The host pieces of the block regime in sequence on a random network of average degree
+    4 with 3000 outputs (the shape of the large workloads' Lambda): partition its graph,
+    order the active coordinates by block pairs, permute Lambda so every block is
+    contiguous, analyse the sparse factor and lay out its supernodes.  Each output is a
+    valid input of the next and the pieces agree on their sizes."""
+    import scipy.sparse as sp
+    q = 3000
+    Lam = synth.random_sparse_precision(q, 4.0, np.random.default_rng(30)).tocsr()
+    U = sp.triu(Lam).tocoo()
+    li, lj = U.row.astype(np.int32), U.col.astype(np.int32)
+    off = li != lj
+    block, k, cut = cg.partition_columns(q, li[off], lj[off], 256)
+    assert k >= -(-q // 256)
+    order, cols, miss = cg.block_order("lambda", q, li, lj, block)
+    assert np.array_equal(np.sort(order), np.arange(li.size)) and cols >= q
+    perm = np.argsort(block, kind="stable").astype(np.int32)
+    rp, ci, v = cg.permute_csr(q, Lam.indptr, Lam.indices, Lam.data, perm)
+    P = sp.csr_matrix((v, ci, rp), shape=(q, q))
+    assert np.array_equal(P.toarray(), Lam.toarray()[np.ix_(perm, perm)])
+    sizes = np.bincount(block)
+    starts = np.r_[0, np.cumsum(sizes)]
+    assert np.array_equal(np.sort(block)[starts[:-1]], np.arange(k))   # blocks contiguous
+    pv, parent, cc, nnz = cg.chol_symbolic(q, rp, ci, cg.CGGM_ORDER_AMD)
+    ss = cg.chol_supernodes(parent, cc)
+    rows_ptr, rows = cg.chol_structure(q, rp, ci, pv, parent, cc, ss)
+    assert ss[0] == 0 and ss[-1] == q and rows_ptr[-1] == cc[ss[:-1]].sum()
+    # every supernode's rows start with its own columns and stay inside the matrix
+    for s in range(len(ss) - 1):
+        r = rows[rows_ptr[s]:rows_ptr[s + 1]]
+        assert np.array_equal(r[:ss[s + 1] - ss[s]], np.arange(ss[s], ss[s + 1]))
+        assert r[-1] < q
