@@ -62,3 +62,27 @@ def test_reference_arm_other_ranks_do_nothing(monkeypatch, capsys):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(types.SimpleNamespace(steps=1, warmup=0, gpus=2))
     assert capsys.readouterr().out == ""
+
+
+def test_clock_summary_parses_nvidia_smi_lines(tmp_path):
+    """The clock record of the timed region: median SM clock, the maximum, and every
+    throttle reason seen active; malformed lines are skipped; the file is removed."""
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "clocks.csv")
+    with open(c.path, "w") as f:
+        f.write("0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 2050, 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("garbage line\n")
+        f.write("0, [N/A], 2070, 1.0, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+    s = c.summary()
+    assert s == {"sm_mhz": 2050.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                 "samples": 3}
+    assert not os.path.exists(c.path)
+
+
+def test_clock_summary_without_samples(tmp_path):
+    c = bench.Clocks(0)
+    c.path = str(tmp_path / "empty.csv")
+    open(c.path, "w").close()
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
