@@ -285,7 +285,7 @@ int cggm_tuned_batch(int64_t q, int64_t m, int precision);
  *   classes written or read.
  * Errors: CGGM_EINVAL for a null path, a file that cannot be opened or written, or (load)
  * a malformed line, an unknown precision or a batch size the precision does not allow;
- * a load that fails merges nothing. */
+ * a load that fails merges nothing.  The paper has no counterpart. */
 cggm_status cggm_tuner_save(const char *path, int64_t *count_out);
 cggm_status cggm_tuner_load(const char *path, int64_t *count_out);
 
