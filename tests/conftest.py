@@ -17,3 +17,11 @@ def pytest_collection_modifyitems(config, items):
     # A GPU test on a machine without a GPU is an error, not a skip: the CUDA path has
     # no fallback.  Deselection is done with -m "not gpu".
     pass
+
+
+@pytest.fixture(scope="session", autouse=True)
+def built_library():
+    """The compiled library every test calls, built once per session if a source is newer
+    (nothing is recompiled when it is up to date)."""
+    from paper_1509_04681_gb300 import build
+    build.build()
