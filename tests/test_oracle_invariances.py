@@ -65,3 +65,16 @@ def test_input_scaling_without_theta_penalty():
     assert abs(s.f - r.f) <= 1e-9 * abs(r.f)
     assert close(s.Lambda, r.Lambda)
     assert close(s.Theta, r.Theta / c[:, None])
+
+
+def test_warm_start_at_the_optimum_stops_at_once():
+    """Started from its own optimum, the method's stopping rule holds at the first check
+    (the minimum-norm subgradient is already below tol times the l1 norms), so the solve
+    returns that point with the same objective."""
+    X, Y = data(seed=45)
+    r = solve(X, Y)
+    w = oracle.solve(X, Y, 0.05, 0.05, tol=1e-6, max_iter=50, Lambda0=r.Lambda,
+                     Theta0=r.Theta)
+    assert w.converged and w.iterations == 1
+    assert np.array_equal(w.Lambda, r.Lambda) and np.array_equal(w.Theta, r.Theta)
+    assert abs(w.f - r.f) <= 1e-14 * abs(r.f)
