@@ -376,6 +376,18 @@ cggm_status cggm_partition_theta_columns(int64_t p, int64_t q, int64_t m, const 
                                          int32_t *block_out, int64_t *nblocks_out,
                                          int64_t *row_blocks_out);
 
+/* Number of blocks of Algorithm 2 for a memory budget, by Section 4's rule: the smallest k
+ * such that the columns a block holds fit in budget_bytes, values of bytes_per_value bytes.
+ *   kind 0 (Lambda, Section 4.1): a block holds 2q/k columns of Sigma and 2q/k of Psi, so
+ *   k is the least with 4 q ceil(q/k) bytes_per_value <= budget_bytes.
+ *   kind 1 (Theta, Section 4.2): q/k columns of Sigma, q ceil(q/k) bytes_per_value.
+ *   *k_out: the number of blocks; *max_block_out: ceil(q / k), the cap to give
+ *   cggm_partition_columns (blocks of equal size up to one fit the budget).  Host code.
+ * Errors: CGGM_EINVAL for another kind, a size below 1 or a null pointer; CGGM_ENOMEM when
+ * the budget does not hold a single block column. */
+cggm_status cggm_block_count(int kind, int64_t q, int64_t bytes_per_value, int64_t budget_bytes,
+                             int64_t *k_out, int64_t *max_block_out);
+
 /* Visiting order of the blocked coordinate passes of Algorithm 2 for a column partition
  * (one block id per column, ids 0..k-1, none empty), and the cache counts of Section 4.
  *   kind 0 (Lambda): (ci[t], cj[t]) with 0 <= ci <= cj < q; a coordinate belongs to the

@@ -35,7 +35,7 @@ EXPORTED = [
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
     "cggm_partition_theta_columns", "cggm_chol_symbolic", "cggm_chol_supernodes",
     "cggm_block_order", "cggm_permute_csr", "cggm_chol_structure", "cggm_tuner_save",
-    "cggm_tuner_load",
+    "cggm_tuner_load", "cggm_block_count",
 ]
 
 
@@ -144,6 +144,8 @@ def _lib():
         lib.cggm_chol_structure.argtypes = [i64, vp, vp, vp, vp, vp, i64, vp, vp, vp]
         lib.cggm_tuner_save.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
         lib.cggm_tuner_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
+        lib.cggm_block_count.argtypes = [ip, i64, i64, i64, ctypes.POINTER(i64),
+                                         ctypes.POINTER(i64)]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
@@ -161,6 +163,7 @@ def _lib():
                                                      "cggm_permute_csr",
                                                      "cggm_chol_structure",
                                                      "cggm_tuner_save", "cggm_tuner_load",
+                                                     "cggm_block_count",
                                                      "cggm_server_submit", "cggm_server_poll"):
                 f.restype = ctypes.c_int
         _LIB = lib
@@ -502,6 +505,17 @@ def chol_supernodes(parent, colcount):
                                        start.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ns)),
            "cggm_chol_supernodes")
     return start[:ns.value + 1].copy()
+
+
+def block_count(kind: str, q: int, bytes_per_value: int, budget_bytes: int):
+    """Blocks of Algorithm 2 for a memory budget by Section 4's rule (cggm_block_count);
+    kind "lambda" or "theta".  Returns (k, max_block)."""
+    k = ctypes.c_int64()
+    mb = ctypes.c_int64()
+    _check(_lib().cggm_block_count({"lambda": 0, "theta": 1}[kind], int(q), int(bytes_per_value),
+                                   int(budget_bytes), ctypes.byref(k), ctypes.byref(mb)),
+           "cggm_block_count")
+    return int(k.value), int(mb.value)
 
 
 def block_order(kind: str, q: int, ci, cj, block):

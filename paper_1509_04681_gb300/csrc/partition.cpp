@@ -597,3 +597,24 @@ extern "C" cggm_status cggm_block_order(int kind, int64_t q, int64_t m, const in
     if (misses_out) *misses_out = misses;
     return CGGM_OK;
 }
+
+// Section 4's rule for the number of blocks: the smallest k whose blocks' columns fit in the
+// budget.  Lambda (Section 4.1) holds 2q/k columns of Sigma and 2q/k of Psi, q entries each,
+// so 4 q ceil(q/k) entries; Theta (Section 4.2) holds q/k columns of Sigma, q ceil(q/k).
+extern "C" cggm_status cggm_block_count(int kind, int64_t q, int64_t bytes_per_value,
+                                        int64_t budget_bytes, int64_t *k_out,
+                                        int64_t *max_block_out)
+{
+    if ((kind != 0 && kind != 1) || q < 1 || bytes_per_value < 1 || budget_bytes < 1 ||
+        !k_out || !max_block_out)
+        return CGGM_EINVAL;
+    const int64_t factor = kind == 0 ? 4 : 1;  // held columns per block column
+    // entries one block column costs, q each; a budget below one column is too small
+    const double per_col = (double)factor * (double)q * (double)bytes_per_value;
+    const int64_t cols = (int64_t)std::floor((double)budget_bytes / per_col);
+    if (cols < 1) return CGGM_ENOMEM;
+    const int64_t max_block = std::min(cols, q);
+    *k_out = (q + max_block - 1) / max_block;
+    *max_block_out = (q + *k_out - 1) / *k_out;  // blocks of equal size up to one
+    return CGGM_OK;
+}

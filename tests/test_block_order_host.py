@@ -103,3 +103,22 @@ def test_block_regime_host_plan_end_to_end():
         r = rows[rows_ptr[s]:rows_ptr[s + 1]]
         assert np.array_equal(r[:ss[s + 1] - ss[s]], np.arange(ss[s], ss[s + 1]))
         assert r[-1] < q
+
+
+def test_block_count_rule():
+    """Section 4's rule: the least k whose block columns fit (Lambda holds 4 q ceil(q/k)
+    values, Theta q ceil(q/k))."""
+    q, b = 200000, 4
+    budget = 3_300_000_000                        # a few GB for the blocks
+    k, mb = cg.block_count("lambda", q, b, budget)
+    assert 4 * q * -(-q // k) * b <= budget           # k blocks fit ...
+    assert k == 1 or 4 * q * -(-q // (k - 1)) * b > budget   # ... and k - 1 would not
+    assert mb == -(-q // k)
+    k, mb = cg.block_count("theta", q, b, budget)
+    assert q * -(-q // k) * b <= budget and (k == 1 or q * -(-q // (k - 1)) * b > budget)
+    assert cg.block_count("lambda", 1000, 8, 10 ** 12) == (1, 1000)   # everything fits
+    with pytest.raises(cg.CGGMError) as e:
+        cg.block_count("lambda", 1000, 8, 4 * 1000 * 8 - 1)            # not one column
+    assert e.value.status == cg.CGGM_ENOMEM
+    with pytest.raises(cg.CGGMError):
+        cg.block_count("lambda", 0, 8, 10 ** 9)
