@@ -171,12 +171,41 @@ def job_rate(iters_per_rank, sec_max, world):
     return world * iters_per_rank / sec_max
 
 
+def pass_cost(run, m, budget_s, k0=1024):
+    """Seconds of one full oracle pass over m coordinates from a bounded sample.
+
+    The oracle's pass wrappers do work that does not grow with the number of coordinates
+    (array copies, zeroing the cache, the initial V = Theta Sigma of the Theta pass), so
+    the pass is timed with no coordinates (that fixed part, t0) and over a prefix of k
+    coordinates, k grown 4x at a time until the coordinate part t(k) - t0 is well above
+    the fixed part's noise or the budget is spent; only the slope (t(k) - t0) / k is
+    scaled to the full set: t_full = t0 + m (t(k) - t0) / k.
+    Returns (t_full, t0, k, t(k))."""
+    def timed(k):
+        ts = time.perf_counter()
+        run(k)
+        return time.perf_counter() - ts
+    t0 = timed(0)
+    spent = t0
+    k = min(m, k0)
+    while True:
+        tk = timed(k)
+        spent += tk
+        if k >= m:
+            return tk, t0, k, tk
+        resolved = tk - t0 >= max(0.5, 0.5 * t0)
+        if resolved or spent + 4 * tk > budget_s:
+            slope = max(0.0, tk - t0) / k
+            return t0 + slope * m, t0, k, tk
+        k = min(m, 4 * k)
+
+
 def cpu_oracle_rate(pr, budget_s=25.0):
     """Oracle Newton iterations per second on a bounded sample of the workload: the dense
-    steps of one iteration (covariances amortised out, Sigma, Psi, gradients, active sets)
-    once, and the two coordinate passes over the leading coordinates of their active
-    sets until the time budget is spent; per-coordinate costs are scaled to the full
-    active sets."""
+    steps of one iteration (covariances amortised out, Sigma, Psi, gradients, active sets,
+    objective) once, counted twice (the Armijo trial evaluates the objective again), and
+    each coordinate pass by pass_cost: its fixed part once plus its per-coordinate cost
+    (timed on a prefix of the active set) times the full active set."""
     import numpy as np
     import oracle
     t0 = time.perf_counter()
@@ -187,28 +216,14 @@ def cpu_oracle_rate(pr, budget_s=25.0):
     t1 = time.perf_counter()
     G_L, G_T, Sigma, Psi = oracle.gradients(Lam, Th, Sxx, Sxy, Syy)
     li, lj, ti, tj = oracle.active_sets(G_L, G_T, Lam, Th, pr.lam_L, pr.lam_T)
-    f0 = oracle.objective(Lam, Th, Sxx, Sxy, Syy, pr.lam_L, pr.lam_T)
+    oracle.objective(Lam, Th, Sxx, Sxy, Syy, pr.lam_L, pr.lam_T)
     t_dense = time.perf_counter() - t1
-    # coordinate passes on growing prefixes until the budget is used
-    per = {}
-    for name, (ii, jj) in (("lambda", (li, lj)), ("theta", (ti, tj))):
-        k = 256
-        spent = 0.0
-        while True:
-            ts = time.perf_counter()
-            if name == "lambda":
-                oracle.lambda_sweep(Sigma, Psi, Syy, Lam, ii[:k], jj[:k], pr.lam_L)
-            else:
-                oracle.theta_sweep(Sxx, Sxy, Sigma, Th, ii[:k], jj[:k], pr.lam_T)
-            dt = time.perf_counter() - ts
-            spent += dt
-            per[name] = (dt, k)
-            # next prefix is 4x longer; stop before it would overrun this pass's share
-            if spent + 4 * dt > budget_s / 3 or k >= len(ii):
-                break
-            k = min(len(ii), k * 4)
-    t_iter = t_dense * 2 + per["lambda"][0] / per["lambda"][1] * len(li) + \
-        per["theta"][0] / per["theta"][1] * len(ti)
+    left = max(2.0, budget_s - t_dense)
+    tl = pass_cost(lambda k: oracle.lambda_sweep(Sigma, Psi, Syy, Lam, li[:k], lj[:k], pr.lam_L),
+                   len(li), left / 2)
+    tt = pass_cost(lambda k: oracle.theta_sweep(Sxx, Sxy, Sigma, Th, ti[:k], tj[:k], pr.lam_T),
+                   len(ti), left / 2)
+    t_iter = 2 * t_dense + tl[0] + tt[0]
     try:
         from threadpoolctl import threadpool_info
         cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
@@ -217,11 +232,14 @@ def cpu_oracle_rate(pr, budget_s=25.0):
     return {"value": 1.0 / t_iter, "unit": "Newton iterations/s", "cores": cores,
             "kind": "oracle",
             "sample": (f"{WORKLOAD} iteration 0: dense steps (Sigma, Psi, gradients, "
-                       f"objective, active sets) timed once and counted twice (the Armijo "
-                       f"objective), Lambda pass over the first {per['lambda'][1]} of "
-                       f"{len(li)} coordinates, Theta pass over the first {per['theta'][1]} "
-                       f"of {len(ti)}, scaled to the full active sets; coordinate passes "
-                       f"single-threaded C, dense steps numpy BLAS"),
+                       f"objective, active sets) timed once ({t_dense:.2f} s) and counted twice "
+                       f"(the Armijo objective); each coordinate pass timed with no coordinates "
+                       f"(its fixed part: Lambda {tl[1]:.2f} s, Theta {tt[1]:.2f} s) and over a "
+                       f"prefix (Lambda {tl[2]} of {len(li)} coordinates in {tl[3]:.2f} s, "
+                       f"Theta {tt[2]} of {len(ti)} in {tt[3]:.2f} s), fixed part counted once "
+                       f"and the per-coordinate slope scaled to the full active set; "
+                       f"coordinate passes single-threaded C, dense steps numpy BLAS"),
+            "seconds_per_iteration": t_iter,
             "seconds_measured": round(time.perf_counter() - t0, 2)}
 
 
@@ -245,12 +263,14 @@ def run_reference(args):
     import synth
     pr = synth.workload(WORKLOAD)
     rates = []
-    budget = max(5.0, 150.0 / max(1, args.steps + args.warmup))
+    budget = max(8.0, 180.0 / max(1, args.steps + args.warmup))
+    t_run = time.perf_counter()
     for k in range(args.warmup + args.steps):
         r = cpu_oracle_rate(pr, budget_s=budget)
         if k >= args.warmup:
             rates.append(r)
     v = statistics.median([r["value"] for r in rates])
+    wall = time.perf_counter() - t_run
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "Newton iterations/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
@@ -259,6 +279,12 @@ def run_reference(args):
             "cpu_baseline": {"kind": "oracle", "cores": rates[0]["cores"],
                              "sample": rates[0]["sample"], "value": v,
                              "unit": "Newton iterations/s"},
+            "timing": {"extrapolated": True,
+                       "note": "each step times a bounded sample of one oracle Newton "
+                               "iteration (dense steps, each pass's fixed part, a prefix of "
+                               "each pass); ms_per_step is the whole iteration it implies",
+                       "sample_wall_s_per_step": wall / max(1, args.warmup + args.steps),
+                       "wall_s": wall},
             "e2e": {"value": v, "unit": "Newton iterations/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -375,6 +401,133 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def pass_rooflines(info, p, q, mixed, step_sec):
+    """Roofline objects of the two coordinate passes over a timed solve: algorithmic bytes
+    (10 q words per Lambda coordinate: the dots Sigma_i.U_j, Psi_i.U_j, Psi_j.U_i and the
+    updates of U_i, U_j; (2 p + 3 q) words per Theta coordinate: (S_xx)_i . Delta V_j and
+    the update of Delta V_i with Sigma_j) over each pass's event-timed seconds."""
+    esz = 4 if mixed else 8
+    iters = max(1, info["iterations"])
+    hbm, src = peaks()
+    out = []
+    for kname, units, per, ksec in (
+            ("lambda_sweep_kernel", info["coords_lambda"], 10 * q,
+             info["sec_sweep_lambda"]),
+            ("theta_sweep_kernel", info["coords_theta"], 2 * p + 3 * q,
+             info["sec_sweep_theta"])):
+        kbytes = units * per * esz
+        achieved = kbytes / ksec / 1e9 if ksec > 0 else 0.0
+        per_unit = (f"10 q x {esz} B per Lambda coordinate" if kname.startswith("lambda")
+                    else f"(2 p + 3 q) x {esz} B per Theta coordinate")
+        out.append({"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                    "unit": "GB/s", "frac": achieved / hbm,
+                    "traffic": profiled_traffic(kname, units / iters),  # per launch
+                    "peak_source": src, "algorithmic_bytes": per_unit,
+                    "launch_seconds": ksec / iters, "share_of_step": ksec / step_sec})
+    return out[0], out[1]
+
+
+def fp64_leg(ctx, cg, Xd, Yd, pr, p, q, dev, steps, warmup):
+    """Newton iterations/s of the double-precision path on the same workload: W iterations
+    from Lambda = I, Theta = 0, then K timed ones (CUDA events on the context's stream)."""
+    import torch
+    L0 = torch.empty((q, q), device=dev, dtype=torch.float64)
+    T0 = torch.empty((p, q), device=dev, dtype=torch.float64)
+    ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
+                   opts=cg.make_opts(precision=cg.CGGM_FP64, max_iter=warmup),
+                   Lambda_out=L0, Theta_out=T0)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    res = ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=L0, warm_Theta=T0,
+                         opts=cg.make_opts(precision=cg.CGGM_FP64, max_iter=steps),
+                         Lambda_out=L0, Theta_out=T0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sec = ev0.elapsed_time(ev1) / 1e3
+    info = res.info
+    it = max(1, info["iterations"])
+    rl, rt = pass_rooflines(info, p, q, False, sec)
+    return {"value": info["iterations"] / sec, "unit": "Newton iterations/s",
+            "steps": info["iterations"], "warmup": warmup, "ms_per_step": 1e3 * sec / it,
+            "dtype": "f64",
+            "per_iteration": {k: info[k] / it for k in ("sec_products", "sec_sweep_lambda",
+                                                          "sec_linesearch", "sec_sweep_theta")},
+            "roofline_lambda_pass": rl, "roofline_theta_pass": rt,
+            "gpu_launches": info["launches"]}
+
+
+def run_gap_trace(args):
+    """Objective against device time for both precisions on the 5000 x 5000 workload: each
+    path runs from Lambda = I, Theta = 0 in chunks of Newton iterations (warm-started from
+    the previous chunk in device memory) until its time budget is spent; after each chunk
+    f(Lambda, Theta) is evaluated in double precision (cggm_objective, not timed).  f_best
+    is the lowest f seen by either path; the gap of an iterate is (f - f_best) / |f_best|
+    (f* <= f_best, so true gaps are at least these).  Also the paper's stopping quantity
+    (the min-norm subgradient ratio of Section 5.1) at each chunk's last iteration."""
+    import numpy as np
+    import torch
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    import synth
+    pr = synth.workload(WORKLOAD)
+    n, p = pr.X.shape
+    q = pr.Y.shape[1]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    Xd = torch.from_numpy(pr.X_raw).to(dev)
+    Yd = torch.from_numpy(pr.Y.astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cg.Context(0, stream=stream.cuda_stream)
+    traces = {}
+    for name, prec in (("fp64", cg.CGGM_FP64), ("mixed", cg.CGGM_MIXED)):
+        L = torch.empty((q, q), device=dev, dtype=torch.float64)
+        T = torch.empty((p, q), device=dev, dtype=torch.float64)
+        t_dev, its, first = 0.0, 0, True
+        rows = []
+        with Clocks(0) as clk:
+            while t_dev < args.gap_trace:
+                kw = {} if first else {"warm_Lambda": L, "warm_Theta": T}
+                r = ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
+                                   opts=cg.make_opts(precision=prec, max_iter=args.gap_chunk),
+                                   Lambda_out=L, Theta_out=T, **kw)
+                first = False
+                t_dev += r.info["seconds"]
+                its += r.info["iterations"]
+                f = ctx.cggm_objective(Xd, Yd, L, T, pr.lam_L, pr.lam_T)
+                rows.append({"seconds": t_dev, "iterations": its, "f": f,
+                             "subgrad_ratio": r.info["subgrad"] / max(1e-300, r.info["l1norm"]),
+                             "m_lambda": r.info["m_lambda"], "m_theta": r.info["m_theta"]})
+                print(json.dumps({"trace": name, **rows[-1]}), flush=True)
+                if r.status == cg.CGGM_OK:
+                    break
+        traces[name] = {"rows": rows, "clocks": clk.summary()}
+    ctx.close()
+    f_best = min(r["f"] for t in traces.values() for r in t["rows"])
+    out = {"gap_trace": {"workload": WORKLOAD, "p": p, "q": q, "n": n, "lambda": pr.lam_L,
+                         "budget_s_per_path": args.gap_trace, "chunk": args.gap_chunk,
+                         "f_best": f_best}}
+    for name, t in traces.items():
+        rows = t["rows"]
+        reach = {}
+        for g in (1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+            hit = [r for r in rows if (r["f"] - f_best) / abs(f_best) <= g]
+            reach[f"{g:g}"] = ({"seconds": hit[0]["seconds"], "iterations": hit[0]["iterations"]}
+                               if hit else None)
+        stop = [r for r in rows if r["subgrad_ratio"] < 0.01]
+        out["gap_trace"][name] = {
+            "seconds": rows[-1]["seconds"], "iterations": rows[-1]["iterations"],
+            "f_last": rows[-1]["f"], "gap_last": (rows[-1]["f"] - f_best) / abs(f_best),
+            "subgrad_ratio_last": rows[-1]["subgrad_ratio"], "time_to_gap": reach,
+            "time_to_paper_stop_0.01": ({"seconds": stop[0]["seconds"],
+                                          "iterations": stop[0]["iterations"]} if stop else None),
+            "clocks": t["clocks"], "trace": rows}
+    print(json.dumps(out), flush=True)
+
+
 def run_cuda(args):
     import numpy as np
     import torch
@@ -427,24 +580,10 @@ def run_cuda(args):
     value = job_rate(iters, sec_max, world)
     clocks = clk.summary()
 
-    # roofline of the dominant kernel: the coordinate pass with the larger time
-    esz = 4 if prec == cg.CGGM_MIXED else 8
-    lam_bytes = info["coords_lambda"] * 10 * q * esz
-    th_bytes = info["coords_theta"] * (2 * p + 3 * q) * esz
-    hbm, src = peaks()
-    if info["sec_sweep_lambda"] >= info["sec_sweep_theta"]:
-        kname, kbytes, ksec = "lambda_sweep_kernel", lam_bytes, info["sec_sweep_lambda"]
-        per_unit = f"10 q x {esz} B per Lambda coordinate"
-    else:
-        kname, kbytes, ksec = "theta_sweep_kernel", th_bytes, info["sec_sweep_theta"]
-        per_unit = f"(2 p + 3 q) x {esz} B per Theta coordinate"
-    achieved = kbytes / ksec / 1e9 if ksec > 0 else 0.0
-    units = info["coords_lambda" if kname == "lambda_sweep_kernel" else "coords_theta"]
-    traffic = profiled_traffic(kname, units / max(1, iters))  # per launch (one per iteration)
-    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-            "peak_source": src, "algorithmic_bytes": per_unit,
-            "launch_seconds": ksec / max(1, iters), "share_of_step": ksec / sec}
+    # roofline of the dominant kernel (the coordinate pass with the larger time) and of the
+    # other pass beside it
+    rl, rt = pass_rooflines(info, p, q, prec == cg.CGGM_MIXED, sec)
+    roof, roof_other = (rl, rt) if info["sec_sweep_lambda"] >= info["sec_sweep_theta"] else (rt, rl)
 
     line = {"metric": METRIC, "value": value, "unit": "Newton iterations/s",
             "n_gpus": world, "steps": iters, "warmup": args.warmup,
@@ -458,7 +597,8 @@ def run_cuda(args):
                        "network": "chain (1.0 / 0.4)", "theta_nnz_per_col": 10,
                        "seed": 0, "l2": "working set (Sigma, Psi, U, S_xx, Delta V: "
                        "~100 MB each) larger than L2; no flush"},
-            "roofline": roof, "clocks": clocks, "gpu_launches": info["launches"],
+            "roofline": roof, "roofline_other_pass": roof_other, "clocks": clocks,
+            "gpu_launches": info["launches"],
             "per_iteration": {"active_lambda_last": info["m_lambda"],
                               "active_theta_last": info["m_theta"],
                               "sec_products": info["sec_products"] / max(1, iters),
@@ -493,6 +633,9 @@ def run_cuda(args):
                        "h2d_bytes_per_step": int(h2d / max(1, it2)),
                        "d2h_bytes_per_step": int((Lo.numel() + To.numel()) * 8 / max(1, it2))}
 
+    if rank == 0 and world == 1 and not args.no_fp64:
+        line["fp64"] = fp64_leg(ctx, cg, Xd, Yd, pr, p, q, dev, min(args.steps, 5), 3)
+        line["mixed_over_fp64_iterations_per_s"] = value / line["fp64"]["value"]
     if rank == 0 and world == 1 and not args.no_ttg:
         small = synth.workload(SMALL)
         line["time_to_gap"] = time_to_gap(ctx, cg, small, torch)
@@ -516,6 +659,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--gap-trace", type=float, default=0.0,
+                    help="seconds of device time per precision: record f against time on the "
+                         "5000 x 5000 workload instead of the default line")
+    ap.add_argument("--gap-chunk", type=int, default=10)
     ap.add_argument("--serve", action="store_true",
                     help="served lambda paths (Poisson arrivals) instead of the default line")
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -532,6 +680,8 @@ def main():
         run_profile_sweep(args)
     elif args.profile_contract:
         run_profile_contract(args)
+    elif args.gap_trace > 0:
+        run_gap_trace(args)
     elif args.serve:
         run_serve(args)
     elif args.impl == "reference":

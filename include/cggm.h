@@ -505,13 +505,15 @@ cggm_status cggm_chol_supernodes(int64_t q, const int32_t *parent, const int64_t
  *    CGGM_EINVAL without touching the GPU.
  *  - Every pointer must be device memory of the current device (CGGM_EINVAL otherwise):
  *    Sigma, Psi, Syy, Lambda (q x q double), ai, aj (m int32, ai <= aj, visiting order),
- *    D_out (q x q double, overwritten).  The indices are not checked (that would take
- *    the device-to-host copy and synchronisation this entry point avoids): the caller
- *    guarantees 0 <= ai <= aj < q, as cggm_active_sets produces them; cggm_lambda_sweep
- *    checks them.  The call runs on cuda_stream (a cudaStream_t;
- *    NULL = the legacy default stream) and returns after the pass has finished.
+ *    D_out (q x q double, overwritten).  The index pairs are checked on the device before
+ *    the pass reads them: a pair outside 0 <= ai <= aj < q returns CGGM_EINVAL (D_out is
+ *    then zero).  The call runs on cuda_stream (a cudaStream_t; NULL = the legacy default
+ *    stream) and returns after the pass has finished and D_out is written (also for
+ *    m = 0, where D_out is set to zero).
  *  - The first call on a device looks up the device address of the array (once per
  *    device, with that device current); make that first call before any stream capture.
+ *    The address is kept for the life of the process: do not use this entry point on a
+ *    device after cudaDeviceReset has been called on it.
  *  - All calls share the one array and it keeps the last call's contents (the call
  *    clears what must start at zero).  Calls that overlap on the GPU - from two host
  *    threads or on two streams - race on it; serialise them.

@@ -42,7 +42,7 @@ struct Status {
 
 inline unsigned ceil_div(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
-// Number of SMs of the current device (cached per process; one device per context).
+// Number of SMs of the current device (looked up once per device).
 int sm_count();
 
 // Host-side count of kernel launches issued by this library (all contexts, process-wide);

@@ -1,6 +1,8 @@
 // SIMT dense kernels: tiled GEMM (double or float), maps and deterministic reductions.
 #include "dense.cuh"
 
+#include <mutex>
+
 namespace cggm {
 
 int64_t &launch_counter() {
@@ -9,14 +11,30 @@ int64_t &launch_counter() {
 }
 
 int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+    // cached per device (contexts on different devices may share the process)
+    constexpr int kMaxDev = 64;
+    static int counts[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
     }
-    return n;
+    if (dev < 0 || dev >= kMaxDev) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        return n > 0 ? n : 1;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (counts[dev] == 0) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
+        counts[dev] = n > 0 ? n : 1;
+    }
+    return counts[dev];
 }
 
 // ---------------------------------------------------------------------------------

@@ -54,6 +54,20 @@ cggm_status scratch_base(int dev, unsigned char **out) {
     return CGGM_OK;
 }
 
+// Every active coordinate must satisfy 0 <= ai <= aj < q: the pass indexes its q x q
+// matrices with them unchecked.  A bad pair sets the status word.
+__global__ void check_pairs_kernel(int64_t m, const int32_t *__restrict__ ai,
+                                   const int32_t *__restrict__ aj, int64_t q, int *err) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = ai[k], b = aj[k];
+        if (a < 0 || a > b || b >= q) {
+            atomicCAS(err, 0, (int)DEV_BADINDEX);
+            return;
+        }
+    }
+}
+
 bool on_device(const void *p, int dev) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
@@ -101,6 +115,20 @@ extern "C" cggm_status cggm_lambda_sweep_noalloc(int64_t q, const double *Sigma,
     // and the diagonals are rewritten in full below.
     const size_t qq = (size_t)q * q;
     CGGM_CUDA_TRY(cudaMemsetAsync(D_out, 0, 8 * qq, st));
+    if (m == 0) {  // the direction is zero; return once it has been written
+        CGGM_CUDA_TRY(cudaStreamSynchronize(st));
+        return CGGM_OK;
+    }
+    // the coordinate list is checked on the device before the pass reads it
+    int bad = 0;
+    CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
+    note_launch();
+    check_pairs_kernel<<<(unsigned)((m + 255) / 256 < 64 ? (m + 255) / 256 : 64), 256, 0, st>>>(
+        m, ai, aj, q, scr.err);
+    CGGM_CUDA_TRY(cudaGetLastError());
+    CGGM_CUDA_TRY(cudaMemcpyAsync(&bad, scr.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CGGM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (bad != 0) return CGGM_EINVAL;
     CGGM_CUDA_TRY(cudaMemsetAsync(U, 0, 8 * qq, st));
     grad_lambda<double>(q, Syy, Sigma, Psi, G, st);
     diag_to_double<double>(q, Sigma, Sd, st);

@@ -1042,6 +1042,7 @@ cggm_status read_err(int *err, cudaStream_t st) {
     CGGM_CUDA_TRY(cudaStreamSynchronize(st));
     if (h == DEV_TIMEOUT) return CGGM_ETIMEDOUT;
     if (h == DEV_NONFINITE) return CGGM_ENONFINITE;
+    if (h == DEV_BADINDEX) return CGGM_EINVAL;
     if (h != 0) return CGGM_ECUDA;
     return CGGM_OK;
 }

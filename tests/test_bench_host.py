@@ -7,7 +7,29 @@ import shutil
 import bench
 
 
-def test_traffic_scales_with_coordinates():
+def _tree_with_fresh_capture(tmp_path, monkeypatch):
+    """A copy of the kernel sources and of the committed Lambda-pass summary whose recorded
+    source hash is set to the copy's: the host logic is checked on a capture that is
+    current by construction (the committed one goes stale whenever the kernel changes)."""
+    import hashlib
+    root = tmp_path / "tree"
+    for rel in bench.SWEEP_SOURCES + ["profiles/lambda_sweep_kernel-q5000-bounded.md"]:
+        dst = root / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, rel), dst)
+    h = hashlib.sha256()
+    for rel in bench.SWEEP_SOURCES:
+        h.update((root / rel).read_bytes())
+    prof = root / "profiles/lambda_sweep_kernel-q5000-bounded.md"
+    lines = [("    source_sha256: " + h.hexdigest()) if l.strip().startswith("source_sha256:")
+             else l for l in prof.read_text().splitlines()]
+    prof.write_text("\n".join(lines) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(root))
+    return root
+
+
+def test_traffic_scales_with_coordinates(tmp_path, monkeypatch):
+    _tree_with_fresh_capture(tmp_path, monkeypatch)
     t1 = bench.profiled_traffic("lambda_sweep_kernel", 1_000_000)
     t2 = bench.profiled_traffic("lambda_sweep_kernel", 2_000_000)
     assert t1 is not None and t1 > 0
@@ -17,18 +39,29 @@ def test_traffic_scales_with_coordinates():
 
 
 def test_traffic_is_null_for_other_kernels_and_changed_sources(tmp_path, monkeypatch):
-    assert bench.profiled_traffic("theta_sweep_kernel", 1000) is None  # no capture committed
-    # a copy of the tree whose kernel source differs by one byte: the capture no longer applies
-    root = tmp_path / "tree"
-    for rel in bench.SWEEP_SOURCES + ["profiles/lambda_sweep_kernel-q5000-bounded.md"]:
-        dst = root / rel
-        dst.parent.mkdir(parents=True, exist_ok=True)
-        shutil.copy(os.path.join(bench.ROOT, rel), dst)
-    monkeypatch.setattr(bench, "ROOT", str(root))
+    root = _tree_with_fresh_capture(tmp_path, monkeypatch)
+    assert bench.profiled_traffic("theta_sweep_kernel", 1000) is None  # no capture there
     assert bench.profiled_traffic("lambda_sweep_kernel", 1000) is not None
+    # a kernel source that differs by one byte: the capture no longer applies
     src = root / bench.SWEEP_SOURCES[0]
     src.write_bytes(src.read_bytes() + b" ")
     assert bench.profiled_traffic("lambda_sweep_kernel", 1000) is None
+
+
+def test_pass_cost_counts_the_fixed_part_once():
+    """A pass costing 0.3 s fixed plus 1 us per coordinate, sampled on a prefix, is
+    extrapolated to 0.3 + 1e-6 m, not scaled as a whole."""
+    import time as _t
+    calls = []
+
+    def run(k):
+        calls.append(k)
+        _t.sleep(0.3 + 1e-6 * k)
+
+    m = 10_000_000
+    t_full, t0, k, tk = bench.pass_cost(run, m, budget_s=3.0, k0=65536)
+    assert calls[0] == 0 and 0.29 <= t0 <= 0.45
+    assert abs(t_full - (0.3 + 1e-6 * m)) <= 0.25 * (0.3 + 1e-6 * m)
 
 
 def test_reference_arm_prints_the_contract_line(monkeypatch, capsys):

@@ -72,6 +72,52 @@ def test_noalloc_lambda_pass_matches_allocating_entry_point():
             np.testing.assert_array_equal(D, D.T)
 
 
+def test_noalloc_at_its_maximum_size_and_empty_active_set():
+    """q = CGGM_NOALLOC_MAX_Q with a near-full active set (the largest scratch layout), then
+    m = 0 on a stream that the default stream does not wait for: the call must have written
+    the zero direction before it returns."""
+    lib = cg.cggm._lib()
+    torch.cuda.set_device(0)
+    q = 256
+    Sigma, Psi, Syy, Lam = spd_inputs(q, 3)
+    iu, ju = np.triu_indices(q)
+    keep = np.random.default_rng(3).uniform(size=iu.size) < 0.9
+    li, lj = iu[keep].astype(np.int32), ju[keep].astype(np.int32)
+    with cg.Context(0) as ctx:
+        st, D = call_noalloc(lib, Sigma, Psi, Syy, Lam, li, lj, 0.01)
+        assert st == 0
+        D_ref = ctx.cggm_lambda_sweep(Sigma, Psi, Syy, Lam, li, lj, 0.01, precision=cg.CGGM_FP64)
+        assert np.abs(D - D_ref).max() <= 1e-9 * max(1e-300, np.abs(D_ref).max())
+    dev = torch.device("cuda", 0)
+    t = [torch.tensor(a, device=dev) for a in (Sigma, Psi, Syy, Lam)]
+    D0 = torch.full((q, q), float("nan"), device=dev, dtype=torch.float64)
+    side = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    st = lib.cggm_lambda_sweep_noalloc(q, *[x.data_ptr() for x in t], 0, None, None, 0.01, 1,
+                                       D0.data_ptr(), ctypes.c_void_p(side.cuda_stream))
+    assert st == 0
+    out = np.empty((q, q))
+    # a plain copy, ordered after nothing on `side`: the call itself must have finished
+    host = D0.to("cpu", non_blocking=False)
+    out[:] = host.numpy()
+    assert np.all(out == 0.0)
+
+
+def test_noalloc_rejects_index_pairs_outside_the_matrix():
+    lib = cg.cggm._lib()
+    torch.cuda.set_device(0)
+    q = 64
+    Sigma, Psi, Syy, Lam = spd_inputs(q, 4)
+    for li, lj in ([[0, 3], [1, 64]], [[0, 5], [1, 4]], [[-1, 0], [2, 2]]):
+        st, _ = call_noalloc(lib, Sigma, Psi, Syy, Lam, np.array(li, np.int32),
+                             np.array(lj, np.int32), 0.01)
+        assert st == cg.CGGM_EINVAL, (li, lj, st)
+    # the entry point still works after a refused call
+    li, lj = active(q, 8, 4)
+    st, D = call_noalloc(lib, Sigma, Psi, Syy, Lam, li, lj, 0.01)
+    assert st == 0 and np.all(np.isfinite(D))
+
+
 def test_noalloc_rejects_sizes_beyond_its_maximum():
     lib = cg.cggm._lib()
     q = 257  # CGGM_NOALLOC_MAX_Q + 1
