@@ -293,13 +293,13 @@ def run_reference(args):
 def time_to_gap(ctx, cg, pr, torch):
     """Seconds (device time of the solve) to reach (f - f*)/|f*| <= 1e-6, f* from the
     double-precision path run until progress stops."""
-    ref = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
+    ref = ctx.cggm_solve_dense(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
                          opts=cg.make_opts(precision=cg.CGGM_FP64, max_iter=4000))
     fstar = ctx.cggm_objective(pr.X, pr.Y, ref.Lambda, ref.Theta, pr.lam_L, pr.lam_T)
     target = fstar + 1e-6 * abs(fstar)
     out = {"workload": SMALL, "f_star": fstar}
     for name, prec in (("mixed", cg.CGGM_MIXED), ("fp64", cg.CGGM_FP64)):
-        r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
+        r = ctx.cggm_solve_dense(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
                            opts=cg.make_opts(precision=prec, max_iter=4000, target_f=target))
         f = ctx.cggm_objective(pr.X, pr.Y, r.Lambda, r.Theta, pr.lam_L, pr.lam_T)
         out[name] = {"seconds": r.info["seconds"], "iterations": r.info["iterations"],
@@ -433,7 +433,7 @@ def fp64_leg(ctx, cg, Xd, Yd, pr, p, q, dev, steps, warmup):
     import torch
     L0 = torch.empty((q, q), device=dev, dtype=torch.float64)
     T0 = torch.empty((p, q), device=dev, dtype=torch.float64)
-    ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
+    ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
                    opts=cg.make_opts(precision=cg.CGGM_FP64, max_iter=warmup),
                    Lambda_out=L0, Theta_out=T0)
     stream = torch.cuda.current_stream(dev)
@@ -441,7 +441,7 @@ def fp64_leg(ctx, cg, Xd, Yd, pr, p, q, dev, steps, warmup):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    res = ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=L0, warm_Theta=T0,
+    res = ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=L0, warm_Theta=T0,
                          opts=cg.make_opts(precision=cg.CGGM_FP64, max_iter=steps),
                          Lambda_out=L0, Theta_out=T0)
     ev1.record(stream)
@@ -491,7 +491,7 @@ def run_gap_trace(args):
         with Clocks(0) as clk:
             while t_dev < args.gap_trace:
                 kw = {} if first else {"warm_Lambda": L, "warm_Theta": T}
-                r = ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
+                r = ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
                                    opts=cg.make_opts(precision=prec, max_iter=args.gap_chunk),
                                    Lambda_out=L, Theta_out=T, **kw)
                 first = False
@@ -555,7 +555,7 @@ def run_cuda(args):
     T1 = torch.empty_like(T0)
 
     # warm-up: W Newton iterations from Lambda = I, Theta = 0
-    ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
+    ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
                    opts=cg.make_opts(precision=prec, max_iter=args.warmup),
                    Lambda_out=L0, Theta_out=T0)
     torch.cuda.synchronize()
@@ -565,7 +565,7 @@ def run_cuda(args):
     ev1 = torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
-        res = ctx.cggm_solve(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=L0,
+        res = ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=L0,
                              warm_Theta=T0,
                              opts=cg.make_opts(precision=prec, max_iter=args.steps),
                              Lambda_out=L1, Theta_out=T1)
@@ -621,7 +621,7 @@ def run_cuda(args):
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
-        r2 = ctx.cggm_solve(Xh, Yh, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=Lh,
+        r2 = ctx.cggm_solve_dense(Xh, Yh, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=Lh,
                             warm_Theta=Th_, Lambda_out=Lo, Theta_out=To,
                             opts=cg.make_opts(precision=prec, max_iter=args.steps))
         torch.cuda.synchronize()

@@ -117,6 +117,16 @@ void cggm_opts_default(cggm_opts *opts);
 /* Short English name of a status code (static storage). */
 const char *cggm_status_string(int status);
 
+/* A sparse matrix as a coordinate list: entry e is (row[e], col[e], val[e]), 0 <= e < nnz.
+ * The paper keeps Lambda and Theta in sparse form (Section 5); Lambda, being symmetric, is
+ * exchanged as its upper triangle (row <= col), Theta in full. */
+typedef struct {
+    int64_t nnz;
+    int32_t *row;
+    int32_t *col;
+    double *val;
+} cggm_coo;
+
 /*
  * Solve Eq. 1 by alternating Newton coordinate descent (Algorithm 1): Theta <- 0,
  * Lambda <- I (or the warm start); each iteration computes Sigma = Lambda^-1 by Cholesky,
@@ -124,18 +134,45 @@ const char *cggm_status_string(int status);
  * coordinate-descent pass for the Newton direction of Lambda (Section 3.1, Eq. 7), an
  * Armijo step on Lambda, and one coordinate-descent pass on Theta (Section 3.2, Eq. 8).
  *
- * X: n x p, dtype xdtype; Y: n x q, dtype ydtype.  lam_L, lam_T >= 0.  tol > 0 overrides
- * opts->tol.  warm_Lambda (q x q, symmetric positive definite) and warm_Theta (p x q)
- * are double, may be NULL (then I and 0).  Lambda_out (q x q) and Theta_out (p x q)
- * receive the solution in double.  info may be NULL.  opts may be NULL (defaults).
+ * X: n x p, dtype xdtype; Y: n x q, dtype ydtype (host or device).  lam_L, lam_T >= 0.
+ * tol > 0 overrides opts->tol.  info may be NULL.  opts may be NULL (defaults).
+ * Parameters are exchanged sparse:
+ *  - warm_Lambda: the upper triangle (row <= col) of a symmetric positive definite q x q
+ *    start, warm_Theta: the entries of a p x q start; either may be NULL (then I and 0).
+ *    Their arrays may be host or device memory and stay the caller's; repeated entries
+ *    add up.  An index outside the matrix (or row > col for Lambda) gives CGGM_EINVAL, a
+ *    non-finite value CGGM_ENONFINITE, a warm Lambda that is not positive definite
+ *    CGGM_ENOTPD.
+ *  - Lambda_out (upper triangle) and Theta_out receive the nonzero entries of the solution
+ *    in row-major order, exact zeros dropped, in arrays the library allocates in host
+ *    memory; release them with cggm_free_coo.  Either may be NULL.  On an error return
+ *    they are left empty (nnz 0, NULL arrays).
  * Returns CGGM_OK when the stopping rule held, CGGM_EMAXITER when max_iter ran out (the
  * outputs then hold the last iterate), or an error.
  */
 cggm_status cggm_solve(cggm_ctx *ctx, const void *X, int xdtype, const void *Y, int ydtype,
                        int64_t n, int64_t p, int64_t q, double lam_L, double lam_T,
-                       double tol, const double *warm_Lambda, const double *warm_Theta,
-                       const cggm_opts *opts, double *Lambda_out, double *Theta_out,
+                       double tol, const cggm_coo *warm_Lambda, const cggm_coo *warm_Theta,
+                       const cggm_opts *opts, cggm_coo *Lambda_out, cggm_coo *Theta_out,
                        cggm_info *info);
+
+/* Release the arrays of a coordinate list returned by cggm_solve and empty it.  NULL, and
+ * an already empty list, are ignored. */
+void cggm_free_coo(cggm_coo *coo);
+
+/*
+ * cggm_solve with dense parameters, for callers that keep Lambda and Theta as dense
+ * matrices (for instance in device memory between calls, as the regularisation-path
+ * server does).  warm_Lambda (q x q, symmetric positive definite) and warm_Theta (p x q)
+ * are double, host or device, and may be NULL (then I and 0).  Lambda_out (q x q) and
+ * Theta_out (p x q) receive the solution in double, host or device.  Everything else as
+ * for cggm_solve.
+ */
+cggm_status cggm_solve_dense(cggm_ctx *ctx, const void *X, int xdtype, const void *Y,
+                             int ydtype, int64_t n, int64_t p, int64_t q, double lam_L,
+                             double lam_T, double tol, const double *warm_Lambda,
+                             const double *warm_Theta, const cggm_opts *opts,
+                             double *Lambda_out, double *Theta_out, cggm_info *info);
 
 /*
  * f(Lambda, Theta) of Eq. 1 in double precision on the device.  Lambda must be positive

@@ -29,6 +29,7 @@ CGGM_ORDER_NATURAL, CGGM_ORDER_RCM, CGGM_ORDER_GIVEN, CGGM_ORDER_MINDEG, CGGM_OR
 
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
+    "cggm_solve_dense", "cggm_free_coo",
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
@@ -60,6 +61,11 @@ class cggm_info(ctypes.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cggm_coo(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int64), ("row", ctypes.POINTER(ctypes.c_int32)),
+                ("col", ctypes.POINTER(ctypes.c_int32)), ("val", ctypes.POINTER(ctypes.c_double))]
 
 
 class cggm_request(ctypes.Structure):
@@ -104,8 +110,15 @@ def _lib():
         lib.cggm_opts_default.restype = None
         lib.cggm_status_string.argtypes = [ip]
         lib.cggm_status_string.restype = ctypes.c_char_p
-        lib.cggm_solve.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, dbl, dbl, dbl, vp, vp,
-                                   ctypes.POINTER(cggm_opts), vp, vp, ctypes.POINTER(cggm_info)]
+        coo_p = ctypes.POINTER(cggm_coo)
+        lib.cggm_solve.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, dbl, dbl, dbl, coo_p,
+                                   coo_p, ctypes.POINTER(cggm_opts), coo_p, coo_p,
+                                   ctypes.POINTER(cggm_info)]
+        lib.cggm_solve_dense.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, dbl, dbl, dbl, vp,
+                                         vp, ctypes.POINTER(cggm_opts), vp, vp,
+                                         ctypes.POINTER(cggm_info)]
+        lib.cggm_free_coo.argtypes = [coo_p]
+        lib.cggm_free_coo.restype = None
         lib.cggm_objective.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, dbl, dbl, ip,
                                        ctypes.POINTER(dbl)]
         lib.cggm_grad.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, vp, vp]
@@ -148,7 +161,8 @@ def _lib():
                                          ctypes.POINTER(i64)]
         for name in EXPORTED:
             f = getattr(lib, name)
-            if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve", "cggm_objective",
+            if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve",
+                                                     "cggm_solve_dense", "cggm_objective",
                                                      "cggm_grad", "cggm_cholesky",
                                                      "cggm_lambda_sweep", "cggm_theta_sweep",
                                                      "cggm_active_sets",
@@ -225,6 +239,61 @@ class SolveResult:
     Theta: object
     info: dict
     status: int
+    Lambda_coo: object = None  # (row, col, val) of cggm_solve: upper triangle of Lambda
+    Theta_coo: object = None   # (row, col, val): the nonzero entries of Theta
+
+
+class _CooIn:
+    """A caller's sparse parameter as a cggm_coo over arrays kept alive here.  Accepts a
+    (row, col, val) triple or a dense matrix (host numpy or torch), whose nonzero entries
+    (only row <= col when `upper`) are listed."""
+
+    def __init__(self, a, upper):
+        if isinstance(a, tuple) and len(a) == 3:
+            r, c, v = a
+        else:
+            try:
+                import torch
+                if isinstance(a, torch.Tensor):
+                    a = a.detach().cpu().numpy()
+            except ImportError:
+                pass
+            d = np.asarray(a, dtype=np.float64)
+            if upper:
+                d = np.triu(d)
+            r, c = np.nonzero(d)
+            v = d[r, c]
+        self.r = np.ascontiguousarray(r, dtype=np.int32)
+        self.c = np.ascontiguousarray(c, dtype=np.int32)
+        self.v = np.ascontiguousarray(v, dtype=np.float64)
+        if not (self.r.shape == self.c.shape == self.v.shape) or self.r.ndim != 1:
+            raise ValueError("row, col and val must be 1-D arrays of one length")
+        self.coo = cggm_coo(nnz=self.r.size,
+                            row=self.r.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                            col=self.c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                            val=self.v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+def _coo_take(coo: cggm_coo):
+    """Copy a library-allocated coordinate list into numpy arrays and release it."""
+    k = int(coo.nnz)
+    try:
+        r = np.ctypeslib.as_array(coo.row, shape=(k,)).copy() if k else np.zeros(0, np.int32)
+        c = np.ctypeslib.as_array(coo.col, shape=(k,)).copy() if k else np.zeros(0, np.int32)
+        v = np.ctypeslib.as_array(coo.val, shape=(k,)).copy() if k else np.zeros(0)
+    finally:
+        _lib().cggm_free_coo(ctypes.byref(coo))
+    return r, c, v
+
+
+def coo_to_dense(coo, shape, symmetric=False):
+    """A dense numpy matrix holding the listed entries (both triangles when `symmetric`)."""
+    r, c, v = coo
+    A = np.zeros(shape)
+    A[r, c] = v
+    if symmetric:
+        A[c, r] = v
+    return A
 
 
 class Context:
@@ -255,8 +324,36 @@ class Context:
 
     # -- cggm_solve --------------------------------------------------------------------
     def cggm_solve(self, X, Y, lam_L, lam_T, tol=0.0, warm_Lambda=None, warm_Theta=None,
-                   opts: Optional[cggm_opts] = None, Lambda_out=None, Theta_out=None,
-                   allow_maxiter=True) -> SolveResult:
+                   opts: Optional[cggm_opts] = None, allow_maxiter=True) -> SolveResult:
+        """cggm_solve: sparse exchange of the parameters.  warm_Lambda / warm_Theta: a
+        (row, col, val) triple (Lambda: its upper triangle) or a dense host matrix whose
+        nonzero entries are passed.  The result carries the returned coordinate lists
+        (Lambda_coo, Theta_coo) and, for convenience, dense numpy copies of them."""
+        n, p = X.shape
+        q = Y.shape[1]
+        xd, xt = _x_dtype(X)
+        yd, yt = _x_dtype(Y)
+        Xa, Ya = _Arr(X, xd), _Arr(Y, yd)
+        wl = _CooIn(warm_Lambda, True) if warm_Lambda is not None else None
+        wt = _CooIn(warm_Theta, False) if warm_Theta is not None else None
+        outL, outT = cggm_coo(), cggm_coo()
+        info = cggm_info()
+        o = opts if opts is not None else opts_default()
+        st = _lib().cggm_solve(self._h, Xa.ptr, xt, Ya.ptr, yt, n, p, q, float(lam_L),
+                               float(lam_T), float(tol),
+                               ctypes.byref(wl.coo) if wl else None,
+                               ctypes.byref(wt.coo) if wt else None, ctypes.byref(o),
+                               ctypes.byref(outL), ctypes.byref(outT), ctypes.byref(info))
+        Lc, Tc = _coo_take(outL), _coo_take(outT)
+        _check(st, "cggm_solve", (CGGM_OK, CGGM_EMAXITER) if allow_maxiter else (CGGM_OK,))
+        return SolveResult(Lambda=coo_to_dense(Lc, (q, q), symmetric=True),
+                           Theta=coo_to_dense(Tc, (p, q)), info=info.as_dict(), status=st,
+                           Lambda_coo=Lc, Theta_coo=Tc)
+
+    def cggm_solve_dense(self, X, Y, lam_L, lam_T, tol=0.0, warm_Lambda=None, warm_Theta=None,
+                         opts: Optional[cggm_opts] = None, Lambda_out=None, Theta_out=None,
+                         allow_maxiter=True) -> SolveResult:
+        """cggm_solve_dense: dense parameters, host or device (torch CUDA tensors)."""
         n, p = X.shape
         q = Y.shape[1]
         xd, xt = _x_dtype(X)
@@ -269,11 +366,12 @@ class Context:
         La, Ta = _Arr(Lo, np.float64), _Arr(To, np.float64)
         info = cggm_info()
         o = opts if opts is not None else opts_default()
-        st = _lib().cggm_solve(self._h, Xa.ptr, xt, Ya.ptr, yt, n, p, q, float(lam_L),
-                               float(lam_T), float(tol), wl.ptr if wl else None,
-                               wt.ptr if wt else None, ctypes.byref(o), La.ptr, Ta.ptr,
-                               ctypes.byref(info))
-        _check(st, "cggm_solve", (CGGM_OK, CGGM_EMAXITER) if allow_maxiter else (CGGM_OK,))
+        st = _lib().cggm_solve_dense(self._h, Xa.ptr, xt, Ya.ptr, yt, n, p, q, float(lam_L),
+                                     float(lam_T), float(tol), wl.ptr if wl else None,
+                                     wt.ptr if wt else None, ctypes.byref(o), La.ptr, Ta.ptr,
+                                     ctypes.byref(info))
+        _check(st, "cggm_solve_dense",
+               (CGGM_OK, CGGM_EMAXITER) if allow_maxiter else (CGGM_OK,))
         return SolveResult(Lambda=La.obj if Lambda_out is None else Lambda_out,
                            Theta=Ta.obj if Theta_out is None else Theta_out,
                            info=info.as_dict(), status=st)

@@ -9,6 +9,7 @@
 
 #include "cg.cuh"
 #include "chol.cuh"
+#include "coo.cuh"
 
 #include <map>
 #include <mutex>
@@ -113,6 +114,8 @@ struct cggm_ctx {
     // mixed path: float operands of the tensor-core products and their TF32 hi/lo splits
     Buf Xt_hi, Xt_lo, Sig_hi, Sig_lo, R_f, R_hi, R_lo, Pt_f, Pt_hi, Pt_lo, Zf, tcerr;
     Buf partial;
+    // sparse exchange at the boundary (cggm_solve): the caller's coordinate lists
+    Buf coo_r, coo_c, coo_v;
     SweepScratch scr;
     cudaEvent_t ev[8];
     bool events = false;
@@ -232,6 +235,9 @@ struct Solver {
     cudaStream_t st;
     double lamL, lamT, lamLd;  // lamLd: penalty on the diagonal
     cggm_opts o;
+    // the starting Lambda / Theta were already written into c->Lam / c->Th (sparse warm
+    // starts); otherwise run() starts from its warm-start pointers or from I and 0
+    bool lam_ready = false, th_ready = false;
 
     double *scal() { return P<double>(c->scal); }
 
@@ -470,13 +476,13 @@ struct Solver {
         // initial point (Algorithm 1: Theta <- 0, Lambda <- I, or the warm start)
         if (warmL) {
             CGGM_TRY(load_double(c, warmL, qq, c->Lam));
-        } else {
+        } else if (!lam_ready) {
             note_launch();
             set_identity<<<gcap(q * q), 256, 0, st>>>(q, P<double>(c->Lam));
         }
         if (warmT) {
             CGGM_TRY(load_double(c, warmT, pq, c->Th));
-        } else {
+        } else if (!th_ready) {
             CGGM_CUDA_TRY(cudaMemsetAsync(c->Th.p, 0, 8 * pq, st));
         }
         CGGM_CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), st));
@@ -716,6 +722,125 @@ cggm_status set_device(cggm_ctx *c) {
     return CGGM_OK;
 }
 
+// A caller's coordinate list (host or device arrays) into the dense device matrix dst
+// (rows x cols), which it overwrites; `sym`: one triangle (row <= col) of a symmetric
+// matrix.  Bad indices give CGGM_EINVAL, non-finite values CGGM_ENONFINITE.
+cggm_status coo_in(cggm_ctx *c, const cggm_coo *a, int64_t rows, int64_t cols, bool sym,
+                   double *dst) {
+    const int64_t nnz = a->nnz;
+    if (nnz < 0 || nnz > rows * cols || (nnz > 0 && (!a->row || !a->col || !a->val)))
+        return CGGM_EINVAL;
+    cudaStream_t st = c->st;
+    CGGM_CUDA_TRY(cudaMemsetAsync(dst, 0, 8 * (size_t)rows * cols, st));
+    if (nnz == 0) return CGGM_OK;
+    CGGM_TRY(ensure(c->coo_r, 4 * (size_t)nnz));
+    CGGM_TRY(ensure(c->coo_c, 4 * (size_t)nnz));
+    CGGM_TRY(ensure(c->coo_v, 8 * (size_t)nnz));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->coo_r.p, a->row, 4 * (size_t)nnz, cudaMemcpyDefault, st));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->coo_c.p, a->col, 4 * (size_t)nnz, cudaMemcpyDefault, st));
+    CGGM_CUDA_TRY(cudaMemcpyAsync(c->coo_v.p, a->val, 8 * (size_t)nnz, cudaMemcpyDefault, st));
+    CGGM_CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), st));
+    coo_scatter(nnz, P<int32_t>(c->coo_r), P<int32_t>(c->coo_c), P<double>(c->coo_v), rows,
+                cols, sym, dst, P<int>(c->err), st);
+    CGGM_CUDA_TRY(cudaGetLastError());
+    int h = 0;
+    CGGM_TRY(read_dev_err(c, &h));
+    if (h == DEV_NONFINITE) return CGGM_ENONFINITE;
+    if (h != 0) return CGGM_EINVAL;
+    return CGGM_OK;
+}
+
+// The nonzero entries of the dense device matrix A (rows x cols; with `upper` only j >= i)
+// as a coordinate list in row-major order, in arrays allocated on the host with malloc
+// (released by cggm_free_coo).  ii, jj: index scratch of the size of the list's worst
+// case; vv: value scratch as large.
+cggm_status coo_out(cggm_ctx *c, const double *A, int64_t rows, int64_t cols, bool upper,
+                    Buf &ii, Buf &jj, Buf &vv, cggm_coo *out) {
+    cudaStream_t st = c->st;
+    int64_t *cnt = P<int64_t>(c->cnt) + 2;
+    active_compact(rows, cols, A, A, INFINITY, INFINITY, upper, P<int64_t>(c->rowcnt),
+                   P<int32_t>(ii), P<int32_t>(jj), cnt, st);
+    int64_t nnz = 0;
+    CGGM_CUDA_TRY(cudaMemcpyAsync(&nnz, cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    CGGM_TRY(sync_err(c));
+    coo_gather(nnz, P<int32_t>(ii), P<int32_t>(jj), A, cols, P<double>(vv), st);
+    const size_t k = nnz > 0 ? (size_t)nnz : 1;
+    int32_t *r = (int32_t *)malloc(4 * k), *cl = (int32_t *)malloc(4 * k);
+    double *v = (double *)malloc(8 * k);
+    if (!r || !cl || !v) {
+        free(r); free(cl); free(v);
+        return CGGM_ENOMEM;
+    }
+    cudaError_t e = cudaSuccess;
+    if (nnz > 0) {
+        e = cudaMemcpyAsync(r, ii.p, 4 * (size_t)nnz, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cl, jj.p, 4 * (size_t)nnz, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(v, vv.p, 8 * (size_t)nnz, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free(r); free(cl); free(v);
+        return CGGM_ECUDA;
+    }
+    out->nnz = nnz;
+    out->row = r;
+    out->col = cl;
+    out->val = v;
+    return CGGM_OK;
+}
+
+template <typename T>
+cggm_status solve_t(cggm_ctx *c, Sizes z, double lamL, double lamT, double lamLd,
+                    const cggm_opts &o, const double *wL, const double *wT, const cggm_coo *cL,
+                    const cggm_coo *cT, cggm_info *info, bool *conv) {
+    Solver<T> S{c, z, c->st, lamL, lamT, lamLd, o};
+    CGGM_TRY(S.alloc());
+    if (cL) {
+        CGGM_TRY(coo_in(c, cL, z.q, z.q, true, P<double>(c->Lam)));
+        S.lam_ready = true;
+    }
+    if (cT) {
+        CGGM_TRY(coo_in(c, cT, z.p, z.q, false, P<double>(c->Th)));
+        S.th_ready = true;
+    }
+    int iters = 0;
+    return S.run(wL, wT, info, &iters, conv);
+}
+
+// Argument checks, input upload and the solve of cggm_solve and cggm_solve_dense; the
+// result is left in c->Lam and c->Th.  Warm starts: dense (wL, wT) or sparse (cL, cT).
+cggm_status solve_common(cggm_ctx *c, const void *X, int xdtype, const void *Y, int ydtype,
+                         int64_t n, int64_t p, int64_t q, double lam_L, double lam_T,
+                         double tol, const double *wL, const double *wT, const cggm_coo *cL,
+                         const cggm_coo *cT, const cggm_opts *opts, cggm_info *info,
+                         bool *conv) {
+    if (!c || !X || !Y) return CGGM_EINVAL;
+    CGGM_TRY(check_sizes(n, p, q));
+    if (!(lam_L >= 0.0) || !(lam_T >= 0.0)) return CGGM_EINVAL;
+    if (!dtypes_ok(xdtype, ydtype)) return CGGM_EINVAL;
+    cggm_opts o;
+    if (opts) o = *opts; else cggm_opts_default(&o);
+    if (tol > 0.0) o.tol = tol;
+    if (!(o.tol > 0.0) || o.max_iter < 0 || o.ls_max_trials < 1 || !(o.ls_beta > 0.0 && o.ls_beta < 1.0))
+        return CGGM_EINVAL;
+    if (o.sweep_batch != 0 && o.sweep_batch != CGGM_SWEEP_BATCH_AUTO && o.sweep_batch != 32 &&
+        o.sweep_batch != 64 && o.sweep_batch != 128 &&
+        !((o.sweep_batch == 256 || o.sweep_batch == 512) && o.precision == CGGM_MIXED))
+        return CGGM_EINVAL;
+    if (o.precision != CGGM_FP64 && o.precision != CGGM_MIXED) return CGGM_EINVAL;
+    if (info) memset(info, 0, sizeof(*info));
+    CGGM_TRY(set_device(c));
+    CGGM_TRY(ensure(c->err, sizeof(int)));
+    CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
+    CGGM_TRY(load_transposed(c, Y, ydtype, n, q, c->Yt, nullptr));
+    const double lamLd = o.penalize_diag ? lam_L : 0.0;
+    const Sizes z{n, p, q};
+    if (o.precision == CGGM_FP64)
+        return solve_t<double>(c, z, lam_L, lam_T, lamLd, o, wL, wT, cL, cT, info, conv);
+    return solve_t<float>(c, z, lam_L, lam_T, lamLd, o, wL, wT, cL, cT, info, conv);
+}
+
 }  // namespace
 
 extern "C" {
@@ -790,7 +915,7 @@ void cggm_destroy(cggm_ctx *c) {
                    &c->tj, &c->rowcnt, &c->scal, &c->cnt, &c->err, &c->partial, &c->colstats, &c->cg_rp, &c->cg_ci, &c->cg_v, &c->cg_b, &c->cg_x, &c->cg_w, &c->bk_th, &c->bk_rt, &c->bk_pt, &c->bk_sig, &c->bk_psi, &c->bk_g,
                    &c->tcA_hi, &c->tcA_lo, &c->tcB_hi, &c->tcB_lo, &c->Xt_hi, &c->Xt_lo,
                    &c->Sig_hi, &c->Sig_lo, &c->R_f, &c->R_hi, &c->R_lo, &c->Pt_f, &c->Pt_hi,
-                   &c->Pt_lo, &c->Zf, &c->tcerr};
+                   &c->Pt_lo, &c->Zf, &c->tcerr, &c->coo_r, &c->coo_c, &c->coo_v};
     for (Buf *b : bufs) if (b->p) cudaFree(b->p);
     scratch_free(c->scr);
     if (c->events) for (int i = 0; i < 8; i++) cudaEventDestroy(c->ev[i]);
@@ -798,46 +923,55 @@ void cggm_destroy(cggm_ctx *c) {
     delete c;
 }
 
-cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, int ydtype,
-                       int64_t n, int64_t p, int64_t q, double lam_L, double lam_T, double tol,
-                       const double *warm_Lambda, const double *warm_Theta, const cggm_opts *opts,
-                       double *Lambda_out, double *Theta_out, cggm_info *info) {
-    if (!c || !X || !Y) return CGGM_EINVAL;
-    CGGM_TRY(check_sizes(n, p, q));
-    if (!(lam_L >= 0.0) || !(lam_T >= 0.0)) return CGGM_EINVAL;
-    if (!dtypes_ok(xdtype, ydtype)) return CGGM_EINVAL;
-    cggm_opts o;
-    if (opts) o = *opts; else cggm_opts_default(&o);
-    if (tol > 0.0) o.tol = tol;
-    if (!(o.tol > 0.0) || o.max_iter < 0 || o.ls_max_trials < 1 || !(o.ls_beta > 0.0 && o.ls_beta < 1.0))
-        return CGGM_EINVAL;
-    if (o.sweep_batch != 0 && o.sweep_batch != CGGM_SWEEP_BATCH_AUTO && o.sweep_batch != 32 &&
-        o.sweep_batch != 64 && o.sweep_batch != 128 &&
-        !((o.sweep_batch == 256 || o.sweep_batch == 512) && o.precision == CGGM_MIXED))
-        return CGGM_EINVAL;
-    if (info) memset(info, 0, sizeof(*info));
+cggm_status cggm_solve_dense(cggm_ctx *c, const void *X, int xdtype, const void *Y,
+                             int ydtype, int64_t n, int64_t p, int64_t q, double lam_L,
+                             double lam_T, double tol, const double *warm_Lambda,
+                             const double *warm_Theta, const cggm_opts *opts,
+                             double *Lambda_out, double *Theta_out, cggm_info *info) {
     const int64_t launches0 = launch_counter();
-    CGGM_TRY(set_device(c));
-    CGGM_TRY(ensure(c->err, sizeof(int)));
-    CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
-    CGGM_TRY(load_transposed(c, Y, ydtype, n, q, c->Yt, nullptr));
-    int iters = 0;
     bool conv = false;
-    cggm_status s;
-    const double lamLd = o.penalize_diag ? lam_L : 0.0;
-    if (o.precision == CGGM_FP64) {
-        Solver<double> S{c, {n, p, q}, c->st, lam_L, lam_T, lamLd, o};
-        s = S.run(warm_Lambda, warm_Theta, info, &iters, &conv);
-    } else if (o.precision == CGGM_MIXED) {
-        Solver<float> S{c, {n, p, q}, c->st, lam_L, lam_T, lamLd, o};
-        s = S.run(warm_Lambda, warm_Theta, info, &iters, &conv);
-    } else {
-        return CGGM_EINVAL;
-    }
-    if (s != CGGM_OK) return s;
+    CGGM_TRY(solve_common(c, X, xdtype, Y, ydtype, n, p, q, lam_L, lam_T, tol, warm_Lambda,
+                          warm_Theta, nullptr, nullptr, opts, info, &conv));
     if (Lambda_out) CGGM_TRY(store_double(c, Lambda_out, c->Lam.p, (size_t)q * q));
     if (Theta_out) CGGM_TRY(store_double(c, Theta_out, c->Th.p, (size_t)p * q));
     CGGM_CUDA_TRY(cudaStreamSynchronize(c->st));
+    if (info) info->launches = launch_counter() - launches0;
+    return conv ? CGGM_OK : CGGM_EMAXITER;
+}
+
+void cggm_free_coo(cggm_coo *a) {
+    if (!a) return;
+    free(a->row);
+    free(a->col);
+    free(a->val);
+    a->nnz = 0;
+    a->row = nullptr;
+    a->col = nullptr;
+    a->val = nullptr;
+}
+
+cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, int ydtype,
+                       int64_t n, int64_t p, int64_t q, double lam_L, double lam_T, double tol,
+                       const cggm_coo *warm_Lambda, const cggm_coo *warm_Theta,
+                       const cggm_opts *opts, cggm_coo *Lambda_out, cggm_coo *Theta_out,
+                       cggm_info *info) {
+    const cggm_coo empty = {0, nullptr, nullptr, nullptr};
+    if (Lambda_out) *Lambda_out = empty;
+    if (Theta_out) *Theta_out = empty;
+    const int64_t launches0 = launch_counter();
+    bool conv = false;
+    CGGM_TRY(solve_common(c, X, xdtype, Y, ydtype, n, p, q, lam_L, lam_T, tol, nullptr,
+                          nullptr, warm_Lambda, warm_Theta, opts, info, &conv));
+    if (Lambda_out)
+        CGGM_TRY(coo_out(c, P<double>(c->Lam), q, q, true, c->li, c->lj, c->GL, Lambda_out));
+    if (Theta_out) {
+        const cggm_status s = coo_out(c, P<double>(c->Th), p, q, false, c->ti, c->tj, c->GT,
+                                      Theta_out);
+        if (s != CGGM_OK) {
+            cggm_free_coo(Lambda_out);
+            return s;
+        }
+    }
     if (info) info->launches = launch_counter() - launches0;
     return conv ? CGGM_OK : CGGM_EMAXITER;
 }

@@ -3,7 +3,7 @@
 // budget; admitted requests run concurrently, each on its own context and stream, so their
 // kernels overlap on the GPU; each request solves its lambda points in order, every solve
 // warm-started from the previous one with Lambda and Theta kept in device memory.  Host
-// code only; every arithmetic step runs in the library's kernels (cggm_solve).
+// code only; every arithmetic step runs in the library's kernels (cggm_solve_dense).
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -108,7 +108,7 @@ cggm_server::Outcome cggm_server::run(const Job *j, cggm_ctx *ctx) {
     for (size_t k = 0; k < j->lambdas.size() && st == CGGM_OK; k++) {
         const double lam = j->lambdas[k];
         cggm_info info;
-        const cggm_status s = cggm_solve(ctx, dX, r.xdtype, dY, r.ydtype, n, p, q, lam, lam, r.tol,
+        const cggm_status s = cggm_solve_dense(ctx, dX, r.xdtype, dY, r.ydtype, n, p, q, lam, lam, r.tol,
                                          k ? dL : nullptr, k ? dT : nullptr, &o, dL, dT, &info);
         if (s != CGGM_OK && s != CGGM_EMAXITER) {
             st = s;

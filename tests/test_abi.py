@@ -84,3 +84,33 @@ def test_no_cpu_fallback_in_the_package():
             src = open(os.path.join(pkg_dir, f)).read()
             assert "oracle" not in src, f
             assert "np.linalg" not in src and "scipy" not in src, f
+
+
+def test_free_coo_accepts_null_and_empty_lists(lib):
+    """cggm_free_coo is host code: NULL and an empty list are ignored, no GPU needed."""
+    import paper_1509_04681_gb300 as cg
+    lib.cggm_free_coo.argtypes = [ctypes.POINTER(cg.cggm_coo)]
+    lib.cggm_free_coo.restype = None
+    lib.cggm_free_coo(None)
+    e = cg.cggm_coo()
+    lib.cggm_free_coo(ctypes.byref(e))
+    assert e.nnz == 0 and not e.row and not e.col and not e.val
+
+
+def test_binding_lists_the_nonzeros_of_dense_warm_starts():
+    """The binding's marshalling of a dense warm start into a coordinate list: Lambda by
+    its upper triangle, Theta in full, row-major, zeros left out; and back."""
+    import numpy as np
+    import paper_1509_04681_gb300.cggm as m
+    L = np.array([[2.0, 0.5, 0.0], [0.5, 3.0, -1.0], [0.0, -1.0, 4.0]])
+    c = m._CooIn(L, upper=True)
+    assert c.coo.nnz == 5
+    assert list(zip(c.r, c.c, c.v)) == [(0, 0, 2.0), (0, 1, 0.5), (1, 1, 3.0), (1, 2, -1.0),
+                                        (2, 2, 4.0)]
+    np.testing.assert_array_equal(m.coo_to_dense((c.r, c.c, c.v), (3, 3), symmetric=True), L)
+    T = np.array([[0.0, 1.5], [-2.0, 0.0]])
+    t = m._CooIn(T, upper=False)
+    assert list(zip(t.r, t.c, t.v)) == [(0, 1, 1.5), (1, 0, -2.0)]
+    np.testing.assert_array_equal(m.coo_to_dense((t.r, t.c, t.v), (2, 2)), T)
+    trip = m._CooIn((np.array([1]), np.array([0]), np.array([7.0])), upper=False)
+    assert trip.coo.nnz == 1 and trip.v[0] == 7.0
