@@ -78,6 +78,9 @@ typedef struct {
                             CGGM_SWEEP_BATCH_AUTO = chosen by the tuner (cggm_tuned_batch) */
     double target_f;     /* also stop once f <= target_f (time-to-gap runs); -inf = off  */
     int verbose;         /* per-iteration line on stderr                                  */
+    int64_t sxx_rows;    /* rows of S_xx = X^T X / n held at once by the Theta pass, formed
+                            from X chunk by chunk; 0 = as many as fit in 256 MiB (all p
+                            rows, formed once per solve, when they fit)                    */
 } cggm_opts;
 
 typedef struct {

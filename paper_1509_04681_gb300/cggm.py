@@ -45,7 +45,7 @@ class cggm_opts(ctypes.Structure):
                 ("ls_sigma", ctypes.c_double), ("ls_beta", ctypes.c_double),
                 ("ls_max_trials", ctypes.c_int), ("penalize_diag", ctypes.c_int),
                 ("sweep_batch", ctypes.c_int), ("target_f", ctypes.c_double),
-                ("verbose", ctypes.c_int)]
+                ("verbose", ctypes.c_int), ("sxx_rows", ctypes.c_int64)]
 
 
 class cggm_info(ctypes.Structure):

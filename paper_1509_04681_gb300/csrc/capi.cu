@@ -238,6 +238,11 @@ struct Solver {
     // the starting Lambda / Theta were already written into c->Lam / c->Th (sparse warm
     // starts); otherwise run() starts from its warm-start pointers or from I and 0
     bool lam_ready = false, th_ready = false;
+    // rows of S_xx held at once (all p when they fit in kSxxChunkBytes: then S_xx is formed
+    // once per solve), and the host copy of the Theta active list's row offsets, by which
+    // the Theta pass is cut into chunks of rows otherwise
+    int64_t sxx_rows = 0;
+    std::vector<int64_t> th_rowoff;
 
     double *scal() { return P<double>(c->scal); }
 
@@ -246,7 +251,9 @@ struct Solver {
         const size_t qq = (size_t)q * q, pq = (size_t)p * q;
         CGGM_TRY(ensure(c->Syy, 8 * qq));
         CGGM_TRY(ensure(c->Sxy, 8 * pq));
-        CGGM_TRY(ensure(c->Sxx, sizeof(T) * (size_t)p * p));
+        sxx_rows = sxx_chunk_rows(p, (int64_t)sizeof(T));
+        if (o.sxx_rows > 0 && o.sxx_rows < sxx_rows) sxx_rows = o.sxx_rows;
+        CGGM_TRY(ensure(c->Sxx, sizeof(T) * (size_t)sxx_rows * p));
         CGGM_TRY(ensure(c->Xd, 8 * (size_t)p));
         CGGM_TRY(ensure(c->Lam, 8 * qq));
         CGGM_TRY(ensure(c->Th, 8 * pq));
@@ -330,30 +337,45 @@ struct Solver {
         return CGGM_OK;
     }
 
-    // S_yy, S_xy, S_xx (Section 2.1) from Xt (p x n) and Yt (q x n), double
+    // Rows r0 .. r1 - 1 of S_xx = X^T X / n (Section 2.1) into the chunk buffer c->Sxx,
+    // from X: on the tensor cores (3xTF32) in the mixed path, SIMT double in the FP64 path.
+    cggm_status form_sxx(int64_t r0, int64_t r1) {
+        const int64_t n = z.n, p = z.p, rows = r1 - r0;
+        const double inv = 1.0 / (double)n;
+        if (sizeof(T) == 8) {
+            const double *Xt = P<double>(c->Xt);
+            gemm<double>(false, true, rows, p, n, inv, Xt + r0 * n, n, Xt, n, 0.0,
+                         (double *)c->Sxx.p, p, st);
+        } else if (tc()) {
+            CGGM_TRY(gemm_tc_nt(rows, p, n, (float)inv, P<float>(c->Xt_hi) + r0 * n, n,
+                                P<float>(c->Xt_hi), n, 0.0f, (float *)c->Sxx.p, p, true,
+                                P<float>(c->Xt_lo) + r0 * n, P<float>(c->Xt_lo),
+                                P<int>(c->tcerr), st));
+        } else {
+            gemm<float>(false, true, rows, p, n, (float)inv, P<float>(c->Xt_f) + r0 * n, n,
+                        P<float>(c->Xt_f), n, 0.0f, (float *)c->Sxx.p, p, st);
+        }
+        return CGGM_OK;
+    }
+
+    // S_yy, S_xy (Section 2.1) from Xt (p x n) and Yt (q x n), double; S_xx whole when it
+    // fits in one chunk (otherwise the Theta pass forms its rows chunk by chunk)
     cggm_status covariances() {
         const int64_t n = z.n, p = z.p, q = z.q;
         const double inv = 1.0 / (double)n;
         const double *Xt = P<double>(c->Xt), *Yt = P<double>(c->Yt);
         gemm<double>(false, true, q, q, n, inv, Yt, n, Yt, n, 0.0, P<double>(c->Syy), q, st);
         gemm<double>(false, true, p, q, n, inv, Xt, n, Yt, n, 0.0, P<double>(c->Sxy), q, st);
-        if (sizeof(T) == 8) {
-            gemm<double>(false, true, p, p, n, inv, Xt, n, Xt, n, 0.0, (double *)c->Sxx.p, p, st);
-        } else {
+        if (sizeof(T) == 4) {
             CGGM_TRY(ensure(c->Xt_f, 4 * (size_t)p * n));
             convert_d2f(p * n, Xt, P<float>(c->Xt_f), st);
             if (tc()) {
                 CGGM_TRY(tc_alloc());
                 CGGM_CUDA_TRY(cudaMemsetAsync(c->tcerr.p, 0, sizeof(int), st));
                 split_tf32(p, n, n, P<float>(c->Xt_f), P<float>(c->Xt_hi), P<float>(c->Xt_lo), st);
-                CGGM_TRY(gemm_tc_nt(p, p, n, (float)inv, P<float>(c->Xt_hi), n, P<float>(c->Xt_hi),
-                                    n, 0.0f, (float *)c->Sxx.p, p, true, P<float>(c->Xt_lo),
-                                    P<float>(c->Xt_lo), P<int>(c->tcerr), st));
-            } else {
-                gemm<float>(false, true, p, p, n, (float)inv, P<float>(c->Xt_f), n,
-                            P<float>(c->Xt_f), n, 0.0f, (float *)c->Sxx.p, p, st);
             }
         }
+        if (sxx_rows == p) CGGM_TRY(form_sxx(0, p));
         note_launch();
         rowsq_kernel<double><<<(unsigned)p, 256, 0, st>>>(p, n, Xt, inv, P<double>(c->Xd));
         CGGM_CUDA_TRY(cudaGetLastError());
@@ -462,6 +484,30 @@ struct Solver {
         return CGGM_OK;
     }
 
+    // One Theta pass (Section 3.2) over the m active coordinates, S_xx rows from the chunk
+    // buffer: with all of S_xx held, one launch; otherwise, for each chunk of rows that
+    // holds active coordinates, its rows of S_xx are formed and the pass continues over
+    // that chunk's part of the (row-major) list.
+    cggm_status theta_pass(int64_t m, int B) {
+        const int64_t p = z.p, q = z.q;
+        const int32_t *ti = P<int32_t>(c->ti), *tj = P<int32_t>(c->tj);
+        if (sxx_rows == p)
+            return theta_sweep<T>(p, q, (const T *)c->Sxx.p, 0, P<double>(c->Xd), SigT(),
+                                  P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m, ti,
+                                  tj, lamT, (T *)c->dV.p, B, c->scr, st);
+        for (int64_t r0 = 0; r0 < p; r0 += sxx_rows) {
+            const int64_t r1 = r0 + sxx_rows < p ? r0 + sxx_rows : p;
+            const int64_t k0 = th_rowoff[r0], k1 = th_rowoff[r1];
+            if (k1 <= k0) continue;
+            CGGM_TRY(form_sxx(r0, r1));
+            CGGM_TRY(theta_sweep<T>(p, q, (const T *)c->Sxx.p, r0, P<double>(c->Xd), SigT(),
+                                    P<double>(c->Sd), P<double>(c->W), P<double>(c->Th),
+                                    k1 - k0, ti + k0, tj + k0, lamT, (T *)c->dV.p, B, c->scr,
+                                    st));
+        }
+        return CGGM_OK;
+    }
+
     double f_from(const double *h) const {
         return -h[S_LOGDET] + h[S_SYYL] + 2.0 * h[S_SXYT] + h[S_TRACE] / (double)z.n +
                lamL * h[S_L1L] + lamT * h[S_L1T];
@@ -549,6 +595,11 @@ struct Solver {
             active_compact(p, q, P<double>(c->GT), P<double>(c->Th), lamT, lamT, false,
                            P<int64_t>(c->rowcnt), P<int32_t>(c->ti), P<int32_t>(c->tj),
                            P<int64_t>(c->cnt) + 1, st);
+            if (sxx_rows < p) {  // row offsets of the Theta list (read after the sync below)
+                th_rowoff.resize((size_t)p + 1);
+                CGGM_CUDA_TRY(cudaMemcpyAsync(th_rowoff.data(), c->rowcnt.p, 8 * (size_t)(p + 1),
+                                              cudaMemcpyDeviceToHost, st));
+            }
             cudaEventRecord(ev[2], st);
             CGGM_CUDA_TRY(cudaMemcpyAsync(h, s, 8 * S_COUNT, cudaMemcpyDeviceToHost, st));
             CGGM_CUDA_TRY(cudaMemcpyAsync(hc, c->cnt.p, 16, cudaMemcpyDeviceToHost, st));
@@ -667,10 +718,7 @@ struct Solver {
                              P<double>(c->Pt), n, 1.0, P<double>(c->W), q, st);
             }
             CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, sizeof(T) * pq, st));
-            CGGM_TRY(theta_sweep<T>(p, q, (const T *)c->Sxx.p, P<double>(c->Xd), SigT(),
-                                    P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), hc[1],
-                                    P<int32_t>(c->ti), P<int32_t>(c->tj), lamT, (T *)c->dV.p, B,
-                                    c->scr, st));
+            CGGM_TRY(theta_pass(hc[1], B));
             cudaEventRecord(ev[6], st);
             CGGM_TRY(sync_err(c));
             CGGM_TRY(tc_check());
@@ -829,6 +877,7 @@ cggm_status solve_common(cggm_ctx *c, const void *X, int xdtype, const void *Y, 
         !((o.sweep_batch == 256 || o.sweep_batch == 512) && o.precision == CGGM_MIXED))
         return CGGM_EINVAL;
     if (o.precision != CGGM_FP64 && o.precision != CGGM_MIXED) return CGGM_EINVAL;
+    if (o.sxx_rows < 0) return CGGM_EINVAL;
     if (info) memset(info, 0, sizeof(*info));
     CGGM_TRY(set_device(c));
     CGGM_TRY(ensure(c->err, sizeof(int)));
@@ -857,6 +906,7 @@ void cggm_opts_default(cggm_opts *o) {
     o->sweep_batch = 0;
     o->target_f = -INFINITY;
     o->verbose = 0;
+    o->sxx_rows = 0;
 }
 
 const char *cggm_status_string(int s) {
@@ -1174,9 +1224,15 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
     CGGM_TRY(check_sizes(n, p, q));
     CGGM_TRY(set_device(c));
     CGGM_TRY(check_pairs(c, ti, tj, m, p, q, false));
+    // the rows of the list on the host, to cut it into runs whose rows fit one S_xx chunk
+    std::vector<int32_t> rows_h((size_t)m);
+    if (m > 0)
+        CGGM_CUDA_TRY(cudaMemcpy(rows_h.data(), ti, 4 * (size_t)m, cudaMemcpyDefault));
     const size_t qq = (size_t)q * q, pq = (size_t)p * q;
+    const int64_t esz = precision == CGGM_FP64 ? 8 : 4;
+    const int64_t R = sxx_chunk_rows(p, esz);
     CGGM_TRY(load_transposed(c, X, CGGM_F64, n, p, c->Xt, nullptr));
-    CGGM_TRY(ensure(c->Sxx, 8 * (size_t)p * p));
+    CGGM_TRY(ensure(c->Sxx, (size_t)esz * (size_t)R * p));
     CGGM_TRY(ensure(c->Xd, 8 * (size_t)p));
     CGGM_TRY(load_double(c, Sxy, pq, c->Sxy));
     CGGM_TRY(load_double(c, Sigma, qq, c->Sig));
@@ -1198,27 +1254,45 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
                  P<double>(c->Pt), n, c->st);
     CGGM_CUDA_TRY(cudaMemcpyAsync(c->W.p, c->Sxy.p, 8 * pq, cudaMemcpyDeviceToDevice, c->st));
     gemm<double>(false, true, p, q, n, inv, Xt, n, P<double>(c->Pt), n, 1.0, P<double>(c->W), q, c->st);
-    if (precision == CGGM_FP64) {
-        gemm<double>(false, true, p, p, n, inv, Xt, n, Xt, n, 0.0, P<double>(c->Sxx), p, c->st);
-        CGGM_TRY(ensure(c->dV, 8 * pq));
-        CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, 8 * pq, c->st));
-        CGGM_TRY(theta_sweep<double>(p, q, P<double>(c->Sxx), P<double>(c->Xd), P<double>(c->Sig),
-                                     P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
-                                     P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<double>(c->dV),
-                                     128, c->scr, c->st));
-    } else {
+    if (precision == CGGM_MIXED) {
         CGGM_TRY(ensure(c->Xt_f, 4 * (size_t)p * n));
         CGGM_TRY(ensure(c->Sig_f, 4 * qq));
         convert_d2f(p * n, Xt, P<float>(c->Xt_f), c->st);
-        gemm<float>(false, true, p, p, n, (float)inv, P<float>(c->Xt_f), n, P<float>(c->Xt_f), n,
-                    0.0f, P<float>(c->Sxx), p, c->st);
         convert_d2f(q * q, P<double>(c->Sig), P<float>(c->Sig_f), c->st);
-        CGGM_TRY(ensure(c->dV, 4 * pq));
-        CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, 4 * pq, c->st));
-        CGGM_TRY(theta_sweep<float>(p, q, P<float>(c->Sxx), P<double>(c->Xd), P<float>(c->Sig_f),
-                                    P<double>(c->Sd), P<double>(c->W), P<double>(c->Th), m,
-                                    P<int32_t>(c->ti), P<int32_t>(c->tj), lam_T, P<float>(c->dV),
-                                    256, c->scr, c->st));
+    }
+    CGGM_TRY(ensure(c->dV, (size_t)esz * pq));
+    CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, (size_t)esz * pq, c->st));
+    // runs of the list whose rows lie within R consecutive rows: S_xx rows lo .. lo + R - 1
+    // formed from X, then the pass continues over the run
+    for (int64_t k0 = 0; k0 < m;) {
+        int64_t lo = rows_h[k0], hi = lo, k1 = k0 + 1;
+        while (k1 < m) {
+            const int64_t r = rows_h[k1];
+            const int64_t nlo = r < lo ? r : lo, nhi = r > hi ? r : hi;
+            if (nhi - nlo + 1 > R) break;
+            lo = nlo;
+            hi = nhi;
+            k1++;
+        }
+        const int64_t x0 = (lo + R <= p) ? lo : p - R;  // the chunk's first row
+        const int64_t rows = R;
+        const int32_t *ri = P<int32_t>(c->ti) + k0, *rj = P<int32_t>(c->tj) + k0;
+        if (precision == CGGM_FP64) {
+            gemm<double>(false, true, rows, p, n, inv, Xt + x0 * n, n, Xt, n, 0.0,
+                         P<double>(c->Sxx), p, c->st);
+            CGGM_TRY(theta_sweep<double>(p, q, P<double>(c->Sxx), x0, P<double>(c->Xd),
+                                         P<double>(c->Sig), P<double>(c->Sd), P<double>(c->W),
+                                         P<double>(c->Th), k1 - k0, ri, rj, lam_T,
+                                         P<double>(c->dV), 128, c->scr, c->st));
+        } else {
+            gemm<float>(false, true, rows, p, n, (float)inv, P<float>(c->Xt_f) + x0 * n, n,
+                        P<float>(c->Xt_f), n, 0.0f, P<float>(c->Sxx), p, c->st);
+            CGGM_TRY(theta_sweep<float>(p, q, P<float>(c->Sxx), x0, P<double>(c->Xd),
+                                        P<float>(c->Sig_f), P<double>(c->Sd), P<double>(c->W),
+                                        P<double>(c->Th), k1 - k0, ri, rj, lam_T,
+                                        P<float>(c->dV), 256, c->scr, c->st));
+        }
+        k0 = k1;
     }
     CGGM_TRY(store_double(c, Theta_out, c->Th.p, pq));
     return sync_err(c);

@@ -15,6 +15,7 @@
 
 #include "common.cuh"
 #include "load.cuh"
+#include "sweeps.cuh"
 
 namespace {
 
@@ -62,7 +63,7 @@ namespace {
 // Bytes a solve of this size holds on the device (the workspace cggm_solve allocates plus
 // the request's own copies of X, Y and its warm start), rounded up by 1 %.
 int64_t footprint_bytes(int64_t n, int64_t p, int64_t q, int precision) {
-    const int64_t qq = q * q, pq = p * q, pp = p * p;
+    const int64_t qq = q * q, pq = p * q;
     const int64_t t = precision == CGGM_MIXED ? 4 : 8;
     int64_t b = 0;
     b += 8 * (n * p + n * q);            // transposed X, Y (double)
@@ -70,7 +71,7 @@ int64_t footprint_bytes(int64_t n, int64_t p, int64_t q, int precision) {
     b += 8 * (10 * qq);                  // S_yy, Lambda, factor, Sigma, trial pair, work, G, D
     b += t * (3 * qq);                   // Sigma copy, Psi, the Lambda cache
     b += 8 * (4 * pq) + t * pq;          // S_xy, Theta, G_Theta, W; the Theta cache
-    b += t * pp;                         // S_xx
+    b += t * (cggm::sxx_chunk_rows(p, t) * p);  // rows of S_xx held at once (at most 256 MiB)
     b += 8 * (3 * q * n) + 8 * (2 * p + 4 * q);
     b += 4 * (qq / 2 + q + 1) * 2 + 4 * pq * 2;  // active lists
     if (precision == CGGM_MIXED) {

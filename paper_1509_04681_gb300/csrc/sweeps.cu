@@ -779,7 +779,8 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
 // ---------------------------------------------------------------------------------
 template <typename T, int NS>
 __global__ void __launch_bounds__(kThreads, 1)
-theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double *__restrict__ Xd,
+theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
+                   const double *__restrict__ Xd,
                    const T *__restrict__ Sig, const double *__restrict__ Sd,
                    const double *__restrict__ W, double *Theta, int64_t m,
                    const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam,
@@ -808,9 +809,10 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
     const bool use_ring = ((p * (int64_t)sizeof(T)) % 16) == 0 && aligned16(Sxx) && aligned16(dVt);
 
     // change of (S_xx Delta V)_ij per unit step of Theta_ab, times 2: 2 (S_xx)_{i a} Sigma_{j b}
-    // (Sigma symmetric; read along row j, b varying fastest across threads)
+    // (Sigma symmetric; read along row j, b varying fastest across threads).  Sxx holds the
+    // rows x0, x0 + 1, ... of S_xx that this launch's coordinates lie in.
     auto coefficient = [&](int64_t i, int64_t j, int64_t a, int64_t b) -> T {
-        return T(2) * Sxx[i * p + a] * Sig[j * q + b];
+        return T(2) * Sxx[(i - x0) * p + a] * Sig[j * q + b];
     };
 
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
@@ -837,7 +839,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
             }
             // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
             DotPlan<T, 2> pl;
-            pl.rows[0] = Sxx + i0 * p;
+            pl.rows[0] = Sxx + (i0 - x0) * p;
             pl.rows[1] = dVt + j0 * p;
             pl.ia[0] = 0; pl.ib[0] = 1;
             if (!two) {
@@ -849,7 +851,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, const double
                 pl.ia[1] = 0; pl.ib[1] = 2;
             } else {
                 pl.nrows = 4;
-                pl.rows[2] = Sxx + i1 * p;
+                pl.rows[2] = Sxx + (i1 - x0) * p;
                 pl.rows[3] = dVt + j1 * p;
                 pl.ia[1] = 2; pl.ib[1] = 3;
             }
@@ -1125,17 +1127,17 @@ cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const do
 }
 
 template <typename T>
-cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, const T *Sigma,
-                        const double *Sd, const double *W, double *Theta, int64_t m,
-                        const int32_t *ti, const int32_t *tj, double lam, T *dV, int B,
-                        SweepScratch &scr, cudaStream_t st) {
+cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, int64_t x0, const double *Xd,
+                        const T *Sigma, const double *Sd, const double *W, double *Theta,
+                        int64_t m, const int32_t *ti, const int32_t *tj, double lam, T *dV,
+                        int B, SweepScratch &scr, cudaStream_t st) {
     if (m <= 0) return CGGM_OK;
     if (B < 32 || B > (sizeof(T) == 4 ? 512 : 128) || (B & (B - 1))) return CGGM_EINVAL;
     CGGM_TRY(scratch_reserve(scr));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
     const size_t smem = smem_layout<T>(B).total;
-    void *args[] = {(void *)&p, (void *)&q, (void *)&Sxx, (void *)&Xd, (void *)&Sigma,
+    void *args[] = {(void *)&p, (void *)&q, (void *)&Sxx, (void *)&x0, (void *)&Xd, (void *)&Sigma,
                     (void *)&Sd, (void *)&W, (void *)&Theta, (void *)&m, (void *)&ti,
                     (void *)&tj, (void *)&lam, (void *)&dV, (void *)&B, (void *)&scr};
     const void *fn;
@@ -1160,11 +1162,12 @@ template cggm_status lambda_sweep<float>(int64_t, const float *, const float *, 
                                          const double *, const double *, const double *, int64_t,
                                          const int32_t *, const int32_t *, double, double, double *,
                                          float *, int, SweepScratch &, cudaStream_t);
-template cggm_status theta_sweep<double>(int64_t, int64_t, const double *, const double *,
-                                         const double *, const double *, const double *, double *,
-                                         int64_t, const int32_t *, const int32_t *, double, double *,
-                                         int, SweepScratch &, cudaStream_t);
-template cggm_status theta_sweep<float>(int64_t, int64_t, const float *, const double *,
+template cggm_status theta_sweep<double>(int64_t, int64_t, const double *, int64_t,
+                                         const double *, const double *, const double *,
+                                         const double *, double *, int64_t, const int32_t *,
+                                         const int32_t *, double, double *, int, SweepScratch &,
+                                         cudaStream_t);
+template cggm_status theta_sweep<float>(int64_t, int64_t, const float *, int64_t, const double *,
                                         const float *, const double *, const double *, double *,
                                         int64_t, const int32_t *, const int32_t *, double, float *,
                                         int, SweepScratch &, cudaStream_t);

@@ -25,14 +25,26 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
                          double *D, T *U, int B, SweepScratch &scr,
                          cudaStream_t st);
 
-// Theta pass: coordinates (ti, tj) row-major.  Sxx (p x p, T) with double diagonal Xd,
+// Theta pass: coordinates (ti, tj) row-major.  Sxx: rows x0 .. x0 + k - 1 of S_xx (k x p,
+// T), holding every row i that the coordinates name; Xd the double diagonal of S_xx;
 // Sigma (q x q, T) with double diagonal Sd, W = S_xy + S_xx Theta Sigma at entry
-// (double p x q), Theta (double p x q) updated in place.  dV (T, p x q) must be zero.
+// (double p x q), Theta (double p x q) updated in place.  dV (T, p x q): Delta V of the
+// pass so far (zero at the start of the pass; a pass may be split into launches over
+// consecutive parts of its list, each with the S_xx rows of its part).
 template <typename T>
-cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, const double *Xd, const T *Sigma,
-                        const double *Sd, const double *W, double *Theta, int64_t m,
-                        const int32_t *ti, const int32_t *tj, double lam, T *dV, int B,
-                        SweepScratch &scr, cudaStream_t st);
+cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, int64_t x0, const double *Xd,
+                        const T *Sigma, const double *Sd, const double *W, double *Theta,
+                        int64_t m, const int32_t *ti, const int32_t *tj, double lam, T *dV,
+                        int B, SweepScratch &scr, cudaStream_t st);
+
+// Rows of S_xx (p x p, element size esz) that the Theta pass holds at once: all p when they
+// fit in 256 MiB, otherwise as many as fit (at least one).  S_xx is formed from X in chunks
+// of this many rows and never stored whole beyond that size.
+constexpr int64_t kSxxChunkBytes = (int64_t)256 << 20;
+inline int64_t sxx_chunk_rows(int64_t p, int64_t esz) {
+    const int64_t r = kSxxChunkBytes / (p * esz);
+    return r >= p ? p : (r < 1 ? 1 : r);
+}
 
 // lambda_sweep in double on scratch buffers laid out by the caller (mu: B doubles, sub1:
 // scratch_sub1_bytes(B, 8), sub2: scratch_sub2_bytes(B, 8), bar, err); allocates nothing.

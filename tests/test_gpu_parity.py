@@ -336,3 +336,40 @@ def test_device_inputs(ctx):
     r2 = ctx.cggm_solve(pr.X.astype(np.float32), pr.Y.astype(np.float32), pr.lam_L, pr.lam_T,
                         tol=1e-6, opts=cg.make_opts(precision=0))
     np.testing.assert_array_equal(r1.Lambda, r2.Lambda)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_solve_with_sxx_in_row_chunks_matches_oracle(ctx, prec):
+    """S_xx held 37 rows at a time (200 inputs: five full chunks and a ragged sixth, each
+    formed from X before the Theta pass continues over its rows): the whole solve meets the
+    method's bar against the oracle, and in double precision stays within rounding of the
+    solve that holds S_xx whole."""
+    pr = synth.workload("chain-gauss-p200-q100-n100")
+    ref = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, max_iter=3000)
+    o = cg.make_opts(precision=prec, max_iter=3000, sxx_rows=37)
+    r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, opts=o)
+    check_solution(pr, r, ref, ref.f)
+    if prec == 0:
+        for k in (1, 3):
+            a = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12,
+                               opts=cg.make_opts(precision=0, max_iter=k, sxx_rows=37))
+            b = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-12, max_iter=k)
+            assert rel(a.Theta, b.Theta) < 1e-8 and rel(a.Lambda, b.Lambda) < 1e-8
+
+
+def test_theta_pass_out_of_row_order(ctx):
+    """The step-level Theta pass with a list that is not row-major (distinct coordinates,
+    rows jumping back and forth) equals the oracle's pass in that order.  (Its rows fit one
+    S_xx chunk here; lists over several chunks are covered at p = 40000 in
+    test_gpu_maxsize.py.)"""
+    pr = problem(50, 12, 30, seed=21)
+    Lam, Th = state_at(pr)
+    Sxx, Sxy, Syy = oracle.covariances(pr.X, pr.Y)
+    Sigma = np.linalg.inv(Lam)
+    rng = np.random.default_rng(21)
+    flat = rng.permutation(50 * 12)[:300]
+    ti = (flat // 12).astype(np.int32)
+    tj = (flat % 12).astype(np.int32)
+    want = oracle.theta_sweep(Sxx, Sxy, Sigma, Th, ti, tj, 0.05)
+    got = ctx.cggm_theta_sweep(pr.X, Sxy, Sigma, Th, ti, tj, 0.05, precision=cg.CGGM_FP64)
+    assert rel(got, want) < 1e-9

@@ -36,3 +36,13 @@ def test_largest_configured_workload_fits_one_gpu():
     """p = 40000, q = 20000, n = 500: one solve fits in a GB300's memory."""
     for prec in (cg.CGGM_FP64, cg.CGGM_MIXED):
         assert cg.footprint(500, 40000, 20000, prec) < 0.5 * HBM_BYTES
+
+
+def test_sxx_is_held_in_chunks_of_at_most_256_mib():
+    """Only up to 256 MiB of S_xx rows count at large p: doubling p from 40000 to 80000
+    adds far less than the 19 GB a whole double S_xx would."""
+    for prec in (cg.CGGM_FP64, cg.CGGM_MIXED):
+        a = cg.footprint(500, 40000, 20000, prec)
+        b = cg.footprint(500, 80000, 20000, prec)
+        per_pq = 8 * 6 + 4  # the p x q matrices a solve keeps, double and cache type
+        assert b - a < per_pq * 40000 * 20000 * 1.2 + (1 << 30)
