@@ -302,6 +302,14 @@ cggm_status cggm_server_submit(cggm_server *srv, const cggm_request *req, uint64
 cggm_status cggm_server_poll(cggm_server *srv, uint64_t id, int wait, cggm_result *out);
 /* Cancel requests not yet admitted, wait for the running ones, release everything. */
 void cggm_server_destroy(cggm_server *srv);
+/* The coordinate passes of the requests that run at once share cooperative launches: a pass
+ * that becomes ready waits briefly (until every running request has one ready, or 200 us)
+ * for the passes of other requests, and up to eight passes of one precision and batch size
+ * then run in one launch, each on its own group of SMs (the result of a pass does not depend
+ * on how many SMs it gets).  Counts since creation: launches, passes launched, and launches
+ * that held more than one pass; each pointer may be NULL.  Not in the paper (a serving layer). */
+cggm_status cggm_server_stats(cggm_server *srv, int64_t *pass_launches, int64_t *passes,
+                              int64_t *shared_launches);
 /* Device bytes a request of this size is accounted for (workspace of cggm_solve plus the
  * request's own device copies); -1 for invalid sizes. */
 int64_t cggm_footprint(int64_t n, int64_t p, int64_t q, int precision);

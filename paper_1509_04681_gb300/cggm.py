@@ -29,7 +29,7 @@ CGGM_ORDER_NATURAL, CGGM_ORDER_RCM, CGGM_ORDER_GIVEN, CGGM_ORDER_MINDEG, CGGM_OR
 
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
-    "cggm_solve_dense", "cggm_free_coo",
+    "cggm_solve_dense", "cggm_free_coo", "cggm_server_stats",
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
@@ -135,6 +135,8 @@ def _lib():
         lib.cggm_server_poll.argtypes = [vp, ctypes.c_uint64, ip, ctypes.POINTER(cggm_result)]
         lib.cggm_server_destroy.argtypes = [vp]
         lib.cggm_server_destroy.restype = None
+        lib.cggm_server_stats.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                          ctypes.POINTER(i64)]
         lib.cggm_footprint.argtypes = [i64, i64, i64, ip]
         lib.cggm_footprint.restype = i64
         lib.cggm_tuned_batch.argtypes = [i64, i64, ip]
@@ -178,7 +180,8 @@ def _lib():
                                                      "cggm_chol_structure",
                                                      "cggm_tuner_save", "cggm_tuner_load",
                                                      "cggm_block_count",
-                                                     "cggm_server_submit", "cggm_server_poll"):
+                                                     "cggm_server_submit", "cggm_server_poll",
+                                                     "cggm_server_stats"):
                 f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -755,6 +758,13 @@ class Server:
             _, _, _, Lo, To = self._keep[rid]
             d["Lambda"], d["Theta"] = Lo, To
         return d
+
+    def stats(self):
+        """cggm_server_stats: pass launches, passes launched, launches holding several."""
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib().cggm_server_stats(self._h, ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(c)), "cggm_server_stats")
+        return {"pass_launches": a.value, "passes": b.value, "shared_launches": c.value}
 
     def close(self):
         if getattr(self, "_h", None):

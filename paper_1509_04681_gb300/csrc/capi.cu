@@ -892,6 +892,12 @@ cggm_status solve_common(cggm_ctx *c, const void *X, int xdtype, const void *Y, 
 
 }  // namespace
 
+namespace cggm {
+void ctx_set_batcher(cggm_ctx *c, PassBatcher *b) {
+    if (c) c->scr.batcher = b;
+}
+}  // namespace cggm
+
 extern "C" {
 
 void cggm_opts_default(cggm_opts *o) {

@@ -44,6 +44,8 @@ struct cggm_server {
     std::vector<std::thread> workers;
     uint64_t next_id = 1;
     bool stopping = false;
+    // the coordinate passes of the requests running at once share cooperative launches
+    cggm::PassBatcher *batcher = nullptr;
 
     double now() const {
         return std::chrono::duration<double>(Clock::now() - t0).count();
@@ -160,7 +162,10 @@ void cggm_server::worker_loop() {
         cggm_ctx *ctx = nullptr;
         Outcome out{CGGM_ECUDA, 0, 0.0};
         if (cggm_create(&ctx, device, nullptr) == CGGM_OK) {
+            cggm::ctx_set_batcher(ctx, batcher);
+            cggm::batcher_add_busy(batcher, 1);
             out = run(j, ctx);
+            cggm::batcher_add_busy(batcher, -1);
             cggm_destroy(ctx);  // return the workspace: the budget accounts for it exactly
         }
         {
@@ -203,6 +208,7 @@ cggm_status cggm_server_create(cggm_server **out, int device, int slots, int64_t
     }
     s->budget = hbm_budget_bytes;
     s->t0 = Clock::now();
+    s->batcher = cggm::batcher_create();
     for (int i = 0; i < slots; i++) s->workers.emplace_back([s] { s->worker_loop(); });
     *out = s;
     return CGGM_OK;
@@ -270,7 +276,15 @@ void cggm_server_destroy(cggm_server *s) {
     s->cv_done.notify_all();
     for (auto &t : s->workers) t.join();
     for (auto &kv : s->jobs) delete kv.second;
+    cggm::batcher_destroy(s->batcher);
     delete s;
+}
+
+cggm_status cggm_server_stats(cggm_server *s, int64_t *pass_launches, int64_t *passes,
+                              int64_t *shared_launches) {
+    if (!s) return CGGM_EINVAL;
+    cggm::batcher_counts(s->batcher, pass_launches, passes, shared_launches);
+    return CGGM_OK;
 }
 
 }  // extern "C"

@@ -25,8 +25,12 @@
 #include "sweeps.cuh"
 #include "mbar.cuh"
 
+#include <chrono>
+#include <condition_variable>
 #include <cooperative_groups.h>
+#include <deque>
 #include <mutex>
+#include <vector>
 
 namespace cggm {
 
@@ -314,9 +318,16 @@ struct DotPlan {
 // len * sizeof(T) a multiple of 16.  Every thread of the CTA calls it.  A copy that does
 // not land within the wait limit makes the whole CTA give up (false, err set), after
 // thread 0 has waited, again with a limit, for the copies it still has in flight.
-template <typename T, int ND>
+// `mid()` is run by every thread once the first chunks are in flight, so that independent
+// work (and its loads) overlaps their latency.
+struct NoWork {
+    __device__ void operator()() const {}
+};
+
+template <typename T, int ND, typename F = NoWork>
 __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
-                          unsigned char *ring, uint64_t *mb, uint32_t &phase, int *err) {
+                          unsigned char *ring, uint64_t *mb, uint32_t &phase, int *err,
+                          F mid = F()) {
     constexpr int CW = kChunkBytes / (int)sizeof(T);
     using VT = typename V16<T>::type;
     constexpr int VN = V16<T>::n;
@@ -344,6 +355,7 @@ __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
         fence_proxy_async();
         for (; issued < nch && issued < kStages; issued++) issue(issued);
     }
+    mid();
     for (int64_t c = 0; c < nch; c++) {
         const int st = (int)(c % kStages);
         const bool ok = mbar_wait(&mb[st], (phase >> st) & 1u, err);
@@ -386,15 +398,37 @@ __device__ __forceinline__ bool aligned16(const T *p) {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
 }
 
-// Load the coordinates of the batch [s, s + nb) into shared memory and find its segments
-// (maximal runs of coordinates with the same first index; the lists are row-major, so a
-// segment is the part of one row of the active set that falls in the batch).
-__device__ void load_batch(const int32_t *__restrict__ ai, const int32_t *__restrict__ aj,
-                           int64_t s, int nb, int32_t *sa, int32_t *sb, int32_t *sseg,
-                           int32_t *snseg) {
-    for (int l = threadIdx.x; l < nb; l += blockDim.x) {
-        sa[l] = ai[s + l];
-        sb[l] = aj[s + l];
+// The coordinates of a batch [s, s + nb) in registers (at most two per thread: B <= 512),
+// fetched ahead of the point where they are stored, so that the load latency overlaps other
+// work (the wait of a grid barrier).
+struct BatchRegs {
+    int32_t a[2], b[2];
+};
+static_assert(2 * kThreads >= 512, "BatchRegs holds two coordinates per thread");
+
+__device__ __forceinline__ void fetch_batch(const int32_t *__restrict__ ai,
+                                            const int32_t *__restrict__ aj, int64_t s, int nb,
+                                            BatchRegs &r) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int l = threadIdx.x + u * kThreads;
+        r.a[u] = l < nb ? __ldg(ai + s + l) : 0;
+        r.b[u] = l < nb ? __ldg(aj + s + l) : 0;
+    }
+}
+
+// Store a fetched batch into shared memory and find its segments (maximal runs of
+// coordinates with the same first index; the lists are row-major, so a segment is the part
+// of one row of the active set that falls in the batch).
+__device__ void store_batch(const BatchRegs &r, int nb, int32_t *sa, int32_t *sb, int32_t *sseg,
+                            int32_t *snseg) {
+#pragma unroll
+    for (int u = 0; u < 2; u++) {
+        const int l = threadIdx.x + u * kThreads;
+        if (l < nb) {
+            sa[l] = r.a[u];
+            sb[l] = r.b[u];
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -441,11 +475,11 @@ __device__ __forceinline__ BatchMeta meta_at(unsigned char *base, int B, int whi
 // of padding coordinates are zeroed.
 template <typename T, int NS>
 __device__ void cross_corrections(int nbn, int nbk, const T *X, const T *smu, const T (&xw)[NS],
-                                  T *corr) {
+                                  T *corr, unsigned bid, unsigned nblk) {
     constexpr int B = NS * 32;
     const int lane = threadIdx.x & 31;
-    const int gw = (int)(blockIdx.x * kWarps + (threadIdx.x >> 5));
-    const int gwarps = (int)(gridDim.x * kWarps);
+    const int gw = (int)(bid * kWarps + (threadIdx.x >> 5));
+    const int gwarps = (int)(nblk * kWarps);
     for (int l = gw; l < nbn; l += gwarps) {
         T acc = T(0);
 #pragma unroll
@@ -456,18 +490,22 @@ __device__ void cross_corrections(int nbn, int nbk, const T *X, const T *smu, co
         acc = warp_sum(acc);
         if (lane == 0) corr[l] = acc;
     }
-    if (blockIdx.x == gridDim.x - 1)
+    if (bid == nblk - 1)
         for (int l = nbn + threadIdx.x; l < B; l += blockDim.x) corr[l] = T(0);
 }
 
+// The pass on a group of nblk CTAs of a cooperative launch, this CTA being number bid of
+// the group (the whole grid for a single pass; a part of it when several passes share one
+// launch).  Every reduction is done by one CTA or one warp in a fixed order, so the result
+// does not depend on nblk.
 template <typename T, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
-lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
-                    const double *__restrict__ Sd, const double *__restrict__ Pd,
-                    const double *__restrict__ G, const double *__restrict__ Lam, int64_t m,
-                    const int32_t *__restrict__ ai, const int32_t *__restrict__ aj,
-                    double lam_off, double lam_diag, double *D, T *Ut, int B_arg,
-                    SweepScratch scr) {
+__device__ __forceinline__ void
+lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
+            const double *__restrict__ Sd, const double *__restrict__ Pd,
+            const double *__restrict__ G, const double *__restrict__ Lam, int64_t m,
+            const int32_t *__restrict__ ai, const int32_t *__restrict__ aj, double lam_off,
+            double lam_diag, double *D, T *Ut, int B_arg, SweepScratch scr, unsigned bid,
+            unsigned nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 6];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
@@ -478,13 +516,12 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
     const SmemLayout L = smem_layout<T>(B);
     unsigned char *work = smem + L.work;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned nblk = gridDim.x;
     T *preb = reinterpret_cast<T *>(scr.sub1);                // [2][PRE_N][B]
     T *coefb = reinterpret_cast<T *>(scr.sub2);               // [2][coef_slots(B)]
     T *gX = coefb + 2 * (size_t)coef_slots(B);                // [B][B]
     T *gcorr = gX + (size_t)B * B;                            // [B]
     const int64_t rows_per = (q + nblk - 1) / nblk;
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    const int64_t r0 = (int64_t)bid * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
     // phase A reads rows through the ring when bulk copies can address them
     const bool use_ring = ((q * (int64_t)sizeof(T)) % 16) == 0 && aligned16(Sig) &&
@@ -520,7 +557,35 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
     // and, when prev is given, the cross coefficients against the previous batch -> gX.
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
                        int nbp, int rank0) {
-        const int nA = (int)nblk - rank0, rank = (int)blockIdx.x - rank0;
+        const int nA = (int)nblk - rank0, rank = (int)bid - rank0;
+        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
+        const int64_t nt = (int64_t)nA * blockDim.x;
+        // The coefficients depend on entries of Sigma and Psi only, not on the dot products:
+        // they are formed while the first chunks of this CTA's dot products are in flight.
+        auto coef_work = [&]() {
+            for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
+                const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
+                pre[k * B + l] = T(0);
+            }
+            const int ncoef = nb * (nb - 1) / 2;
+#pragma unroll 2
+            for (int64_t e = t0; e < ncoef; e += nt) {
+                int l, l1;
+                decode_pair((int)e, l, l1);
+                coef[colbase(l1, B) + (l - l1 - 1)] =
+                    coefficient(bm.sa[l], bm.sb[l], bm.sa[l1], bm.sb[l1]);
+            }
+            if (prev) {
+                const int64_t ncross = (int64_t)nb * nbp;
+#pragma unroll 4
+                for (int64_t e = t0; e < ncross; e += nt) {
+                    const int l = (int)(e / nbp), l1 = (int)(e % nbp);
+                    gX[(size_t)l * B + l1] =
+                        coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
+                }
+            }
+        };
+        bool coef_done = false;
         for (int l = rank; l < nb; l += 2 * nA) {
             const int lb = l + nA;
             const bool two = lb < nb;
@@ -579,8 +644,15 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             }
             T acc[6];
             if (use_ring) {
-                if (!ring_dots<T, 6>(pl, q, acc, work, s_ring, ring_phase, scr.err)) return;
+                const bool ok = coef_done
+                                    ? ring_dots<T, 6>(pl, q, acc, work, s_ring, ring_phase, scr.err)
+                                    : ring_dots<T, 6>(pl, q, acc, work, s_ring, ring_phase,
+                                                      scr.err, coef_work);
+                coef_done = true;
+                if (!ok) return;
             } else {
+                if (!coef_done) coef_work();
+                coef_done = true;
 #pragma unroll
                 for (int d = 0; d < 6; d++) acc[d] = T(0);
                 for (int64_t t = threadIdx.x; t < q; t += blockDim.x) {
@@ -610,25 +682,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                 step_constants<T>(bb, a, cij, lam, pre, B, lw);
             }
         }
-        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
-        const int64_t nt = (int64_t)nA * blockDim.x;
-        for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
-            const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
-            pre[k * B + l] = T(0);
-        }
-        const int ncoef = nb * (nb - 1) / 2;
-        for (int64_t e = t0; e < ncoef; e += nt) {
-            int l, l1;
-            decode_pair((int)e, l, l1);
-            coef[colbase(l1, B) + (l - l1 - 1)] = coefficient(bm.sa[l], bm.sb[l], bm.sa[l1], bm.sb[l1]);
-        }
-        if (prev) {
-            const int64_t ncross = (int64_t)nb * nbp;
-            for (int64_t e = t0; e < ncross; e += nt) {
-                const int l = (int)(e / nbp), l1 = (int)(e % nbp);
-                gX[(size_t)l * B + l1] = coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
-            }
-        }
+        if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
     };
 
     // prologue: phase A of batch 0 by every CTA; no correction from an earlier batch
@@ -638,9 +692,12 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
     }
     BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
     int nbk = (int)(m < B ? m : B);
-    load_batch(ai, aj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
+    BatchRegs breg;  // indices of the next batch, fetched ahead
+    fetch_batch(ai, aj, 0, nbk, breg);
+    store_batch(breg, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
+    bool pref = false;  // breg holds the batch after the current one
     phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
-    if (blockIdx.x == 0) {
+    if (bid == 0) {
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
         if (threadIdx.x == 0) {
             for (int k = 0; k <= NS; k++) mbar_init(&s_mb[k], 1);
@@ -655,10 +712,13 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         T *pre_k = preb + (size_t)(k & 1) * PRE_N * B, *coef_k = coefb + (size_t)(k & 1) * coef_slots(B);
         T *pre_n = preb + (size_t)((k + 1) & 1) * PRE_N * B;
         T *coef_n = coefb + (size_t)((k + 1) & 1) * coef_slots(B);
-        if (nbn > 0) load_batch(ai, aj, sn, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
+        if (nbn > 0) {
+            if (!pref) fetch_batch(ai, aj, sn, nbn, breg);
+            store_batch(breg, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
+        }
 
         // ---- phase B of batch k on CTA 0, phase A of batch k+1 on the others ----
-        if (blockIdx.x == 0) {
+        if (bid == 0) {
             phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
                            scr.err);
@@ -669,7 +729,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
         // steps: they are issued between this CTA's arrival at the barrier and its wait, so
         // that their latency overlaps the wait.
         constexpr int R = NS <= 8 ? kRowsInFlight : 2;  // registers: R x NS values per lane
-        T sta[R], sv[R][NS], uv[R][NS];
+        T sta[R], sv[R][NS], uv[R][NS], ua[R];
         int bv[NS];
         auto seg_columns = [&](int g) {
             const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
@@ -684,12 +744,16 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             for (int r = 0; r < R; r++) {
                 const int64_t t = tb + (int64_t)kWarps * r;
                 sta[r] = T(0);
+                ua[r] = T(0);
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++) sv[r][kk] = uv[r][kk] = T(0);
                 if (t < r1) {
                     const T *Sr = Sig + t * q;
                     const T *Ur = Ut + t * q;
                     sta[r] = Sr[a];
+                    // U^T[t][a] is written at the end of this row's update only (the segment's
+                    // other columns b != a), so it is read here with the rest
+                    if (lane == 0) ua[r] = __ldcg(Ur + a);
 #pragma unroll
                     for (int kk = 0; kk < NS; kk++) {
                         if (bv[kk] >= 0) {
@@ -715,7 +779,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
                 const double mu = __ldcg(scr.mu + l);
                 smu[l] = (T)mu;
-                if (blockIdx.x == nblk - 1) {  // the direction itself
+                if (bid == nblk - 1) {  // the direction itself
                     const int64_t i = cur.sa[l], j = cur.sb[l];
                     D[i * q + j] = mu;
                     if (i != j) D[j * q + i] = mu;
@@ -724,7 +788,7 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
             __syncthreads();
             T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
             {
-                const int gw = (int)(blockIdx.x * kWarps + warp);
+                const int gw = (int)(bid * kWarps + warp);
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++) {
                     const int l1 = lane + 32 * kk;
@@ -758,14 +822,22 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
                             }
                         }
                         dot = warp_sum(dot);
-                        if (lane == 0) Ur[a] = __ldcg(Ur + a) + dot;
+                        if (lane == 0) Ur[a] = ua[r] + dot;
                     }
                 }
                 __syncwarp();  // this segment's writes before the next segment's reads
             }
-            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr);
+            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr, bid, nblk);
         }
-        if (!grid_sync(scr.bar, scr.err, nblk)) return;
+        {
+            // the indices of batch k + 2 are fetched while this barrier completes
+            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            const int64_t s2 = (k + 2) * B;
+            const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
+            pref = nb2 > 0;
+            if (pref) fetch_batch(ai, aj, s2, nb2, breg);
+            if (!grid_wait(scr.bar, scr.err, tk)) return;
+        }
         BatchMeta tmp = cur;
         cur = nxt;
         nxt = tmp;
@@ -777,14 +849,14 @@ lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ 
 // Theta sweep kernel.  Cache: dVt = (Delta V)^T (q x p), dVt[j][t] = (Delta Theta Sigma)[t][j].
 // Pipelined like the Lambda pass.
 // ---------------------------------------------------------------------------------
+// The pass on a group of nblk CTAs (see lambda_pass).
 template <typename T, int NS>
-__global__ void __launch_bounds__(kThreads, 1)
-theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
-                   const double *__restrict__ Xd,
-                   const T *__restrict__ Sig, const double *__restrict__ Sd,
-                   const double *__restrict__ W, double *Theta, int64_t m,
-                   const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam,
-                   T *dVt, int B_arg, SweepScratch scr) {
+__device__ __forceinline__ void
+theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
+           const double *__restrict__ Xd, const T *__restrict__ Sig,
+           const double *__restrict__ Sd, const double *__restrict__ W, double *Theta, int64_t m,
+           const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam, T *dVt,
+           int B_arg, SweepScratch scr, unsigned bid, unsigned nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 2];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
@@ -795,13 +867,12 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     const SmemLayout L = smem_layout<T>(B);
     unsigned char *work = smem + L.work;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned nblk = gridDim.x;
     T *preb = reinterpret_cast<T *>(scr.sub1);
     T *coefb = reinterpret_cast<T *>(scr.sub2);
     T *gX = coefb + 2 * (size_t)coef_slots(B);
     T *gcorr = gX + (size_t)B * B;
     const int64_t rows_per = (q + nblk - 1) / nblk;
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per;
+    const int64_t r0 = (int64_t)bid * rows_per;
     const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
     constexpr int VN = V16<T>::n;
     const int64_t nbatch = (m + B - 1) / B;
@@ -817,11 +888,39 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
 
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
                        int nbp, int rank0) {
-        const int nA = (int)nblk - rank0, rank = (int)blockIdx.x - rank0;
+        const int nA = (int)nblk - rank0, rank = (int)bid - rank0;
         // rows of Delta V that can be nonzero: those at or before this batch's first row
         // (the ring copies whole 16-byte words: entries beyond tmax are zero)
         const int64_t tmax = (int64_t)bm.sa[0] + 1;
         const int64_t tlen = ((tmax + VN - 1) / VN) * VN < p ? ((tmax + VN - 1) / VN) * VN : p;
+        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
+        const int64_t nt = (int64_t)nA * blockDim.x;
+        // the coefficients (entries of S_xx and Sigma only) are formed while the first chunks
+        // of this CTA's dot products are in flight
+        auto coef_work = [&]() {
+            for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
+                const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
+                pre[k * B + l] = T(0);
+            }
+            const int ncoef = nb * (nb - 1) / 2;
+#pragma unroll 2
+            for (int64_t e = t0; e < ncoef; e += nt) {
+                int l, l1;
+                decode_pair((int)e, l, l1);
+                coef[colbase(l1, B) + (l - l1 - 1)] =
+                    coefficient(bm.sa[l], bm.sb[l], bm.sa[l1], bm.sb[l1]);
+            }
+            if (prev) {
+                const int64_t ncross = (int64_t)nb * nbp;
+#pragma unroll 4
+                for (int64_t e = t0; e < ncross; e += nt) {
+                    const int l = (int)(e / nbp), l1 = (int)(e % nbp);
+                    gX[(size_t)l * B + l1] =
+                        coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
+                }
+            }
+        };
+        bool coef_done = false;
         for (int l = rank; l < nb; l += 2 * nA) {
             const int lb = l + nA;
             const bool two = lb < nb;
@@ -857,8 +956,16 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             }
             T acc[2];
             if (use_ring) {
-                if (!ring_dots<T, 2>(pl, tlen, acc, work, s_ring, ring_phase, scr.err)) return;
+                const bool ok = coef_done
+                                    ? ring_dots<T, 2>(pl, tlen, acc, work, s_ring, ring_phase,
+                                                      scr.err)
+                                    : ring_dots<T, 2>(pl, tlen, acc, work, s_ring, ring_phase,
+                                                      scr.err, coef_work);
+                coef_done = true;
+                if (!ok) return;
             } else {
+                if (!coef_done) coef_work();
+                coef_done = true;
                 acc[0] = acc[1] = T(0);
                 for (int64_t t = threadIdx.x; t < tmax; t += blockDim.x) {
                     T x[4];
@@ -876,25 +983,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                 step_constants<T>(2.0 * wij + 2.0 * d, a, cij, lam, pre, B, lw);
             }
         }
-        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
-        const int64_t nt = (int64_t)nA * blockDim.x;
-        for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
-            const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
-            pre[k * B + l] = T(0);
-        }
-        const int ncoef = nb * (nb - 1) / 2;
-        for (int64_t e = t0; e < ncoef; e += nt) {
-            int l, l1;
-            decode_pair((int)e, l, l1);
-            coef[colbase(l1, B) + (l - l1 - 1)] = coefficient(bm.sa[l], bm.sb[l], bm.sa[l1], bm.sb[l1]);
-        }
-        if (prev) {
-            const int64_t ncross = (int64_t)nb * nbp;
-            for (int64_t e = t0; e < ncross; e += nt) {
-                const int l = (int)(e / nbp), l1 = (int)(e % nbp);
-                gX[(size_t)l * B + l1] = coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
-            }
-        }
+        if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
     };
 
     if (threadIdx.x == 0) {
@@ -903,9 +992,12 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     }
     BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
     int nbk = (int)(m < B ? m : B);
-    load_batch(ti, tj, 0, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
+    BatchRegs breg;  // indices of the next batch, fetched ahead
+    fetch_batch(ti, tj, 0, nbk, breg);
+    store_batch(breg, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
+    bool pref = false;  // breg holds the batch after the current one
     phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
-    if (blockIdx.x == 0) {
+    if (bid == 0) {
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
         if (threadIdx.x == 0) {
             for (int k = 0; k <= NS; k++) mbar_init(&s_mb[k], 1);
@@ -920,9 +1012,12 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
         T *pre_k = preb + (size_t)(k & 1) * PRE_N * B, *coef_k = coefb + (size_t)(k & 1) * coef_slots(B);
         T *pre_n = preb + (size_t)((k + 1) & 1) * PRE_N * B;
         T *coef_n = coefb + (size_t)((k + 1) & 1) * coef_slots(B);
-        if (nbn > 0) load_batch(ti, tj, sn, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
+        if (nbn > 0) {
+            if (!pref) fetch_batch(ti, tj, sn, nbn, breg);
+            store_batch(breg, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
+        }
 
-        if (blockIdx.x == 0) {
+        if (bid == 0) {
             phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
                            scr.err);
@@ -933,7 +1028,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
         // on the steps: they are issued between this CTA's arrival at the barrier and its
         // wait.
         constexpr int R = NS <= 8 ? kRowsInFlight : 2;  // registers: R x NS values per lane
-        T sv[R][NS];
+        T sv[R][NS], va[R];
         int jv[NS];
         auto seg_columns = [&](int g) {
             const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
@@ -943,19 +1038,22 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                 jv[kk] = (l < l1) ? cur.sb[l] : -1;
             }
         };
-        auto load_rows = [&](int64_t tb) {
+        // Delta V^T[t][i] (the entry this segment adds to in row t) is read with the Sigma
+        // entries, by the lane that writes it
+        auto load_rows = [&](int64_t i, int64_t tb) {
 #pragma unroll
             for (int r = 0; r < R; r++) {
                 const int64_t t = tb + (int64_t)kWarps * r;
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++)
                     sv[r][kk] = (t < r1 && jv[kk] >= 0) ? Sig[t * q + jv[kk]] : T(0);
+                va[r] = (t < r1 && lane == 0) ? __ldcg(dVt + t * p + i) : T(0);
             }
         };
         {
             const GridTicket tk = grid_arrive(scr.bar, nblk);
             seg_columns(0);
-            load_rows(r0 + warp);
+            load_rows(cur.sa[cur.sseg[0]], r0 + warp);
             if (!grid_wait(scr.bar, scr.err, tk)) return;
         }
 
@@ -965,7 +1063,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
                 const double mu = __ldcg(scr.mu + l);
                 smu[l] = (T)mu;
-                if (blockIdx.x == nblk - 1) {  // Theta itself
+                if (bid == nblk - 1) {  // Theta itself
                     const int64_t i = cur.sa[l], j = cur.sb[l];
                     Theta[i * q + j] = __ldcg(Theta + i * q + j) + mu;
                 }
@@ -973,7 +1071,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             __syncthreads();
             T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
             {
-                const int gw = (int)(blockIdx.x * kWarps + warp);
+                const int gw = (int)(bid * kWarps + warp);
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++) {
                     const int l1 = lane + 32 * kk;
@@ -992,7 +1090,7 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                     mv[kk] = (l < l1) ? smu[l] : T(0);
                 }
                 for (int64_t tb = r0 + warp; tb < r1; tb += kWarps * R) {
-                    if (g > 0 || tb != r0 + warp) load_rows(tb);  // else: loaded before the barrier
+                    if (g > 0 || tb != r0 + warp) load_rows(i, tb);  // else: before the barrier
 #pragma unroll
                     for (int r = 0; r < R; r++) {
                         const int64_t t = tb + (int64_t)kWarps * r;
@@ -1001,21 +1099,85 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
 #pragma unroll
                         for (int kk = 0; kk < NS; kk++) dot = fma(mv[kk], sv[r][kk], dot);
                         dot = warp_sum(dot);
-                        if (lane == 0) {
-                            T *Vr = dVt + t * p;
-                            Vr[i] = __ldcg(Vr + i) + dot;
-                        }
+                        if (lane == 0) dVt[t * p + i] = va[r] + dot;
                     }
                 }
             }
-            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr);
+            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr, bid, nblk);
         }
-        if (!grid_sync(scr.bar, scr.err, nblk)) return;
+        {
+            // the indices of batch k + 2 are fetched while this barrier completes
+            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            const int64_t s2 = (k + 2) * B;
+            const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
+            pref = nb2 > 0;
+            if (pref) fetch_batch(ti, tj, s2, nb2, breg);
+            if (!grid_wait(scr.bar, scr.err, tk)) return;
+        }
         BatchMeta tmp = cur;
         cur = nxt;
         nxt = tmp;
         nbk = nbn;
     }
+}
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(kThreads, 1)
+lambda_sweep_kernel(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
+                    const double *__restrict__ Sd, const double *__restrict__ Pd,
+                    const double *__restrict__ G, const double *__restrict__ Lam, int64_t m,
+                    const int32_t *__restrict__ ai, const int32_t *__restrict__ aj,
+                    double lam_off, double lam_diag, double *D, T *Ut, int B_arg,
+                    SweepScratch scr) {
+    lambda_pass<T, NS>(q, Sig, Psi, Sd, Pd, G, Lam, m, ai, aj, lam_off, lam_diag, D, Ut, B_arg,
+                       scr, blockIdx.x, gridDim.x);
+}
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(kThreads, 1)
+theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
+                   const double *__restrict__ Xd, const T *__restrict__ Sig,
+                   const double *__restrict__ Sd, const double *__restrict__ W, double *Theta,
+                   int64_t m, const int32_t *__restrict__ ti, const int32_t *__restrict__ tj,
+                   double lam, T *dVt, int B_arg, SweepScratch scr) {
+    theta_pass<T, NS>(p, q, Sxx, x0, Xd, Sig, Sd, W, Theta, m, ti, tj, lam, dVt, B_arg, scr,
+                      blockIdx.x, gridDim.x);
+}
+
+// One pass of a multi-pass launch: its kind, its group of CTAs and its arguments.
+template <typename T>
+struct PassDesc {
+    int kind;  // 0: Lambda pass, 1: Theta pass
+    unsigned cta0, ncta;
+    int64_t p, q, m, x0;
+    const T *Sig, *Psi, *Sxx;
+    const double *Sd, *Pd, *G, *Lam, *Xd, *W;
+    const int32_t *ia, *ja;
+    double lam_off, lam_diag;  // Theta pass: lam_off is its lambda
+    double *out;               // Lambda pass: D; Theta pass: Theta
+    T *cache;                  // Lambda pass: U^T; Theta pass: Delta V^T
+    SweepScratch scr;
+};
+constexpr int kMaxPassGroups = 8;
+template <typename T>
+struct MultiPass {
+    int n;
+    PassDesc<T> d[kMaxPassGroups];
+};
+
+template <typename T, int NS>
+__global__ void __launch_bounds__(kThreads, 1)
+multi_pass_kernel(const __grid_constant__ MultiPass<T> mp) {
+    int g = 0;
+    while (g + 1 < mp.n && blockIdx.x >= mp.d[g + 1].cta0) g++;
+    const PassDesc<T> &d = mp.d[g];
+    const unsigned bid = blockIdx.x - d.cta0;
+    if (d.kind == 0)
+        lambda_pass<T, NS>(d.q, d.Sig, d.Psi, d.Sd, d.Pd, d.G, d.Lam, d.m, d.ia, d.ja, d.lam_off,
+                           d.lam_diag, d.out, d.cache, NS * 32, d.scr, bid, d.ncta);
+    else
+        theta_pass<T, NS>(d.p, d.q, d.Sxx, d.x0, d.Xd, d.Sig, d.Sd, d.W, d.out, d.m, d.ia, d.ja,
+                          d.lam_off, d.cache, NS * 32, d.scr, bid, d.ncta);
 }
 
 // A persistent pass needs every SM at once; two of them issued from different host threads
@@ -1051,6 +1213,170 @@ cggm_status read_err(int *err, cudaStream_t st) {
 }  // namespace
 
 int sweep_grid() { return sm_count(); }
+
+// ---------------------------------------------------------------------------------
+// Pass batcher: the coordinate passes of concurrent solves in one cooperative launch.
+// ---------------------------------------------------------------------------------
+struct PassBatcher {
+    struct Entry {
+        bool f32;
+        int B;
+        PassDesc<float> df;
+        PassDesc<double> dd;
+        cudaStream_t st;
+        cudaEvent_t ready;  // the submitting stream's work before the pass
+        cggm_status status = CGGM_OK;
+        bool done = false;
+    };
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Entry *> pending;
+    bool leader = false;
+    int busy = 0;
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    int64_t n_launch = 0, n_pass = 0, n_shared = 0;
+};
+
+PassBatcher *batcher_create() { return new PassBatcher(); }
+
+void batcher_destroy(PassBatcher *b) {
+    if (!b) return;
+    if (b->stream) {
+        cudaSetDevice(b->device);
+        cudaStreamSynchronize(b->stream);
+        cudaEventDestroy(b->done_ev);
+        cudaStreamDestroy(b->stream);
+    }
+    delete b;
+}
+
+void batcher_add_busy(PassBatcher *b, int delta) {
+    std::lock_guard<std::mutex> lk(b->mu);
+    b->busy += delta;
+    b->cv.notify_all();
+}
+
+void batcher_counts(PassBatcher *b, int64_t *launches, int64_t *passes, int64_t *shared) {
+    std::lock_guard<std::mutex> lk(b->mu);
+    if (launches) *launches = b->n_launch;
+    if (passes) *passes = b->n_pass;
+    if (shared) *shared = b->n_shared;
+}
+
+namespace {
+
+template <typename T, int NS>
+cggm_status launch_multi(PassBatcher &b, std::vector<PassBatcher::Entry *> &batch) {
+    MultiPass<T> mp;
+    mp.n = (int)batch.size();
+    const int grid = sweep_grid();
+    const int per = grid / mp.n, rem = grid % mp.n;
+    if (per < 2) return CGGM_ECUDA;  // each pass needs two CTAs at least
+    unsigned c0 = 0;
+    for (int g = 0; g < mp.n; g++) {
+        PassDesc<T> d;
+        if constexpr (sizeof(T) == 4) d = batch[g]->df;
+        else d = batch[g]->dd;
+        d.cta0 = c0;
+        d.ncta = (unsigned)(per + (g < rem ? 1 : 0));
+        c0 += d.ncta;
+        mp.d[g] = d;
+    }
+    const size_t smem = smem_layout<T>(NS * 32).total;
+    const void *fn = (const void *)multi_pass_kernel<T, NS>;
+    CGGM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    void *args[] = {(void *)&mp};
+    for (PassBatcher::Entry *e : batch) CGGM_CUDA_TRY(cudaStreamWaitEvent(b.stream, e->ready, 0));
+    {
+        std::lock_guard<std::mutex> lock(coop_mutex());
+        note_launch();
+        CGGM_CUDA_TRY(cudaLaunchCooperativeKernel(fn, dim3(c0), dim3(kThreads), args, smem,
+                                                  b.stream));
+        CGGM_CUDA_TRY(cudaEventRecord(b.done_ev, b.stream));
+        CGGM_CUDA_TRY(cudaEventSynchronize(b.done_ev));
+    }
+    for (PassBatcher::Entry *e : batch) CGGM_CUDA_TRY(cudaStreamWaitEvent(e->st, b.done_ev, 0));
+    return CGGM_OK;
+}
+
+cggm_status launch_batch(PassBatcher &b, std::vector<PassBatcher::Entry *> &batch) {
+    if (!b.stream) {
+        CGGM_CUDA_TRY(cudaGetDevice(&b.device));
+        CGGM_CUDA_TRY(cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking));
+        CGGM_CUDA_TRY(cudaEventCreateWithFlags(&b.done_ev, cudaEventDisableTiming));
+    }
+    const bool f32 = batch[0]->f32;
+    switch (batch[0]->B) {
+        case 32: return f32 ? launch_multi<float, 1>(b, batch) : launch_multi<double, 1>(b, batch);
+        case 64: return f32 ? launch_multi<float, 2>(b, batch) : launch_multi<double, 2>(b, batch);
+        case 128: return f32 ? launch_multi<float, 4>(b, batch) : launch_multi<double, 4>(b, batch);
+        case 256: return f32 ? launch_multi<float, 8>(b, batch) : CGGM_EINVAL;
+        case 512: return f32 ? launch_multi<float, 16>(b, batch) : CGGM_EINVAL;
+        default: return CGGM_EINVAL;
+    }
+}
+
+// Hand one pass to the batcher and return once it has run (its error word is then read by
+// the caller).  The first thread to find no launch being prepared gathers: it waits until
+// every busy solve has a pass waiting or 200 us have passed, takes the oldest pass and up to
+// seven more of the same precision and batch size, and launches them together.
+cggm_status run_batched(PassBatcher &b, PassBatcher::Entry &e) {
+    CGGM_CUDA_TRY(cudaEventCreateWithFlags(&e.ready, cudaEventDisableTiming));
+    cudaError_t re = cudaEventRecord(e.ready, e.st);
+    if (re != cudaSuccess) {
+        cudaEventDestroy(e.ready);
+        CGGM_CUDA_TRY(re);
+    }
+    std::unique_lock<std::mutex> lk(b.mu);
+    b.pending.push_back(&e);
+    b.cv.notify_all();
+    while (!e.done) {
+        if (b.leader) {
+            b.cv.wait(lk);
+            continue;
+        }
+        b.leader = true;
+        const auto deadline = std::chrono::steady_clock::now() + std::chrono::microseconds(200);
+        while ((int)b.pending.size() < b.busy && std::chrono::steady_clock::now() < deadline)
+            b.cv.wait_until(lk, deadline);
+        std::vector<PassBatcher::Entry *> batch;
+        const PassBatcher::Entry *first = b.pending.front();
+        for (auto it = b.pending.begin(); it != b.pending.end() && (int)batch.size() < kMaxPassGroups;) {
+            if ((*it)->f32 == first->f32 && (*it)->B == first->B) {
+                batch.push_back(*it);
+                it = b.pending.erase(it);
+            } else {
+                ++it;
+            }
+        }
+        lk.unlock();
+        const cggm_status st = launch_batch(b, batch);
+        lk.lock();
+        b.n_launch++;
+        b.n_pass += (int64_t)batch.size();
+        if (batch.size() > 1) b.n_shared++;
+        for (PassBatcher::Entry *x : batch) {
+            x->status = st;
+            x->done = true;
+        }
+        b.leader = false;
+        b.cv.notify_all();
+    }
+    lk.unlock();
+    cudaEventDestroy(e.ready);
+    return e.status;
+}
+
+template <typename T>
+PassDesc<T> &desc_of(PassBatcher::Entry &e);
+template <>
+PassDesc<float> &desc_of<float>(PassBatcher::Entry &e) { return e.df; }
+template <>
+PassDesc<double> &desc_of<double>(PassBatcher::Entry &e) { return e.dd; }
+
+}  // namespace
 
 cggm_status scratch_reserve(SweepScratch &scr) {
     if (scr.mu) return CGGM_OK;
@@ -1095,6 +1421,21 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
         case 256: fn = (const void *)lambda_sweep_kernel<T, 8>; break;
         case 512: fn = (const void *)lambda_sweep_kernel<float, 16>; break;
         default: return CGGM_EINVAL;
+    }
+    if (scr.batcher) {
+        PassBatcher::Entry e;
+        e.f32 = sizeof(T) == 4;
+        e.B = B;
+        e.st = st;
+        PassDesc<T> &d = desc_of<T>(e);
+        d = PassDesc<T>{};
+        d.kind = 0;
+        d.q = q; d.m = m;
+        d.Sig = Sigma; d.Psi = Psi; d.Sd = Sd; d.Pd = Pd; d.G = G; d.Lam = Lambda;
+        d.ia = ai; d.ja = aj; d.lam_off = lam_off; d.lam_diag = lam_diag;
+        d.out = D; d.cache = U; d.scr = scr;
+        CGGM_TRY(run_batched(*scr.batcher, e));
+        return read_err(scr.err, st);
     }
     std::lock_guard<std::mutex> lock(coop_mutex());
     CGGM_TRY(launch_coop<T>(fn, args, smem, st));
@@ -1148,6 +1489,21 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, int64_t x0, const do
         case 256: fn = (const void *)theta_sweep_kernel<T, 8>; break;
         case 512: fn = (const void *)theta_sweep_kernel<float, 16>; break;
         default: return CGGM_EINVAL;
+    }
+    if (scr.batcher) {
+        PassBatcher::Entry e;
+        e.f32 = sizeof(T) == 4;
+        e.B = B;
+        e.st = st;
+        PassDesc<T> &d = desc_of<T>(e);
+        d = PassDesc<T>{};
+        d.kind = 1;
+        d.p = p; d.q = q; d.m = m; d.x0 = x0;
+        d.Sxx = Sxx; d.Xd = Xd; d.Sig = Sigma; d.Sd = Sd; d.W = W;
+        d.ia = ti; d.ja = tj; d.lam_off = lam;
+        d.out = Theta; d.cache = dV; d.scr = scr;
+        CGGM_TRY(run_batched(*scr.batcher, e));
+        return read_err(scr.err, st);
     }
     std::lock_guard<std::mutex> lock(coop_mutex());
     CGGM_TRY(launch_coop<T>(fn, args, smem, st));

@@ -5,6 +5,8 @@
 
 namespace cggm {
 
+struct PassBatcher;
+
 // Device scratch shared by the sweep kernels (sized for the largest B).
 struct SweepScratch {
     double *mu = nullptr;  // [B] the batch's steps
@@ -13,7 +15,26 @@ struct SweepScratch {
                            // [B][B] cross coefficients, [B] corrections (T)
     GridBarrier *bar = nullptr;
     int *err = nullptr;
+    // host: when set, the passes of this context are handed to the batcher, which runs the
+    // passes of concurrent solves together in one cooperative launch
+    PassBatcher *batcher = nullptr;
 };
+
+// Several coordinate passes of concurrent solves in one cooperative launch: the grid is cut
+// into groups of CTAs, one per pass, each running its pass on its own scratch and barrier
+// (results do not depend on the group's size).  Passes handed over by
+// lambda_sweep/theta_sweep of contexts that share a batcher are collected for a short
+// window - until every solve the batcher serves has one waiting, or 200 us - and launched
+// together (passes of one precision and batch size per launch, at most 8).
+PassBatcher *batcher_create();
+void batcher_destroy(PassBatcher *b);
+// solves in progress that may hand over passes (the gathering window ends early once as
+// many passes wait)
+void batcher_add_busy(PassBatcher *b, int delta);
+// launches, passes launched, and launches that held more than one pass (statistics)
+void batcher_counts(PassBatcher *b, int64_t *launches, int64_t *passes, int64_t *shared);
+// route the passes of a context's solves through a batcher (nullptr: launch them alone)
+void ctx_set_batcher(cggm_ctx *c, PassBatcher *b);
 
 // Lambda direction: one pass over (ai, aj), ai <= aj.  Sigma, Psi (q x q, T) with
 // double diagonals Sd, Pd; G = S_yy - Sigma - Psi (double); Lambda (double).
