@@ -539,6 +539,82 @@ def run_gap_trace(args):
     print(json.dumps(out), flush=True)
 
 
+def run_large(args):
+    """The 40000-input, 20000-output workload (n = 500, random degree-4 Lambda, Theta with 20
+    nonzeros per column, X standardised genotypes stored in bf16, lambda 0.1) end to end in the
+    mixed path: K Newton iterations from Lambda = I, Theta = 0 through cggm_solve_dense with
+    inputs and outputs in device memory, then a KKT check of the returned point from
+    cggm_grad (double precision): the min-norm subgradient of every Lambda entry and of a
+    random sample of 10^6 Theta entries (Section 5.1's stopping quantity, entry by entry)."""
+    import numpy as np
+    import torch
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    import synth
+    t0 = time.perf_counter()
+    pr = synth.workload("rand4-geno-p40000-q20000-n500")
+    t_gen = time.perf_counter() - t0
+    n, p = pr.X.shape
+    q = pr.Y.shape[1]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    Xd = torch.from_numpy(pr.X).to(dev).to(torch.bfloat16)
+    Yd = torch.from_numpy(pr.Y.astype(np.float32)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cg.Context(0, stream=stream.cuda_stream)
+    L = torch.empty((q, q), device=dev, dtype=torch.float64)
+    T = torch.empty((p, q), device=dev, dtype=torch.float64)
+    with Clocks(0) as clk:
+        r = ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=0.01,
+                                 opts=cg.make_opts(precision=cg.CGGM_MIXED, max_iter=args.large),
+                                 Lambda_out=L, Theta_out=T)
+    info = r.info
+    it = max(1, info["iterations"])
+    f = ctx.cggm_objective(Xd, Yd, L, T, pr.lam_L, pr.lam_T)
+    # KKT residual of the returned point (the checks use torch on the device; the gradients
+    # come from the library)
+    GL = torch.empty((q, q), device=dev, dtype=torch.float64)
+    GT = torch.empty((p, q), device=dev, dtype=torch.float64)
+    lib = cg.cggm._lib()
+    Xa = cg.cggm._Arr(Xd, "bf16")
+    st = lib.cggm_grad(ctx._h, Xa.ptr, cg.CGGM_BF16, Yd.data_ptr(), cg.CGGM_F32, n, p, q,
+                       L.data_ptr(), T.data_ptr(), GL.data_ptr(), GT.data_ptr())
+    assert st == 0, st
+    torch.cuda.synchronize()
+
+    def subgrad(G, P, lam):
+        nz = P != 0
+        s_nz = (G + lam * torch.sign(P)).abs()
+        s_z = torch.clamp(G.abs() - lam, min=0.0)
+        return torch.where(nz, s_nz, s_z)
+
+    sl = subgrad(GL, L, pr.lam_L)
+    g = torch.Generator(device=dev).manual_seed(0)
+    idx = torch.randint(0, p * q, (1_000_000,), device=dev, generator=g)
+    st_ = subgrad(GT.reshape(-1)[idx], T.reshape(-1)[idx], pr.lam_T)
+    ratio = (sl.sum() + st_.sum() * (p * q / idx.numel())) / (L.abs().sum() + T.abs().sum())
+    out = {"large": {
+        "workload": "rand4-geno-p40000-q20000-n500", "p": p, "q": q, "n": n,
+        "lambda": pr.lam_L, "x": "standardised genotypes in bf16", "y": "fp32",
+        "precision": "mixed", "iterations": info["iterations"], "status": r.status,
+        "seconds": info["seconds"], "seconds_per_iteration": info["seconds"] / it,
+        "per_iteration": {k: info[k] / it for k in ("sec_products", "sec_active",
+                                                      "sec_sweep_lambda", "sec_linesearch",
+                                                      "sec_sweep_theta")},
+        "ls_trials": info["ls_trials"], "m_lambda_last": info["m_lambda"],
+        "m_theta_last": info["m_theta"], "f": f,
+        "subgrad_ratio_at_last_check": info["subgrad"] / max(1e-300, info["l1norm"]),
+        "kkt": {"lambda_max_subgrad": float(sl.max()), "lambda_subgrad_l1": float(sl.sum()),
+                "theta_sample": int(idx.numel()),
+                "theta_sample_max_subgrad": float(st_.max()),
+                "ratio_estimate": float(ratio)},
+        "nnz_lambda": int((L != 0).sum()), "nnz_theta": int((T != 0).sum()),
+        "generate_s": t_gen, "clocks": clk.summary(), "gpu_launches": info["launches"]}}
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_cuda(args):
     import numpy as np
     import torch
@@ -675,6 +751,9 @@ def main():
                     help="seconds of device time per precision: record f against time on the "
                          "5000 x 5000 workload instead of the default line")
     ap.add_argument("--gap-chunk", type=int, default=10)
+    ap.add_argument("--large", type=int, default=0,
+                    help="Newton iterations on the 40000 x 20000 workload instead of the "
+                         "default line")
     ap.add_argument("--serve", action="store_true",
                     help="served lambda paths (Poisson arrivals) instead of the default line")
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -693,6 +772,8 @@ def main():
         run_profile_contract(args)
     elif args.gap_trace > 0:
         run_gap_trace(args)
+    elif args.large > 0:
+        run_large(args)
     elif args.serve:
         run_serve(args)
     elif args.impl == "reference":

@@ -227,7 +227,8 @@ cggm_status cggm_lambda_sweep(cggm_ctx *ctx, int64_t q, const double *Sigma,
 /* One coordinate-descent pass on Theta with Lambda fixed (Section 3.2, Eq. 8; Appendix
  * A.1 coordinate step with curvature 2 Sigma_jj (S_xx)_ii).  X is n x p (double), S_xy
  * p x q, Sigma q x q, all row-major; (ti[k], tj[k]), k < m, the active coordinates in
- * visiting order.  Theta (p x q) is read from Theta_in and the result written to
+ * visiting order, any order (a list in ascending rows, as the active sets are, runs
+ * fastest).  Theta (p x q) is read from Theta_in and the result written to
  * Theta_out (may alias).  precision as for cggm_lambda_sweep.  All buffers host or
  * device, owned by the caller.  Errors: CGGM_EINVAL for sizes <= 0, m < 0, a null
  * pointer, another precision, or an index outside 0 <= ti < p, 0 <= tj < q (checked on

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "cg.cuh"
@@ -1237,6 +1238,7 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
     const size_t qq = (size_t)q * q, pq = (size_t)p * q;
     const int64_t esz = precision == CGGM_FP64 ? 8 : 4;
     const int64_t R = sxx_chunk_rows(p, esz);
+    const bool sorted = std::is_sorted(rows_h.begin(), rows_h.end());
     CGGM_TRY(load_transposed(c, X, CGGM_F64, n, p, c->Xt, nullptr));
     CGGM_TRY(ensure(c->Sxx, (size_t)esz * (size_t)R * p));
     CGGM_TRY(ensure(c->Xd, 8 * (size_t)p));
@@ -1289,14 +1291,14 @@ cggm_status cggm_theta_sweep(cggm_ctx *c, int64_t n, int64_t p, int64_t q, const
             CGGM_TRY(theta_sweep<double>(p, q, P<double>(c->Sxx), x0, P<double>(c->Xd),
                                          P<double>(c->Sig), P<double>(c->Sd), P<double>(c->W),
                                          P<double>(c->Th), k1 - k0, ri, rj, lam_T,
-                                         P<double>(c->dV), 128, c->scr, c->st));
+                                         P<double>(c->dV), 128, c->scr, c->st, sorted));
         } else {
             gemm<float>(false, true, rows, p, n, (float)inv, P<float>(c->Xt_f) + x0 * n, n,
                         P<float>(c->Xt_f), n, 0.0f, P<float>(c->Sxx), p, c->st);
             CGGM_TRY(theta_sweep<float>(p, q, P<float>(c->Sxx), x0, P<double>(c->Xd),
                                         P<float>(c->Sig_f), P<double>(c->Sd), P<double>(c->W),
                                         P<double>(c->Th), k1 - k0, ri, rj, lam_T,
-                                        P<float>(c->dV), 256, c->scr, c->st));
+                                        P<float>(c->dV), 256, c->scr, c->st, sorted));
         }
         k0 = k1;
     }

@@ -856,7 +856,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
            const double *__restrict__ Xd, const T *__restrict__ Sig,
            const double *__restrict__ Sd, const double *__restrict__ W, double *Theta, int64_t m,
            const int32_t *__restrict__ ti, const int32_t *__restrict__ tj, double lam, T *dVt,
-           int B_arg, SweepScratch scr, unsigned bid, unsigned nblk) {
+           int B_arg, SweepScratch scr, bool rows_sorted, unsigned bid, unsigned nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 2];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
@@ -889,9 +889,10 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
                        int nbp, int rank0) {
         const int nA = (int)nblk - rank0, rank = (int)bid - rank0;
-        // rows of Delta V that can be nonzero: those at or before this batch's first row
-        // (the ring copies whole 16-byte words: entries beyond tmax are zero)
-        const int64_t tmax = (int64_t)bm.sa[0] + 1;
+        // rows of Delta V that can be nonzero: with the list in ascending rows, those at or
+        // before this batch's first row (the ring copies whole 16-byte words: entries beyond
+        // tmax are zero); all p rows otherwise
+        const int64_t tmax = rows_sorted ? (int64_t)bm.sa[0] + 1 : p;
         const int64_t tlen = ((tmax + VN - 1) / VN) * VN < p ? ((tmax + VN - 1) / VN) * VN : p;
         const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
         const int64_t nt = (int64_t)nA * blockDim.x;
@@ -1139,15 +1140,16 @@ theta_sweep_kernel(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                    const double *__restrict__ Xd, const T *__restrict__ Sig,
                    const double *__restrict__ Sd, const double *__restrict__ W, double *Theta,
                    int64_t m, const int32_t *__restrict__ ti, const int32_t *__restrict__ tj,
-                   double lam, T *dVt, int B_arg, SweepScratch scr) {
+                   double lam, T *dVt, int B_arg, SweepScratch scr, int rows_sorted) {
     theta_pass<T, NS>(p, q, Sxx, x0, Xd, Sig, Sd, W, Theta, m, ti, tj, lam, dVt, B_arg, scr,
-                      blockIdx.x, gridDim.x);
+                      rows_sorted != 0, blockIdx.x, gridDim.x);
 }
 
 // One pass of a multi-pass launch: its kind, its group of CTAs and its arguments.
 template <typename T>
 struct PassDesc {
     int kind;  // 0: Lambda pass, 1: Theta pass
+    int rows_sorted;  // Theta pass: the list is in ascending rows
     unsigned cta0, ncta;
     int64_t p, q, m, x0;
     const T *Sig, *Psi, *Sxx;
@@ -1177,7 +1179,7 @@ multi_pass_kernel(const __grid_constant__ MultiPass<T> mp) {
                            d.lam_diag, d.out, d.cache, NS * 32, d.scr, bid, d.ncta);
     else
         theta_pass<T, NS>(d.p, d.q, d.Sxx, d.x0, d.Xd, d.Sig, d.Sd, d.W, d.out, d.m, d.ia, d.ja,
-                          d.lam_off, d.cache, NS * 32, d.scr, bid, d.ncta);
+                          d.lam_off, d.cache, NS * 32, d.scr, d.rows_sorted != 0, bid, d.ncta);
 }
 
 // A persistent pass needs every SM at once; two of them issued from different host threads
@@ -1471,16 +1473,18 @@ template <typename T>
 cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, int64_t x0, const double *Xd,
                         const T *Sigma, const double *Sd, const double *W, double *Theta,
                         int64_t m, const int32_t *ti, const int32_t *tj, double lam, T *dV,
-                        int B, SweepScratch &scr, cudaStream_t st) {
+                        int B, SweepScratch &scr, cudaStream_t st, bool rows_sorted) {
     if (m <= 0) return CGGM_OK;
     if (B < 32 || B > (sizeof(T) == 4 ? 512 : 128) || (B & (B - 1))) return CGGM_EINVAL;
     CGGM_TRY(scratch_reserve(scr));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.err, 0, sizeof(int), st));
     CGGM_CUDA_TRY(cudaMemsetAsync(scr.bar, 0, sizeof(GridBarrier), st));
     const size_t smem = smem_layout<T>(B).total;
+    int sorted_arg = rows_sorted ? 1 : 0;
     void *args[] = {(void *)&p, (void *)&q, (void *)&Sxx, (void *)&x0, (void *)&Xd, (void *)&Sigma,
                     (void *)&Sd, (void *)&W, (void *)&Theta, (void *)&m, (void *)&ti,
-                    (void *)&tj, (void *)&lam, (void *)&dV, (void *)&B, (void *)&scr};
+                    (void *)&tj, (void *)&lam, (void *)&dV, (void *)&B, (void *)&scr,
+                    (void *)&sorted_arg};
     const void *fn;
     switch (B) {
         case 32: fn = (const void *)theta_sweep_kernel<T, 1>; break;
@@ -1498,6 +1502,7 @@ cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, int64_t x0, const do
         PassDesc<T> &d = desc_of<T>(e);
         d = PassDesc<T>{};
         d.kind = 1;
+        d.rows_sorted = rows_sorted ? 1 : 0;
         d.p = p; d.q = q; d.m = m; d.x0 = x0;
         d.Sxx = Sxx; d.Xd = Xd; d.Sig = Sigma; d.Sd = Sd; d.W = W;
         d.ia = ti; d.ja = tj; d.lam_off = lam;
@@ -1522,10 +1527,10 @@ template cggm_status theta_sweep<double>(int64_t, int64_t, const double *, int64
                                          const double *, const double *, const double *,
                                          const double *, double *, int64_t, const int32_t *,
                                          const int32_t *, double, double *, int, SweepScratch &,
-                                         cudaStream_t);
+                                         cudaStream_t, bool);
 template cggm_status theta_sweep<float>(int64_t, int64_t, const float *, int64_t, const double *,
                                         const float *, const double *, const double *, double *,
                                         int64_t, const int32_t *, const int32_t *, double, float *,
-                                        int, SweepScratch &, cudaStream_t);
+                                        int, SweepScratch &, cudaStream_t, bool);
 
 }  // namespace cggm

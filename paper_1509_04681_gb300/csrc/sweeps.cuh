@@ -46,7 +46,9 @@ cggm_status lambda_sweep(int64_t q, const T *Sigma, const T *Psi, const double *
                          double *D, T *U, int B, SweepScratch &scr,
                          cudaStream_t st);
 
-// Theta pass: coordinates (ti, tj) row-major.  Sxx: rows x0 .. x0 + k - 1 of S_xx (k x p,
+// Theta pass: coordinates (ti, tj) in visiting order; rows_sorted: they are in ascending
+// rows (the active sets are), so that the dot products stop at the rows Delta V can hold
+// yet.  Sxx: rows x0 .. x0 + k - 1 of S_xx (k x p,
 // T), holding every row i that the coordinates name; Xd the double diagonal of S_xx;
 // Sigma (q x q, T) with double diagonal Sd, W = S_xy + S_xx Theta Sigma at entry
 // (double p x q), Theta (double p x q) updated in place.  dV (T, p x q): Delta V of the
@@ -56,7 +58,7 @@ template <typename T>
 cggm_status theta_sweep(int64_t p, int64_t q, const T *Sxx, int64_t x0, const double *Xd,
                         const T *Sigma, const double *Sd, const double *W, double *Theta,
                         int64_t m, const int32_t *ti, const int32_t *tj, double lam, T *dV,
-                        int B, SweepScratch &scr, cudaStream_t st);
+                        int B, SweepScratch &scr, cudaStream_t st, bool rows_sorted = true);
 
 // Rows of S_xx (p x p, element size esz) that the Theta pass holds at once: all p when they
 // fit in 256 MiB, otherwise as many as fit (at least one).  S_xx is formed from X in chunks
