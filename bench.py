@@ -356,24 +356,23 @@ def run_profile_contract(args):
                                            "c_abs_sum": float(C.abs().sum())}}))
 
 
-def run_serve(args):
-    """Served regularisation paths: requests of uneven size arriving as a Poisson process
-    (20 per second), each an 8-point lambda grid from 0.5 down to 0.02 solved with warm
-    starts, admitted by device-memory footprint into `slots` concurrent workers.  Prints
-    lambda-path solves per second over the makespan and p50 / p99 latency (arrival to the
-    last lambda point)."""
+def serve_measure(n_requests, scale, slots, max_iter, rate=20.0):
+    """Served regularisation paths: n_requests requests of uneven size (p, q, n log-uniform in
+    [500, 8000], [200, 4000], [200, 1000], each divided by `scale`) arriving as a Poisson
+    process (`rate` per second), each an 8-point lambda grid from 0.5 down to 0.02 solved with
+    warm starts (tol 0.01, at most max_iter Newton iterations per point), admitted by
+    device-memory footprint into `slots` concurrent workers whose coordinate passes share
+    cooperative launches.  Returns lambda-point solves per second over the makespan and p50 /
+    p99 latency (arrival to the last lambda point)."""
     import numpy as np
     import paper_1509_04681_gb300 as cg
-    from paper_1509_04681_gb300 import build as pkg_build
-    pkg_build.build()
     import synth
-    scale = args.serve_scale
-    reqs = synth.serving_requests(n_req=args.serve_requests, rate_per_s=20.0, seed=0,
-                                  p_range=(int(500 / scale), int(8000 / scale)),
-                                  q_range=(int(200 / scale), int(4000 / scale)),
-                                  n_range=(int(200 / scale), int(1000 / scale)))
+    lo = lambda v: max(1, int(v / scale))  # noqa: E731
+    reqs = synth.serving_requests(n_req=n_requests, rate_per_s=rate, seed=0,
+                                  p_range=(lo(500), lo(8000)), q_range=(lo(200), lo(4000)),
+                                  n_range=(lo(200), lo(1000)))
     probs = [(r, r.problem()) for r in reqs]
-    with cg.Server(0, slots=args.serve_slots) as srv:
+    with cg.Server(0, slots=slots) as srv:
         t0 = time.perf_counter()
         ids = []
         for r, pr in probs:
@@ -381,23 +380,31 @@ def run_serve(args):
             if wait > 0:
                 time.sleep(wait)
             ids.append(srv.submit(pr.X.astype(np.float32), pr.Y.astype(np.float32), r.lambdas,
-                                  tol=0.01, max_iter=args.serve_max_iter,
-                                  precision=cg.CGGM_MIXED, want_outputs=False))
+                                  tol=0.01, max_iter=max_iter, precision=cg.CGGM_MIXED,
+                                  want_outputs=False))
         res = [srv.poll(i, wait=True) for i in ids]
         makespan = time.perf_counter() - t0
+        stats = srv.stats()
     lat = sorted(r["finish_s"] - r["arrival_s"] for r in res)
     pts = sum(len(r.lambdas) for r, _ in probs)
-    line = {"metric": METRIC, "serving": {
-        "value": pts / makespan, "unit": "lambda-point solves/s",
-        "requests": len(res), "lambda_points": pts, "makespan_s": makespan,
-        "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-        "slots": args.serve_slots, "statuses": sorted(set(r["status"] for r in res)),
-        "iterations": sum(r["iterations"] for r in res),
-        "workload": (f"{len(res)} requests, sizes log-uniform p in [{int(500/scale)}, "
-                     f"{int(8000/scale)}], q in [{int(200/scale)}, {int(4000/scale)}], n in "
-                     f"[{int(200/scale)}, {int(1000/scale)}]; 8-point grid 0.5 -> 0.02; Poisson "
-                     f"arrivals 20/s; tol 0.01, at most {args.serve_max_iter} iterations per point; "
-                     f"mixed precision")}}
+    return {"value": pts / makespan, "unit": "lambda-point solves/s", "requests": len(res),
+            "lambda_points": pts, "makespan_s": makespan,
+            "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "slots": slots,
+            "statuses": sorted(set(r["status"] for r in res)),
+            "iterations": sum(r["iterations"] for r in res), "pass_batching": stats,
+            "workload": (f"{len(res)} requests, sizes log-uniform p in [{lo(500)}, {lo(8000)}], "
+                         f"q in [{lo(200)}, {lo(4000)}], n in [{lo(200)}, {lo(1000)}]; 8-point "
+                         f"grid 0.5 -> 0.02 with warm starts; Poisson arrivals {rate:g}/s; tol "
+                         f"0.01, at most {max_iter} Newton iterations per point; mixed precision")}
+
+
+def run_serve(args):
+    """Served regularisation paths alone (one JSON line with the "serving" object)."""
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    line = {"metric": METRIC, "serving": serve_measure(args.serve_requests, args.serve_scale,
+                                                       args.serve_slots, args.serve_max_iter)}
     print(json.dumps(line), flush=True)
 
 
@@ -723,6 +730,13 @@ def run_cuda(args):
     if rank == 0 and world == 1 and not args.no_fp64:
         line["fp64"] = fp64_leg(ctx, cg, Xd, Yd, pr, p, q, dev, min(args.steps, 5), 3)
         line["mixed_over_fp64_iterations_per_s"] = value / line["fp64"]["value"]
+    if rank == 0 and world == 1 and not args.no_serve:
+        sv = serve_measure(args.line_serve_requests, 1.0, args.serve_slots,
+                           args.line_serve_max_iter)
+        sv["trimmed"] = (f"{args.line_serve_requests} of the 64 requests of the served "
+                         f"workload, at most {args.line_serve_max_iter} iterations per lambda "
+                         f"point, to keep the benchmark within minutes; request sizes in full")
+        line["serving"] = sv
     if rank == 0 and world == 1 and not args.no_ttg:
         small = synth.workload(SMALL)
         line["time_to_gap"] = time_to_gap(ctx, cg, small, torch)
@@ -757,10 +771,14 @@ def main():
     ap.add_argument("--serve", action="store_true",
                     help="served lambda paths (Poisson arrivals) instead of the default line")
     ap.add_argument("--serve-requests", type=int, default=64)
-    ap.add_argument("--serve-scale", type=float, default=4.0,
+    ap.add_argument("--serve-scale", type=float, default=1.0,
                     help="divide the request size ranges by this factor")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-max-iter", type=int, default=100)
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--line-serve-requests", type=int, default=16,
+                    help="served requests measured within the default line")
+    ap.add_argument("--line-serve-max-iter", type=int, default=25)
     ap.add_argument("--profile-sweep", action="store_true",
                     help="run only a bounded Lambda pass at q=5000 (for ncu captures)")
     ap.add_argument("--profile-contract", action="store_true",

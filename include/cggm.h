@@ -178,6 +178,23 @@ cggm_status cggm_solve_dense(cggm_ctx *ctx, const void *X, int xdtype, const voi
                              double *Lambda_out, double *Theta_out, cggm_info *info);
 
 /*
+ * Prediction with a fitted model (Section 2.1): given x, y is Gaussian with mean
+ * -Lambda^-1 Theta^T x, so the rows of X (n x p, dtype xdtype, host or device; genotype
+ * counts are standardised as in cggm_solve) predict Yhat = X B with the regression
+ * coefficients B = -Theta Sigma, Sigma = Lambda^-1.  Lambda (upper triangle) and Theta are
+ * coordinate lists as cggm_solve returns them (host or device arrays).
+ *   Yhat_out: n x q row-major double, B_out: p x q row-major double (host or device); either
+ *   may be NULL, not both.  Double precision throughout (Cholesky of Lambda, Sigma, the
+ *   product over Theta's nonzeros).
+ * Errors: CGGM_EINVAL (sizes, a NULL pointer, an index outside its matrix or below the
+ * diagonal of Lambda), CGGM_ENONFINITE (a non-finite value), CGGM_ENOTPD (Lambda not
+ * positive definite).
+ */
+cggm_status cggm_predict(cggm_ctx *ctx, const void *X, int xdtype, int64_t n, int64_t p,
+                         int64_t q, const cggm_coo *Lambda, const cggm_coo *Theta,
+                         double *Yhat_out, double *B_out);
+
+/*
  * f(Lambda, Theta) of Eq. 1 in double precision on the device.  Lambda must be positive
  * definite (CGGM_ENOTPD otherwise).  penalize_diag as in cggm_opts.
  */

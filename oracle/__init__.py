@@ -33,6 +33,7 @@ from .cggm_oracle import (  # noqa: F401
     solve,
     soft_threshold,
     spd_solve,
+    predict,
 )
 from . import blocks  # noqa: F401,E402
 from . import symbolic  # noqa: F401,E402

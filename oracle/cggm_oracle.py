@@ -291,3 +291,13 @@ def solve(X, Y, lam_L, lam_T, tol=0.01, max_iter=100, Lambda0=None, Theta0=None,
             callback(rec, Lam, Th)
     return SolveResult(Lambda=Lam, Theta=Th, f=f, iterations=len(hist), converged=converged,
                        history=hist)
+
+
+def predict(X, Lam, Theta):
+    """Conditional mean of the outputs given the inputs (Section 2.1): y | x has mean
+    -Lambda^-1 Theta^T x, so the n rows of X predict Yhat = X B with the regression
+    coefficients B = -Theta Sigma, Sigma = Lambda^-1.  Returns (Yhat, B)."""
+    Lam = np.asarray(Lam, dtype=np.float64)
+    _chol(Lam)  # positive definite, or NotPositiveDefinite
+    B = -np.asarray(Theta, dtype=np.float64) @ np.linalg.inv(Lam)
+    return np.asarray(X, dtype=np.float64) @ B, B

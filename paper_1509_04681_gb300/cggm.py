@@ -29,7 +29,7 @@ CGGM_ORDER_NATURAL, CGGM_ORDER_RCM, CGGM_ORDER_GIVEN, CGGM_ORDER_MINDEG, CGGM_OR
 
 EXPORTED = [
     "cggm_create", "cggm_destroy", "cggm_opts_default", "cggm_status_string", "cggm_solve",
-    "cggm_solve_dense", "cggm_free_coo", "cggm_server_stats",
+    "cggm_solve_dense", "cggm_free_coo", "cggm_server_stats", "cggm_predict",
     "cggm_objective", "cggm_grad", "cggm_cholesky", "cggm_lambda_sweep", "cggm_theta_sweep",
     "cggm_active_sets", "cggm_lambda_sweep_noalloc", "cggm_contract", "cggm_server_create",
     "cggm_server_submit", "cggm_server_poll", "cggm_server_destroy", "cggm_footprint",
@@ -119,6 +119,7 @@ def _lib():
                                          ctypes.POINTER(cggm_info)]
         lib.cggm_free_coo.argtypes = [coo_p]
         lib.cggm_free_coo.restype = None
+        lib.cggm_predict.argtypes = [vp, vp, ip, i64, i64, i64, coo_p, coo_p, vp, vp]
         lib.cggm_objective.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, dbl, dbl, ip,
                                        ctypes.POINTER(dbl)]
         lib.cggm_grad.argtypes = [vp, vp, ip, vp, ip, i64, i64, i64, vp, vp, vp, vp]
@@ -181,7 +182,7 @@ def _lib():
                                                      "cggm_tuner_save", "cggm_tuner_load",
                                                      "cggm_block_count",
                                                      "cggm_server_submit", "cggm_server_poll",
-                                                     "cggm_server_stats"):
+                                                     "cggm_server_stats", "cggm_predict"):
                 f.restype = ctypes.c_int
         _LIB = lib
     return _LIB
@@ -378,6 +379,24 @@ class Context:
         return SolveResult(Lambda=La.obj if Lambda_out is None else Lambda_out,
                            Theta=Ta.obj if Theta_out is None else Theta_out,
                            info=info.as_dict(), status=st)
+
+    def cggm_predict(self, X, Lam, Th, q=None, want_B=True):
+        """cggm_predict: Yhat = X B with B = -Theta Lambda^-1.  Lam (upper triangle used) and
+        Th: (row, col, val) triples (then q is required) or dense host matrices.  Returns
+        (Yhat, B or None)."""
+        n, p = X.shape
+        xd, xt = _x_dtype(X)
+        Xa = _Arr(X, xd)
+        if q is None:
+            q = Lam.shape[0]
+        L = _CooIn(Lam, True)
+        T = _CooIn(Th, False)
+        Yh = np.empty((n, q))
+        B = np.empty((p, q)) if want_B else None
+        _check(_lib().cggm_predict(self._h, Xa.ptr, xt, n, p, q, ctypes.byref(L.coo),
+                                   ctypes.byref(T.coo), Yh.ctypes.data,
+                                   B.ctypes.data if B is not None else None), "cggm_predict")
+        return Yh, B
 
     def cggm_objective(self, X, Y, Lam, Th, lam_L, lam_T, penalize_diag=True) -> float:
         n, p = X.shape

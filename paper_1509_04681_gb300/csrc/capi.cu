@@ -1033,6 +1033,49 @@ cggm_status cggm_solve(cggm_ctx *c, const void *X, int xdtype, const void *Y, in
     return conv ? CGGM_OK : CGGM_EMAXITER;
 }
 
+cggm_status cggm_predict(cggm_ctx *c, const void *X, int xdtype, int64_t n, int64_t p,
+                         int64_t q, const cggm_coo *Lambda, const cggm_coo *Theta,
+                         double *Yhat_out, double *B_out) {
+    if (!c || !X || !Lambda || !Theta || (!Yhat_out && !B_out)) return CGGM_EINVAL;
+    if (!dtypes_ok(xdtype, CGGM_F64)) return CGGM_EINVAL;
+    CGGM_TRY(check_sizes(n, p, q));
+    CGGM_TRY(set_device(c));
+    const size_t qq = (size_t)q * q, pq = (size_t)p * q, qn = (size_t)q * n;
+    CGGM_TRY(ensure(c->err, sizeof(int)));
+    CGGM_TRY(ensure(c->scal, 8 * S_COUNT));
+    CGGM_TRY(ensure(c->Lam, 8 * qq));
+    CGGM_TRY(ensure(c->Lch, 8 * qq));
+    CGGM_TRY(ensure(c->logd, 8 * (size_t)q));
+    CGGM_TRY(ensure(c->Sig, 8 * qq));
+    CGGM_TRY(ensure(c->work, 8 * qq));
+    CGGM_TRY(ensure(c->Th, 8 * pq));
+    CGGM_TRY(coo_in(c, Lambda, q, q, true, P<double>(c->Lam)));
+    CGGM_TRY(coo_in(c, Theta, p, q, false, P<double>(c->Th)));
+    cggm_opts o;
+    cggm_opts_default(&o);
+    Solver<double> S{c, {n, p, q}, c->st, 0.0, 0.0, 0.0, o};
+    CGGM_TRY(S.factor(c->Lam, c->Lch, c->logd, S_LOGDET));  // CGGM_ENOTPD if not PD
+    inverse_from_cholesky(q, P<double>(c->Lch), P<double>(c->Sig), P<double>(c->work), c->st);
+    if (B_out) {  // B = -Theta Sigma (p x q)
+        CGGM_TRY(ensure(c->W, 8 * pq));
+        gemm<double>(false, false, p, q, q, -1.0, P<double>(c->Th), q, P<double>(c->Sig), q, 0.0,
+                     P<double>(c->W), q, c->st);
+        CGGM_TRY(store_double(c, B_out, c->W.p, pq));
+    }
+    if (Yhat_out) {  // Yhat^T = -Sigma Theta^T X^T (q x n), R^T over Theta's nonzeros
+        CGGM_TRY(load_transposed(c, X, xdtype, n, p, c->Xt, nullptr));
+        CGGM_TRY(ensure(c->Rt, 8 * qn));
+        CGGM_TRY(ensure(c->Pt, 8 * qn));
+        CGGM_TRY(ensure(c->Z, 8 * qn));
+        theta_t_xt(p, q, n, P<double>(c->Th), P<double>(c->Xt), P<double>(c->Rt), c->st);
+        gemm<double>(false, false, q, n, q, -1.0, P<double>(c->Sig), q, P<double>(c->Rt), n, 0.0,
+                     P<double>(c->Pt), n, c->st);
+        transpose<double, double>(q, n, P<double>(c->Pt), P<double>(c->Z), c->st);
+        CGGM_TRY(store_double(c, Yhat_out, c->Z.p, qn));
+    }
+    return sync_err(c);
+}
+
 cggm_status cggm_objective(cggm_ctx *c, const void *X, int xdtype, const void *Y, int ydtype,
                            int64_t n, int64_t p, int64_t q, const double *Lambda,
                            const double *Theta, double lam_L, double lam_T, int penalize_diag,

@@ -339,3 +339,21 @@ def test_spd_solve_closed_forms():
     assert np.all(S * (-1.0) ** (i + j) > 0)
     with pytest.raises(oracle.NotPositiveDefinite):
         oracle.spd_solve(np.array([[1.0, 2.0], [2.0, 1.0]]), np.eye(2))
+
+
+def test_prediction_at_lambda_zero_is_the_least_squares_fit():
+    """Section 2.1's conditional mean at the lambda = 0 optimum: B = -Theta Sigma equals the
+    least-squares coefficients S_xx^-1 S_xy, so the predictions are the ordinary
+    least-squares fit of Y on X (numpy lstsq, a different algorithm).  A sign flip, a
+    transposed Theta or a Lambda in place of Sigma fails it."""
+    X, Y = small_problem(6, 4, 60, seed=3)
+    r = oracle.solve(X, Y, 0.0, 0.0, tol=1e-13, max_iter=20000)
+    Yhat, B = oracle.predict(X, r.Lambda, r.Theta)
+    coef, *_ = np.linalg.lstsq(X, Y, rcond=None)
+    assert np.max(np.abs(B - coef)) < 1e-7 * np.max(np.abs(coef))
+    assert np.max(np.abs(Yhat - X @ coef)) < 1e-7 * np.max(np.abs(Y))
+    # scalar case by hand: Lambda = 2, Theta = 3 -> B = -3/2
+    Yh, B1 = oracle.predict(np.array([[1.0], [-2.0]]), np.array([[2.0]]), np.array([[3.0]]))
+    assert B1[0, 0] == -1.5 and np.allclose(Yh[:, 0], [-1.5, 3.0])
+    with pytest.raises(oracle.NotPositiveDefinite):
+        oracle.predict(X, -np.eye(4), r.Theta)
