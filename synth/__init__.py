@@ -19,4 +19,7 @@ from .problems import (  # noqa: F401
     workload,
     WORKLOADS,
     serving_requests,
+    clustered_precision,
+    clustered_theta,
+    clustered_problem,
 )

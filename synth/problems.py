@@ -154,6 +154,99 @@ def sample_Y(X: np.ndarray, Theta: sp.spmatrix, Lambda: sp.spmatrix,
     return mean + E
 
 
+def clustered_precision(q: int, rng: np.random.Generator, cluster: int = 250,
+                        avg_degree: float = 10.0, intra: float = 0.9,
+                        margin: float = 0.1) -> sp.csr_matrix:
+    """The clustered random network of the paper's second synthetic family (Section 5):
+    outputs in consecutive clusters of ``cluster`` nodes (the last one may be smaller),
+    q * avg_degree / 2 distinct edges of weight 1, a fraction ``intra`` of them between two
+    random nodes of one cluster (the cluster drawn in proportion to its number of node pairs)
+    and the rest between two random nodes anywhere.  The paper sets the diagonal so that
+    Lambda is positive definite; here it is the row's absolute sum plus ``margin`` (strictly
+    diagonally dominant)."""
+    n_edges = int(round(q * avg_degree / 2.0))
+    starts = np.arange(0, q, cluster)
+    sizes = np.minimum(cluster, q - starts)
+    pairs = sizes * (sizes - 1) / 2.0
+    n_pairs_all = q * (q - 1) / 2.0
+    n_intra = min(int(round(intra * n_edges)), int(pairs.sum()))
+    n_inter = min(n_edges - n_intra, int(n_pairs_all - pairs.sum()))
+    seen = set()
+    rows, cols = [], []
+
+    def add(i, j):
+        i, j = (i, j) if i < j else (j, i)
+        if i == j or (i, j) in seen:
+            return False
+        seen.add((i, j))
+        rows.append(i)
+        cols.append(j)
+        return True
+
+    prob = pairs / pairs.sum() if pairs.sum() > 0 else None
+    k = 0
+    while k < n_intra:
+        c = rng.choice(len(sizes), p=prob)
+        a, b = rng.integers(0, sizes[c], size=2)
+        if add(starts[c] + a, starts[c] + b):
+            k += 1
+    cid = np.repeat(np.arange(len(sizes)), sizes)
+    k = 0
+    while k < n_inter:
+        a, b = rng.integers(0, q, size=2)
+        if cid[a] != cid[b] and add(a, b):
+            k += 1
+    r = np.asarray(rows, dtype=np.int64)
+    c = np.asarray(cols, dtype=np.int64)
+    upper = sp.coo_matrix((np.ones(r.size), (r, c)), shape=(q, q))
+    off = (upper + upper.T).tocsr()
+    diag = np.asarray(abs(off).sum(axis=1)).ravel() + margin
+    return (off + sp.diags(diag)).tocsr()
+
+
+def clustered_theta(p: int, q: int, rng: np.random.Generator, inputs: Optional[int] = None,
+                    edges_per_output: int = 10) -> sp.csc_matrix:
+    """Theta of the clustered family (Section 5): min(p, round(100 sqrt(p))) inputs chosen at
+    random have edges to at least one output; edges_per_output * q distinct edges of weight 1
+    in all: one from each chosen input to a random output, the rest from random chosen inputs
+    to random outputs."""
+    total_want = edges_per_output * q
+    k = min(p, int(round(100.0 * math.sqrt(p)))) if inputs is None else min(p, inputs)
+    k = min(k, total_want)  # every chosen input keeps an edge
+    sel = rng.choice(p, size=k, replace=False)
+    total = min(total_want, k * q)
+    seen = set()
+    rows, cols = [], []
+    for i in sel.tolist():
+        j = int(rng.integers(0, q))
+        seen.add((i, j))
+        rows.append(i)
+        cols.append(j)
+    while len(rows) < total:
+        i = int(sel[rng.integers(0, k)])
+        j = int(rng.integers(0, q))
+        if (i, j) in seen:
+            continue
+        seen.add((i, j))
+        rows.append(i)
+        cols.append(j)
+    return sp.csc_matrix((np.ones(len(rows)), (rows, cols)), shape=(p, q))
+
+
+def clustered_problem(p: int, q: int, n: int = 200, lam: float = 0.1, seed: int = 0,
+                      name: Optional[str] = None) -> "Problem":
+    """The paper's random graphs with clustering (Section 5): clustered Lambda, Theta on
+    100 sqrt(p) inputs with 10 q edges, Gaussian inputs X ~ N(0, 1) (the paper does not state
+    their distribution), Y drawn from the CGGM; n = 200 as in the paper."""
+    sx, sl, st, sn = _streams(seed)
+    X = gaussian_X(n, p, sx)
+    Lam = clustered_precision(q, sl)
+    Th = clustered_theta(p, q, st)
+    Y = sample_Y(X, Th, Lam, sn)
+    return Problem(name=name or f"cluster-gauss-p{p}-q{q}-n{n}", X=X, Y=Y, Lambda_true=Lam,
+                   Theta_true=Th, lam_L=lam, lam_T=lam, seed=seed)
+
+
 @dataclasses.dataclass
 class Problem:
     name: str

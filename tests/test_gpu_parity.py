@@ -373,3 +373,15 @@ def test_theta_pass_out_of_row_order(ctx):
     want = oracle.theta_sweep(Sxx, Sxy, Sigma, Th, ti, tj, 0.05)
     got = ctx.cggm_theta_sweep(pr.X, Sxy, Sigma, Th, ti, tj, 0.05, precision=cg.CGGM_FP64)
     assert rel(got, want) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_clustered_network_family_matches_oracle(ctx, prec):
+    """The paper's random graphs with clustering (Section 5: clusters of 250, average degree
+    10, Theta on 100 sqrt(p) inputs with 10 q edges, n = 200) through cggm_solve, by the
+    method's bar against the oracle."""
+    pr = synth.clustered_problem(300, 250, n=200, lam=0.15, seed=2)
+    ref = oracle.solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7, max_iter=3000)
+    r = ctx.cggm_solve(pr.X, pr.Y, pr.lam_L, pr.lam_T, tol=1e-7,
+                       opts=cg.make_opts(precision=prec, max_iter=3000))
+    check_solution(pr, r, ref, ref.f)

@@ -137,3 +137,35 @@ def test_serving_requests():
     assert kinds == {"chain", "random4"}
     # log-uniform: the median size sits near the geometric mean of its range
     assert abs(math.log(np.median([r.p for r in reqs])) - math.log(math.sqrt(125 * 2000))) < 0.3
+
+
+def test_clustered_family_recipe():
+    """The paper's random graphs with clustering (Section 5): clusters of 250, average degree
+    10, 90 % of edges inside clusters, unit weights, Lambda positive definite; Theta with
+    round(100 sqrt(p)) active inputs (at most p) and 10 q unit edges."""
+    import math
+    import scipy.sparse as sp
+    rng = np.random.default_rng(5)
+    q = 1000
+    L = synth.clustered_precision(q, rng)
+    assert (abs(L - L.T) > 0).nnz == 0
+    off = sp.triu(L, k=1).tocoo()
+    assert off.nnz == q * 10 // 2
+    assert np.all(off.data == 1.0)
+    intra = np.mean(off.row // 250 == off.col // 250)
+    assert abs(intra - 0.9) < 0.01
+    deg = np.asarray((L != 0).sum(axis=1)).ravel() - 1
+    assert abs(deg.mean() - 10.0) < 1e-9
+    assert np.linalg.eigvalsh(L.toarray()).min() > 0.09
+    p = 4000
+    T = synth.clustered_theta(p, q, rng)
+    assert T.nnz == 10 * q and np.all(T.data == 1.0)
+    assert np.unique(T.tocoo().row).size == min(p, round(100 * math.sqrt(p)))  # all 4000
+    T2 = synth.clustered_theta(1_000_000, q, rng)   # 100 sqrt(p) = 10^5 > 10 q: capped at 10 q
+    assert T2.nnz == 10 * q and np.unique(T2.tocoo().row).size == 10 * q
+    T3 = synth.clustered_theta(90_000, 5000, rng)   # 30000 chosen inputs, 50000 edges
+    assert T3.nnz == 50_000 and np.unique(T3.tocoo().row).size == 30_000
+    small = synth.clustered_theta(50, 20, rng)   # 100 sqrt(50) > 50: every input may be used
+    assert small.nnz == 200
+    pr = synth.clustered_problem(300, 300, seed=1)
+    assert pr.X.shape == (200, 300) and pr.Y.shape == (200, 300)
