@@ -42,9 +42,12 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kRowsInFlight = 5;
 // Phase A: rows per CTA held at once, chunks in flight, bytes per row and chunk.
 constexpr int kRingRows = 10;
-constexpr int kStages = 3;
 constexpr int kChunkBytes = 4096;
-constexpr size_t kRingBytes = (size_t)kStages * kRingRows * kChunkBytes;
+// The ring takes the whole work area of shared memory (which phase A does not share with
+// the other phases): as many stages of the plan's rows as fit, up to kMaxStages, so that a
+// q = 5000 row set (five chunks per row) is in flight at once.
+constexpr int kMaxStages = 16;
+constexpr size_t kRingBytes = (size_t)200 * 1024;
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
@@ -60,6 +63,7 @@ __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, 
 // the upper branch is taken exactly when vp > -c, the lower one when vm < -c.  A correction
 // sum acc added to b shifts both vp and vm by -acc/a, so they are kept as
 // vp - ai acc, vm - ai acc with ai = 1/a.  Zero curvature (a = 0): vp = vm = -c, ai = 0.
+// They are formed as vp = -b ai - lam ai, vm = lam ai - b ai.
 enum { PRE_VPH, PRE_VPL, PRE_VMH, PRE_VML, PRE_AI, PRE_MC, PRE_N };
 static_assert(PRE_N == kStepConstants, "step constant count");
 
@@ -69,13 +73,18 @@ __device__ __forceinline__ void split(double v, T *hi, T *lo) {
     *lo = (T)(v - (double)*hi);
 }
 
+// The step constants of coordinate l from its correction-free b (base), 1/a (ai) and lam/a
+// (lai); ai and lai depend on Sigma and Psi (or S_xx) entries only, so they are formed
+// before the dot products and only b's few double operations follow them.  curv: a > 0
+// (otherwise the entry goes to zero: vp = vm = -c, ai = 0).
 template <typename T>
-__device__ void step_constants(double base, double a, double c, double lam, T *pre, int B, int l) {
+__device__ void step_constants(double base, double ai, double lai, bool curv, double c, T *pre,
+                               int B, int l) {
     T *o = pre;
-    if (a > 0.0 && isfinite(a)) {
-        const double ai = 1.0 / a;
-        split<T>(-(base + lam) * ai, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
-        split<T>((lam - base) * ai, o + PRE_VMH * B + l, o + PRE_VML * B + l);
+    if (curv) {
+        const double t = base * ai;
+        split<T>(-t - lai, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
+        split<T>(lai - t, o + PRE_VMH * B + l, o + PRE_VML * B + l);
         o[PRE_AI * B + l] = (T)ai;
     } else {  // zero curvature: the entry goes to zero
         split<T>(-c, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
@@ -116,7 +125,7 @@ __host__ __device__ __forceinline__ int panel_off(int s, int B) {
 
 struct SmemLayout {
     size_t meta;  // twice (current and next batch): sa[B], sb[B], sseg[B + 1], nseg (ints)
-    size_t work;  // union: phase A ring of row chunks (kRingBytes);
+    size_t work;  // union: phase A ring of row chunks (kRingBytes, all stages);
                   //        phase B coefficient panels [coef_area(B)], step constants
                   //          [PRE_N][B], corr[B] (T);
                   //        phase C mu[B] (T)
@@ -302,9 +311,9 @@ __device__ __forceinline__ double cta_total(const double *red, int d) {
 
 // ---------------------------------------------------------------------------------
 // Phase A dot products from shared memory.  The rows that one CTA's dot products read
-// (kRingRows at most) are brought into shared memory in column chunks by bulk copies,
-// kStages chunks ahead, so that an SM keeps kStages x rows x kChunkBytes in flight rather
-// than the few loads per thread its warps would have outstanding.
+// (kRingRows at most) are brought into shared memory in column chunks by bulk copies, as
+// many chunks ahead as the ring holds (up to 200 KB in flight per SM), rather than the few
+// loads per thread its warps would have outstanding.
 // ---------------------------------------------------------------------------------
 
 template <typename T, int ND>
@@ -332,13 +341,17 @@ __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
     using VT = typename V16<T>::type;
     constexpr int VN = V16<T>::n;
     const int64_t nch = (len + CW - 1) / CW;
+    // stages of pl.nrows chunks that the ring holds
+    int nst = (int)(kRingBytes / ((size_t)pl.nrows * kChunkBytes));
+    nst = nst > kMaxStages ? kMaxStages : nst;
+    const size_t stage_bytes = (size_t)pl.nrows * kChunkBytes;
     int64_t issued = 0;  // chunks issued (thread 0)
     auto issue = [&](int64_t c) {
-        const int st = (int)(c % kStages);
+        const int st = (int)(c % nst);
         const int64_t c0 = c * CW;
         const int64_t n = (len - c0) < CW ? (len - c0) : CW;
         const uint32_t bytes = (uint32_t)(n * (int64_t)sizeof(T));
-        T *dst = reinterpret_cast<T *>(ring + (size_t)st * kRingRows * kChunkBytes);
+        T *dst = reinterpret_cast<T *>(ring + (size_t)st * stage_bytes);
         mbar_expect_tx(&mb[st], bytes * (uint32_t)pl.nrows);
         for (int r = 0; r < pl.nrows; r++)
             bulk_load(dst + (size_t)r * CW, pl.rows[r] + c0, bytes, &mb[st]);
@@ -353,15 +366,15 @@ __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
     if (threadIdx.x == 0) {
         // the ring was last read (and the rows possibly written) through the generic proxy
         fence_proxy_async();
-        for (; issued < nch && issued < kStages; issued++) issue(issued);
+        for (; issued < nch && issued < nst; issued++) issue(issued);
     }
     mid();
     for (int64_t c = 0; c < nch; c++) {
-        const int st = (int)(c % kStages);
+        const int st = (int)(c % nst);
         const bool ok = mbar_wait(&mb[st], (phase >> st) & 1u, err);
         if (ok) {
             phase ^= 1u << st;
-            const VT *src = reinterpret_cast<const VT *>(ring + (size_t)st * kRingRows * kChunkBytes);
+            const VT *src = reinterpret_cast<const VT *>(ring + (size_t)st * stage_bytes);
             const int64_t c0 = c * CW;
             const int nv = (int)(((len - c0) < CW ? (len - c0) : CW) / VN);
             for (int v = threadIdx.x; v < nv; v += blockDim.x) {
@@ -377,7 +390,7 @@ __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
         if (!__syncthreads_and(ok)) {
             if (threadIdx.x == 0)
                 for (int64_t c2 = ok ? c + 1 : c; c2 < issued; c2++) {
-                    const int s2 = (int)(c2 % kStages);
+                    const int s2 = (int)(c2 % nst);
                     if (!mbar_wait(&mb[s2], (phase >> s2) & 1u, err, false)) break;
                     phase ^= 1u << s2;
                 }
@@ -509,7 +522,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 6];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
-    __shared__ uint64_t s_ring[kStages];  // phase A ring
+    __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
     uint32_t mb_phase = 0, ring_phase = 0;
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
@@ -595,17 +608,21 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             // are loaded first, so that their latency hides behind the dot products
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
-            double sij = 0.0, pij = 0.0, gij = 0.0, cij = 0.0;
-            double sdi = 0.0, sdj = 0.0, pdi = 0.0, pdj = 0.0;
+            double gij = 0.0, cij = 0.0, ai = 0.0, lai = 0.0;
+            bool curv = false;
             if (which >= 0) {
-                sij = (double)Sig[ii * q + jj];
-                pij = (double)Psi[ii * q + jj];
+                const double sij = (double)Sig[ii * q + jj], pij = (double)Psi[ii * q + jj];
+                const double sdi = Sd[ii], sdj = Sd[jj], pdi = Pd[ii], pdj = Pd[jj];
                 gij = G[ii * q + jj];
                 cij = Lam[ii * q + jj];
-                sdi = Sd[ii];
-                sdj = Sd[jj];
-                pdi = Pd[ii];
-                pdj = Pd[jj];
+                // curvature of the exact quadratic model along the coordinate (Appendix A.1
+                // with the E1/E5 readings), its inverse and lam/a, ahead of the dot products
+                const double a = (ii != jj)
+                                     ? sij * sij + sdi * sdj + sdi * pdj + sdj * pdi + 2.0 * sij * pij
+                                     : sdi * sdi + 2.0 * sdi * pdi;
+                curv = a > 0.0 && isfinite(a);
+                ai = curv ? 1.0 / a : 0.0;
+                lai = ((ii != jj) ? lam_off : lam_diag) * ai;
             }
             // (Sigma D Sigma)_ij = Sigma_i . U_{:,j}, (Psi D Sigma)_ij = Psi_i . U_{:,j},
             // (Psi D Sigma)_ji = Psi_j . U_{:,i}; rows 0..4 serve coordinate l, and the
@@ -669,17 +686,8 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 const double d0 = cta_total<6>(s_red, 3 * which);
                 const double d1 = cta_total<6>(s_red, 3 * which + 1);
                 const double d2 = cta_total<6>(s_red, 3 * which + 2);
-                double a, bb, lam;
-                if (ii != jj) {
-                    a = sij * sij + sdi * sdj + sdi * pdj + sdj * pdi + 2.0 * sij * pij;
-                    bb = gij + d0 + d1 + d2;
-                    lam = lam_off;
-                } else {
-                    a = sdi * sdi + 2.0 * sdi * pdi;
-                    bb = gij + d0 + 2.0 * d1;
-                    lam = lam_diag;
-                }
-                step_constants<T>(bb, a, cij, lam, pre, B, lw);
+                const double bb = (ii != jj) ? (gij + d0) + (d1 + d2) : gij + d0 + 2.0 * d1;
+                step_constants<T>(bb, ai, lai, curv, cij, pre, B, lw);
             }
         }
         if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
@@ -687,7 +695,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
 
     // prologue: phase A of batch 0 by every CTA; no correction from an earlier batch
     if (threadIdx.x == 0) {
-        for (int k = 0; k < kStages; k++) mbar_init(&s_ring[k], 1);
+        for (int k = 0; k < kMaxStages; k++) mbar_init(&s_ring[k], 1);
         mbar_init_fence();
     }
     BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
@@ -860,7 +868,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 2];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
-    __shared__ uint64_t s_ring[kStages];  // phase A ring
+    __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
     uint32_t mb_phase = 0, ring_phase = 0;
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
@@ -930,12 +938,18 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             // thread 0 finishes coordinate l, thread 32 coordinate lb; their scalars first
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
-            double wij = 0.0, cij = 0.0, xii = 0.0, sdj = 0.0;
+            double wij = 0.0, cij = 0.0, ai = 0.0, lai = 0.0;
+            bool curv = false;
             if (which >= 0) {
                 wij = W[ii * q + jj];
                 cij = __ldcg(Theta + ii * q + jj);
-                xii = Xd[ii];
-                sdj = Sd[jj];
+                const double xii = Xd[ii], sdj = Sd[jj];
+                // curvature 2 Sigma_jj (S_xx)_ii (Appendix A.1 with the E2 reading), zero for a
+                // constant input column; its inverse and lam/a ahead of the dot products
+                const double a = (xii != 0.0) ? 2.0 * sdj * xii : 0.0;
+                curv = a > 0.0 && isfinite(a);
+                ai = curv ? 1.0 / a : 0.0;
+                lai = lam * ai;
             }
             // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
             DotPlan<T, 2> pl;
@@ -980,15 +994,14 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             if (which >= 0) {
                 const int lw = which ? lb : l;
                 const double d = cta_total<2>(s_red, which);
-                const double a = (xii != 0.0) ? 2.0 * sdj * xii : 0.0;
-                step_constants<T>(2.0 * wij + 2.0 * d, a, cij, lam, pre, B, lw);
+                step_constants<T>(2.0 * (wij + d), ai, lai, curv, cij, pre, B, lw);
             }
         }
         if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
     };
 
     if (threadIdx.x == 0) {
-        for (int k = 0; k < kStages; k++) mbar_init(&s_ring[k], 1);
+        for (int k = 0; k < kMaxStages; k++) mbar_init(&s_ring[k], 1);
         mbar_init_fence();
     }
     BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
