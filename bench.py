@@ -650,7 +650,8 @@ def run_cuda(args):
 
     # warm-up: W Newton iterations from Lambda = I, Theta = 0
     ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
-                   opts=cg.make_opts(precision=prec, max_iter=args.warmup),
+                   opts=cg.make_opts(precision=prec, max_iter=args.warmup,
+                                     sweep_batch=args.sweep_batch),
                    Lambda_out=L0, Theta_out=T0)
     torch.cuda.synchronize()
     barrier(world)
@@ -661,7 +662,8 @@ def run_cuda(args):
         ev0.record(stream)
         res = ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12, warm_Lambda=L0,
                              warm_Theta=T0,
-                             opts=cg.make_opts(precision=prec, max_iter=args.steps),
+                             opts=cg.make_opts(precision=prec, max_iter=args.steps,
+                                               sweep_batch=args.sweep_batch),
                              Lambda_out=L1, Theta_out=T1)
         ev1.record(stream)
         torch.cuda.synchronize()
@@ -761,6 +763,8 @@ def main():
     ap.add_argument("--no-ttg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--sweep-batch", type=int, default=0,
+                    help="coordinates per blocked Gauss-Seidel batch (0: the library default)")
     ap.add_argument("--gap-trace", type=float, default=0.0,
                     help="seconds of device time per precision: record f against time on the "
                          "5000 x 5000 workload instead of the default line")
@@ -776,9 +780,9 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-max-iter", type=int, default=100)
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--line-serve-requests", type=int, default=16,
+    ap.add_argument("--line-serve-requests", type=int, default=8,
                     help="served requests measured within the default line")
-    ap.add_argument("--line-serve-max-iter", type=int, default=25)
+    ap.add_argument("--line-serve-max-iter", type=int, default=8)
     ap.add_argument("--profile-sweep", action="store_true",
                     help="run only a bounded Lambda pass at q=5000 (for ncu captures)")
     ap.add_argument("--profile-contract", action="store_true",

@@ -43,11 +43,11 @@ constexpr int kRowsInFlight = 5;
 // Phase A: rows per CTA held at once, chunks in flight, bytes per row and chunk.
 constexpr int kRingRows = 10;
 constexpr int kChunkBytes = 4096;
-// The ring takes the whole work area of shared memory (which phase A does not share with
-// the other phases): as many stages of the plan's rows as fit, up to kMaxStages, so that a
-// q = 5000 row set (five chunks per row) is in flight at once.
+// The ring holds as many stages of the plan's rows as fit in kRingBytes, up to kMaxStages
+// (three stages of ten rows; more of fewer rows).  A larger ring (200 KB) was slower: the
+// shared memory it takes comes out of the L1 cache that the coefficient gathers use.
 constexpr int kMaxStages = 16;
-constexpr size_t kRingBytes = (size_t)200 * 1024;
+constexpr size_t kRingBytes = (size_t)3 * kRingRows * kChunkBytes;
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
@@ -63,7 +63,6 @@ __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, 
 // the upper branch is taken exactly when vp > -c, the lower one when vm < -c.  A correction
 // sum acc added to b shifts both vp and vm by -acc/a, so they are kept as
 // vp - ai acc, vm - ai acc with ai = 1/a.  Zero curvature (a = 0): vp = vm = -c, ai = 0.
-// They are formed as vp = -b ai - lam ai, vm = lam ai - b ai.
 enum { PRE_VPH, PRE_VPL, PRE_VMH, PRE_VML, PRE_AI, PRE_MC, PRE_N };
 static_assert(PRE_N == kStepConstants, "step constant count");
 
@@ -73,25 +72,45 @@ __device__ __forceinline__ void split(double v, T *hi, T *lo) {
     *lo = (T)(v - (double)*hi);
 }
 
-// The step constants of coordinate l from its correction-free b (base), 1/a (ai) and lam/a
-// (lai); ai and lai depend on Sigma and Psi (or S_xx) entries only, so they are formed
-// before the dot products and only b's few double operations follow them.  curv: a > 0
-// (otherwise the entry goes to zero: vp = vm = -c, ai = 0).
+// Step constants in two parts.  The part that depends on scalars only (G_ij or W_ij, the
+// curvature a from the Sigma/Psi or S_xx diagonals, lambda, c) is formed in double before
+// the dot products: vp0 = -(g + lam) / a and vm0 = (lam - g) / a, split into hi + lo
+// words of T.  The dot products' part enters afterwards in T: their sum d shifts both by
+// -d / a, which is folded into the lo words (d carries the cache type's accuracy anyway),
+// so that only a few T operations follow the dot products.  curv: a > 0 (otherwise the
+// entry goes to zero: vp = vm = -c, 1/a = 0).
 template <typename T>
-__device__ void step_constants(double base, double ai, double lai, bool curv, double c, T *pre,
-                               int B, int l) {
-    T *o = pre;
-    if (curv) {
-        const double t = base * ai;
-        split<T>(-t - lai, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
-        split<T>(lai - t, o + PRE_VMH * B + l, o + PRE_VML * B + l);
-        o[PRE_AI * B + l] = (T)ai;
+struct StepHead {
+    T vph, vpl, vmh, vml, ai, mc;
+};
+
+template <typename T>
+__device__ StepHead<T> step_head(double g, double a, double lam, double c) {
+    StepHead<T> h;
+    if (a > 0.0 && isfinite(a)) {
+        const double ai = 1.0 / a;
+        split<T>(-(g + lam) * ai, &h.vph, &h.vpl);
+        split<T>((lam - g) * ai, &h.vmh, &h.vml);
+        h.ai = (T)ai;
     } else {  // zero curvature: the entry goes to zero
-        split<T>(-c, o + PRE_VPH * B + l, o + PRE_VPL * B + l);
-        split<T>(-c, o + PRE_VMH * B + l, o + PRE_VML * B + l);
-        o[PRE_AI * B + l] = T(0);
+        split<T>(-c, &h.vph, &h.vpl);
+        split<T>(-c, &h.vmh, &h.vml);
+        h.ai = T(0);
     }
-    o[PRE_MC * B + l] = (T)(-c);
+    h.mc = (T)(-c);
+    return h;
+}
+
+// Stores coordinate l's constants with the dot products' sum d applied.
+template <typename T>
+__device__ void step_constants(const StepHead<T> &h, T d, T *pre, int B, int l) {
+    const T corr = d * h.ai;  // zero when the curvature is zero
+    pre[PRE_VPH * B + l] = h.vph;
+    pre[PRE_VPL * B + l] = h.vpl - corr;
+    pre[PRE_VMH * B + l] = h.vmh;
+    pre[PRE_VML * B + l] = h.vml - corr;
+    pre[PRE_AI * B + l] = h.ai;
+    pre[PRE_MC * B + l] = h.mc;
 }
 
 __device__ __forceinline__ void decode_pair(int e, int &l, int &l1) {
@@ -286,7 +305,7 @@ __device__ __forceinline__ float vget(const float4 &v, int k) { return k == 0 ? 
 __device__ __forceinline__ double vget(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
 
 // Per-warp sums of ND per-thread values, written to red[warp][d] (shared); after a
-// __syncthreads, cta_total(red, d) adds the warps' sums in double, in a fixed order.
+// __syncthreads, cta_total(red, d) adds the warps' sums in the cache type, in a fixed order.
 template <typename T, int ND>
 __device__ __forceinline__ void warp_partials(const T (&v)[ND], double *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -297,11 +316,11 @@ __device__ __forceinline__ void warp_partials(const T (&v)[ND], double *red) {
     }
 }
 
-template <int ND>
-__device__ __forceinline__ double cta_total(const double *red, int d) {
-    double s[kWarps];
+template <typename T, int ND>
+__device__ __forceinline__ T cta_total(const double *red, int d) {
+    T s[kWarps];
 #pragma unroll
-    for (int w = 0; w < kWarps; w++) s[w] = red[w * ND + d];
+    for (int w = 0; w < kWarps; w++) s[w] = (T)red[w * ND + d];
 #pragma unroll
     for (int h = kWarps / 2; h > 0; h /= 2)  // pairwise: three dependent additions, not seven
 #pragma unroll
@@ -312,8 +331,8 @@ __device__ __forceinline__ double cta_total(const double *red, int d) {
 // ---------------------------------------------------------------------------------
 // Phase A dot products from shared memory.  The rows that one CTA's dot products read
 // (kRingRows at most) are brought into shared memory in column chunks by bulk copies, as
-// many chunks ahead as the ring holds (up to 200 KB in flight per SM), rather than the few
-// loads per thread its warps would have outstanding.
+// many chunks ahead as the ring holds (120 KB in flight per SM), rather than the few loads
+// per thread its warps would have outstanding.
 // ---------------------------------------------------------------------------------
 
 template <typename T, int ND>
@@ -608,21 +627,17 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             // are loaded first, so that their latency hides behind the dot products
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
-            double gij = 0.0, cij = 0.0, ai = 0.0, lai = 0.0;
-            bool curv = false;
+            StepHead<T> head{};
             if (which >= 0) {
                 const double sij = (double)Sig[ii * q + jj], pij = (double)Psi[ii * q + jj];
                 const double sdi = Sd[ii], sdj = Sd[jj], pdi = Pd[ii], pdj = Pd[jj];
-                gij = G[ii * q + jj];
-                cij = Lam[ii * q + jj];
                 // curvature of the exact quadratic model along the coordinate (Appendix A.1
-                // with the E1/E5 readings), its inverse and lam/a, ahead of the dot products
+                // with the E1/E5 readings) and the constants' scalar part, ahead of the dots
                 const double a = (ii != jj)
                                      ? sij * sij + sdi * sdj + sdi * pdj + sdj * pdi + 2.0 * sij * pij
                                      : sdi * sdi + 2.0 * sdi * pdi;
-                curv = a > 0.0 && isfinite(a);
-                ai = curv ? 1.0 / a : 0.0;
-                lai = ((ii != jj) ? lam_off : lam_diag) * ai;
+                head = step_head<T>(G[ii * q + jj], a, (ii != jj) ? lam_off : lam_diag,
+                                    Lam[ii * q + jj]);
             }
             // (Sigma D Sigma)_ij = Sigma_i . U_{:,j}, (Psi D Sigma)_ij = Psi_i . U_{:,j},
             // (Psi D Sigma)_ji = Psi_j . U_{:,i}; rows 0..4 serve coordinate l, and the
@@ -683,11 +698,10 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             __syncthreads();
             if (which >= 0) {
                 const int lw = which ? lb : l;
-                const double d0 = cta_total<6>(s_red, 3 * which);
-                const double d1 = cta_total<6>(s_red, 3 * which + 1);
-                const double d2 = cta_total<6>(s_red, 3 * which + 2);
-                const double bb = (ii != jj) ? (gij + d0) + (d1 + d2) : gij + d0 + 2.0 * d1;
-                step_constants<T>(bb, ai, lai, curv, cij, pre, B, lw);
+                const T d0 = cta_total<T, 6>(s_red, 3 * which);
+                const T d1 = cta_total<T, 6>(s_red, 3 * which + 1);
+                const T d2 = cta_total<T, 6>(s_red, 3 * which + 2);
+                step_constants<T>(head, (ii != jj) ? d0 + (d1 + d2) : d0 + T(2) * d1, pre, B, lw);
             }
         }
         if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
@@ -938,18 +952,13 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             // thread 0 finishes coordinate l, thread 32 coordinate lb; their scalars first
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
-            double wij = 0.0, cij = 0.0, ai = 0.0, lai = 0.0;
-            bool curv = false;
+            StepHead<T> head{};
             if (which >= 0) {
-                wij = W[ii * q + jj];
-                cij = __ldcg(Theta + ii * q + jj);
                 const double xii = Xd[ii], sdj = Sd[jj];
                 // curvature 2 Sigma_jj (S_xx)_ii (Appendix A.1 with the E2 reading), zero for a
-                // constant input column; its inverse and lam/a ahead of the dot products
+                // constant input column, and the constants' scalar part ahead of the dots
                 const double a = (xii != 0.0) ? 2.0 * sdj * xii : 0.0;
-                curv = a > 0.0 && isfinite(a);
-                ai = curv ? 1.0 / a : 0.0;
-                lai = lam * ai;
+                head = step_head<T>(2.0 * W[ii * q + jj], a, lam, __ldcg(Theta + ii * q + jj));
             }
             // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
             DotPlan<T, 2> pl;
@@ -993,8 +1002,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             __syncthreads();
             if (which >= 0) {
                 const int lw = which ? lb : l;
-                const double d = cta_total<2>(s_red, which);
-                step_constants<T>(2.0 * (wij + d), ai, lai, curv, cij, pre, B, lw);
+                step_constants<T>(head, T(2) * cta_total<T, 2>(s_red, which), pre, B, lw);
             }
         }
         if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
