@@ -79,25 +79,29 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 }
 
 // Grid-wide barrier of a cooperative launch, in two halves so that a CTA can issue loads
-// between its arrival and its wait (the fence before the arrival would otherwise wait for
-// them).  Every CTA adds one to a counter that only grows; the CTAs of round r wait until
-// it reaches (r + 1) nblocks, where r follows from the value the CTA's own addition returned
-// (no CTA can arrive at round r + 1 before all have arrived at round r).  One L2 round trip
-// per CTA plus the time for the last arrival to be seen.  A wait that exceeds deadline_ns,
-// or sees another CTA's error, returns false (and records DEV_TIMEOUT in the first case).
+// between its arrival and its wait.  Every CTA passes the barriers of a launch in the same
+// order and counts them itself (`round`, from 0): its arrival adds one to a counter that
+// only grows, as a release reduction that returns nothing (so the arrival costs no round
+// trip), and its wait lasts until the counter reaches (round + 1) nblocks.  A wait that
+// exceeds deadline_ns, or sees another CTA's error, returns false (and records DEV_TIMEOUT
+// in the first case).
 struct GridTicket {
-    unsigned long long target;  // thread 0: the count that ends this round (0: arrived last)
+    unsigned long long target;  // thread 0: the count that ends this round
 };
 
-__device__ __forceinline__ GridTicket grid_arrive(GridBarrier *bar, unsigned nblocks) {
-    __syncthreads();  // the CTA's work of this round is done
+__device__ __forceinline__ void red_release_add(unsigned long long *p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ GridTicket grid_arrive(GridBarrier *bar, unsigned nblocks,
+                                                  unsigned &round) {
+    __syncthreads();  // the CTA's work of this round is done (and ordered before the release)
     GridTicket t{0};
     if (threadIdx.x == 0) {
-        __threadfence();  // this CTA's writes before its arrival
-        const unsigned long long old = atomicAdd(&bar->arrived, 1ull);
-        const unsigned long long target = (old / nblocks + 1) * nblocks;
-        t.target = (old + 1 == target) ? 0ull : target;
+        red_release_add(&bar->arrived, 1ull);
+        t.target = (unsigned long long)(round + 1) * nblocks;
     }
+    round++;
     return t;
 }
 
@@ -106,24 +110,17 @@ __device__ __forceinline__ bool grid_wait(GridBarrier *bar, int *err, GridTicket
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (t.target != 0) {
-            const uint64_t t0 = global_ns();
-            unsigned spins = 0;
-            while (ld_acquire_u64(&bar->arrived) < t.target) {
-                if ((++spins & 63u) == 0) {
-                    if (ld_acquire_int(err) != 0) { ok = 0; break; }
-                    if (global_ns() - t0 > deadline_ns) {
-                        atomicCAS(err, 0, (int)DEV_TIMEOUT);
-                        ok = 0;
-                        break;
-                    }
+        const uint64_t t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u64(&bar->arrived) < t.target) {
+            if ((++spins & 63u) == 0) {
+                if (ld_acquire_int(err) != 0) { ok = 0; break; }
+                if (global_ns() - t0 > deadline_ns) {
+                    atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                    ok = 0;
+                    break;
                 }
             }
-        } else {
-            // the last arrival: an acquire read of the counter (its own addition is the last
-            // in the counter's order) orders the other CTAs' writes before later reads without
-            // waiting, as a fence would, for this thread's loads still in flight
-            (void)ld_acquire_u64(&bar->arrived);
         }
         if (ok && ld_acquire_int(err) != 0) ok = 0;
         s_ok = ok;
@@ -133,8 +130,8 @@ __device__ __forceinline__ bool grid_wait(GridBarrier *bar, int *err, GridTicket
 }
 
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int *err, unsigned nblocks,
-                                          uint64_t deadline_ns = 2000000000ull) {
-    return grid_wait(bar, err, grid_arrive(bar, nblocks), deadline_ns);
+                                          unsigned &round, uint64_t deadline_ns = 2000000000ull) {
+    return grid_wait(bar, err, grid_arrive(bar, nblocks, round), deadline_ns);
 }
 
 // Warp reductions

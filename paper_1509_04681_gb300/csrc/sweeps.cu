@@ -47,6 +47,28 @@ constexpr int kChunkBytes = 4096;
 // (three stages of ten rows; more of fewer rows).  A larger ring (200 KB) was slower: the
 // shared memory it takes comes out of the L1 cache that the coefficient gathers use.
 constexpr int kMaxStages = 16;
+// Phase A: warps 0 .. kDotWarps - 1 compute the dot products (through the ring) while the
+// other warps form the coefficients; the dot warps synchronise among themselves on named
+// barrier kBarDots.
+constexpr int kDotWarps = 4;
+constexpr int kDotThreads = kDotWarps * 32;
+constexpr int kCoefThreads = kThreads - kDotThreads;
+constexpr int kBarDots = 1;
+
+__device__ __forceinline__ void bar_sync_n(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+// barrier `id` over n threads that also reduces p by AND
+__device__ __forceinline__ bool bar_and_n(int id, int n, bool p) {
+    int r;
+    asm volatile(
+        "{\n\t.reg .pred pi, po;\n\tsetp.ne.s32 pi, %1, 0;\n\t"
+        "bar.red.and.pred po, %2, %3, pi;\n\tselp.s32 %0, 1, 0, po;\n\t}"
+        : "=r"(r)
+        : "r"((int)p), "r"(id), "r"(n)
+        : "memory");
+    return r != 0;
+}
 constexpr size_t kRingBytes = (size_t)3 * kRingRows * kChunkBytes;
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
@@ -304,8 +326,9 @@ template <> struct V16<double> { using type = double2; static const int n = 2; }
 __device__ __forceinline__ float vget(const float4 &v, int k) { return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w; }
 __device__ __forceinline__ double vget(const double2 &v, int k) { return k == 0 ? v.x : v.y; }
 
-// Per-warp sums of ND per-thread values, written to red[warp][d] (shared); after a
-// __syncthreads, cta_total(red, d) adds the warps' sums in the cache type, in a fixed order.
+// Per-warp sums of ND per-thread values of the dot warps, written to red[warp][d] (shared);
+// after their barrier, cta_total(red, d) adds the warps' sums in the cache type, in a fixed
+// order.
 template <typename T, int ND>
 __device__ __forceinline__ void warp_partials(const T (&v)[ND], double *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -318,11 +341,11 @@ __device__ __forceinline__ void warp_partials(const T (&v)[ND], double *red) {
 
 template <typename T, int ND>
 __device__ __forceinline__ T cta_total(const double *red, int d) {
-    T s[kWarps];
+    T s[kDotWarps];
 #pragma unroll
-    for (int w = 0; w < kWarps; w++) s[w] = (T)red[w * ND + d];
+    for (int w = 0; w < kDotWarps; w++) s[w] = (T)red[w * ND + d];
 #pragma unroll
-    for (int h = kWarps / 2; h > 0; h /= 2)  // pairwise: three dependent additions, not seven
+    for (int h = kDotWarps / 2; h > 0; h /= 2)  // pairwise
 #pragma unroll
         for (int w = 0; w < h; w++) s[w] += s[w + h];
     return s[0];
@@ -343,19 +366,12 @@ struct DotPlan {
 };
 
 // Per-thread partial sums acc[d] of the plan's dot products over columns [0, len), with
-// len * sizeof(T) a multiple of 16.  Every thread of the CTA calls it.  A copy that does
-// not land within the wait limit makes the whole CTA give up (false, err set), after
-// thread 0 has waited, again with a limit, for the copies it still has in flight.
-// `mid()` is run by every thread once the first chunks are in flight, so that independent
-// work (and its loads) overlaps their latency.
-struct NoWork {
-    __device__ void operator()() const {}
-};
-
-template <typename T, int ND, typename F = NoWork>
+// len * sizeof(T) a multiple of 16.  The kDotThreads threads of the dot warps call it.  A
+// copy that does not land within the wait limit makes them all give up (false, err set),
+// after thread 0 has waited, again with a limit, for the copies it still has in flight.
+template <typename T, int ND>
 __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
-                          unsigned char *ring, uint64_t *mb, uint32_t &phase, int *err,
-                          F mid = F()) {
+                          unsigned char *ring, uint64_t *mb, uint32_t &phase, int *err) {
     constexpr int CW = kChunkBytes / (int)sizeof(T);
     using VT = typename V16<T>::type;
     constexpr int VN = V16<T>::n;
@@ -387,7 +403,6 @@ __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
         fence_proxy_async();
         for (; issued < nch && issued < nst; issued++) issue(issued);
     }
-    mid();
     for (int64_t c = 0; c < nch; c++) {
         const int st = (int)(c % nst);
         const bool ok = mbar_wait(&mb[st], (phase >> st) & 1u, err);
@@ -396,7 +411,7 @@ __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
             const VT *src = reinterpret_cast<const VT *>(ring + (size_t)st * stage_bytes);
             const int64_t c0 = c * CW;
             const int nv = (int)(((len - c0) < CW ? (len - c0) : CW) / VN);
-            for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+            for (int v = threadIdx.x; v < nv; v += kDotThreads) {
 #pragma unroll
                 for (int d = 0; d < ND; d++) {
                     const VT x = src[oa[d] + v];
@@ -406,14 +421,14 @@ __device__ bool ring_dots(const DotPlan<T, ND> &pl, int64_t len, T (&acc)[ND],
                 }
             }
         }
-        if (!__syncthreads_and(ok)) {
+        if (!bar_and_n(kBarDots, kDotThreads, ok)) {
             if (threadIdx.x == 0)
                 for (int64_t c2 = ok ? c + 1 : c; c2 < issued; c2++) {
                     const int s2 = (int)(c2 % nst);
                     if (!mbar_wait(&mb[s2], (phase >> s2) & 1u, err, false)) break;
                     phase ^= 1u << s2;
                 }
-            __syncthreads();
+            bar_sync_n(kBarDots, kDotThreads);
             return false;
         }
         if (threadIdx.x == 0 && issued < nch) {  // stage st is free again
@@ -540,9 +555,11 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             unsigned nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 6];
+    __shared__ StepHead<T> s_head[2];  // the scalar part of the two coordinates' constants
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
     __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
     uint32_t mb_phase = 0, ring_phase = 0;
+    unsigned bar_round = 0;  // grid barriers passed (every CTA of the group passes the same)
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
     const SmemLayout L = smem_layout<T>(B);
@@ -590,10 +607,11 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
                        int nbp, int rank0) {
         const int nA = (int)nblk - rank0, rank = (int)bid - rank0;
-        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
-        const int64_t nt = (int64_t)nA * blockDim.x;
+        // the coefficient warps' thread index and count over the group's phase-A CTAs
+        const int64_t t0 = (int64_t)rank * kCoefThreads + ((int)threadIdx.x - kDotThreads);
+        const int64_t nt = (int64_t)nA * kCoefThreads;
         // The coefficients depend on entries of Sigma and Psi only, not on the dot products:
-        // they are formed while the first chunks of this CTA's dot products are in flight.
+        // the coefficient warps form them while the dot warps compute the dot products.
         auto coef_work = [&]() {
             for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
                 const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
@@ -617,7 +635,10 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 }
             }
         };
-        bool coef_done = false;
+        if (threadIdx.x >= kDotThreads) {
+            coef_work();
+            return;
+        }
         for (int l = rank; l < nb; l += 2 * nA) {
             const int lb = l + nA;
             const bool two = lb < nb;
@@ -627,7 +648,6 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             // are loaded first, so that their latency hides behind the dot products
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
-            StepHead<T> head{};
             if (which >= 0) {
                 const double sij = (double)Sig[ii * q + jj], pij = (double)Psi[ii * q + jj];
                 const double sdi = Sd[ii], sdj = Sd[jj], pdi = Pd[ii], pdj = Pd[jj];
@@ -636,8 +656,10 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 const double a = (ii != jj)
                                      ? sij * sij + sdi * sdj + sdi * pdj + sdj * pdi + 2.0 * sij * pij
                                      : sdi * sdi + 2.0 * sdi * pdi;
-                head = step_head<T>(G[ii * q + jj], a, (ii != jj) ? lam_off : lam_diag,
-                                    Lam[ii * q + jj]);
+                // stored before the dot products (the ring's waits order it): the double
+                // operations then run while the data is in flight, not after it
+                s_head[which] = step_head<T>(G[ii * q + jj], a, (ii != jj) ? lam_off : lam_diag,
+                                             Lam[ii * q + jj]);
             }
             // (Sigma D Sigma)_ij = Sigma_i . U_{:,j}, (Psi D Sigma)_ij = Psi_i . U_{:,j},
             // (Psi D Sigma)_ji = Psi_j . U_{:,i}; rows 0..4 serve coordinate l, and the
@@ -676,18 +698,11 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             }
             T acc[6];
             if (use_ring) {
-                const bool ok = coef_done
-                                    ? ring_dots<T, 6>(pl, q, acc, work, s_ring, ring_phase, scr.err)
-                                    : ring_dots<T, 6>(pl, q, acc, work, s_ring, ring_phase,
-                                                      scr.err, coef_work);
-                coef_done = true;
-                if (!ok) return;
+                if (!ring_dots<T, 6>(pl, q, acc, work, s_ring, ring_phase, scr.err)) return;
             } else {
-                if (!coef_done) coef_work();
-                coef_done = true;
 #pragma unroll
                 for (int d = 0; d < 6; d++) acc[d] = T(0);
-                for (int64_t t = threadIdx.x; t < q; t += blockDim.x) {
+                for (int64_t t = threadIdx.x; t < q; t += kDotThreads) {
                     T x[kRingRows];
                     for (int r = 0; r < pl.nrows; r++) x[r] = __ldcg(pl.rows[r] + t);
 #pragma unroll
@@ -695,16 +710,17 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 }
             }
             warp_partials<T, 6>(acc, s_red);
-            __syncthreads();
+            bar_sync_n(kBarDots, kDotThreads);
             if (which >= 0) {
                 const int lw = which ? lb : l;
                 const T d0 = cta_total<T, 6>(s_red, 3 * which);
                 const T d1 = cta_total<T, 6>(s_red, 3 * which + 1);
                 const T d2 = cta_total<T, 6>(s_red, 3 * which + 2);
-                step_constants<T>(head, (ii != jj) ? d0 + (d1 + d2) : d0 + T(2) * d1, pre, B, lw);
+                step_constants<T>(s_head[which], (ii != jj) ? d0 + (d1 + d2) : d0 + T(2) * d1,
+                                  pre, B, lw);
             }
+            bar_sync_n(kBarDots, kDotThreads);  // s_red read before the next pair writes it
         }
-        if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
     };
 
     // prologue: phase A of batch 0 by every CTA; no correction from an earlier batch
@@ -726,7 +742,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             mbar_init_fence();
         }
     }
-    if (!grid_sync(scr.bar, scr.err, nblk)) return;
+    if (!grid_sync(scr.bar, scr.err, nblk, bar_round)) return;
 
     for (int64_t k = 0; k < nbatch; k++) {
         const int64_t sk = k * B, sn = sk + B;
@@ -787,7 +803,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             }
         };
         {
-            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
             seg_columns(0);
             load_rows(cur.sa[cur.sseg[0]], r0 + warp);
             if (!grid_wait(scr.bar, scr.err, tk)) return;
@@ -853,7 +869,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
         }
         {
             // the indices of batch k + 2 are fetched while this barrier completes
-            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
             const int64_t s2 = (k + 2) * B;
             const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
             pref = nb2 > 0;
@@ -881,9 +897,11 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
            int B_arg, SweepScratch scr, bool rows_sorted, unsigned bid, unsigned nblk) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 2];
+    __shared__ StepHead<T> s_head[2];
     __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
     __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
     uint32_t mb_phase = 0, ring_phase = 0;
+    unsigned bar_round = 0;  // grid barriers passed (every CTA of the group passes the same)
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
     const SmemLayout L = smem_layout<T>(B);
@@ -916,10 +934,11 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
         // tmax are zero); all p rows otherwise
         const int64_t tmax = rows_sorted ? (int64_t)bm.sa[0] + 1 : p;
         const int64_t tlen = ((tmax + VN - 1) / VN) * VN < p ? ((tmax + VN - 1) / VN) * VN : p;
-        const int64_t t0 = (int64_t)rank * blockDim.x + threadIdx.x;
-        const int64_t nt = (int64_t)nA * blockDim.x;
-        // the coefficients (entries of S_xx and Sigma only) are formed while the first chunks
-        // of this CTA's dot products are in flight
+        // the coefficient warps' thread index and count over the group's phase-A CTAs
+        const int64_t t0 = (int64_t)rank * kCoefThreads + ((int)threadIdx.x - kDotThreads);
+        const int64_t nt = (int64_t)nA * kCoefThreads;
+        // the coefficients (entries of S_xx and Sigma only) are formed by the coefficient
+        // warps while the dot warps compute the dot products
         auto coef_work = [&]() {
             for (int64_t e = t0; e < (int64_t)(B - nb) * PRE_N; e += nt) {  // padding coordinates
                 const int k = (int)(e / (B - nb)), l = nb + (int)(e % (B - nb));
@@ -943,7 +962,10 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                 }
             }
         };
-        bool coef_done = false;
+        if (threadIdx.x >= kDotThreads) {
+            coef_work();
+            return;
+        }
         for (int l = rank; l < nb; l += 2 * nA) {
             const int lb = l + nA;
             const bool two = lb < nb;
@@ -952,13 +974,13 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             // thread 0 finishes coordinate l, thread 32 coordinate lb; their scalars first
             const int which = threadIdx.x == 0 ? 0 : (threadIdx.x == 32 && two ? 1 : -1);
             const int64_t ii = which == 1 ? i1 : i0, jj = which == 1 ? j1 : j0;
-            StepHead<T> head{};
             if (which >= 0) {
                 const double xii = Xd[ii], sdj = Sd[jj];
                 // curvature 2 Sigma_jj (S_xx)_ii (Appendix A.1 with the E2 reading), zero for a
                 // constant input column, and the constants' scalar part ahead of the dots
                 const double a = (xii != 0.0) ? 2.0 * sdj * xii : 0.0;
-                head = step_head<T>(2.0 * W[ii * q + jj], a, lam, __ldcg(Theta + ii * q + jj));
+                s_head[which] = step_head<T>(2.0 * W[ii * q + jj], a, lam,
+                                             __ldcg(Theta + ii * q + jj));
             }
             // (S_xx Delta V)_ij = (S_xx)_i . Delta V_{:,j}
             DotPlan<T, 2> pl;
@@ -980,18 +1002,10 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             }
             T acc[2];
             if (use_ring) {
-                const bool ok = coef_done
-                                    ? ring_dots<T, 2>(pl, tlen, acc, work, s_ring, ring_phase,
-                                                      scr.err)
-                                    : ring_dots<T, 2>(pl, tlen, acc, work, s_ring, ring_phase,
-                                                      scr.err, coef_work);
-                coef_done = true;
-                if (!ok) return;
+                if (!ring_dots<T, 2>(pl, tlen, acc, work, s_ring, ring_phase, scr.err)) return;
             } else {
-                if (!coef_done) coef_work();
-                coef_done = true;
                 acc[0] = acc[1] = T(0);
-                for (int64_t t = threadIdx.x; t < tmax; t += blockDim.x) {
+                for (int64_t t = threadIdx.x; t < tmax; t += kDotThreads) {
                     T x[4];
                     for (int r = 0; r < pl.nrows; r++) x[r] = __ldcg(pl.rows[r] + t);
                     acc[0] = fma(x[pl.ia[0]], x[pl.ib[0]], acc[0]);
@@ -999,13 +1013,14 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                 }
             }
             warp_partials<T, 2>(acc, s_red);
-            __syncthreads();
+            bar_sync_n(kBarDots, kDotThreads);
             if (which >= 0) {
                 const int lw = which ? lb : l;
-                step_constants<T>(head, T(2) * cta_total<T, 2>(s_red, which), pre, B, lw);
+                step_constants<T>(s_head[which], T(2) * cta_total<T, 2>(s_red, which), pre, B,
+                                  lw);
             }
+            bar_sync_n(kBarDots, kDotThreads);  // s_red read before the next pair writes it
         }
-        if (!coef_done) coef_work();  // a CTA without a coordinate of this batch
     };
 
     if (threadIdx.x == 0) {
@@ -1026,7 +1041,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             mbar_init_fence();
         }
     }
-    if (!grid_sync(scr.bar, scr.err, nblk)) return;
+    if (!grid_sync(scr.bar, scr.err, nblk, bar_round)) return;
 
     for (int64_t k = 0; k < nbatch; k++) {
         const int64_t sk = k * B, sn = sk + B;
@@ -1073,7 +1088,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             }
         };
         {
-            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
             seg_columns(0);
             load_rows(cur.sa[cur.sseg[0]], r0 + warp);
             if (!grid_wait(scr.bar, scr.err, tk)) return;
@@ -1129,7 +1144,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
         }
         {
             // the indices of batch k + 2 are fetched while this barrier completes
-            const GridTicket tk = grid_arrive(scr.bar, nblk);
+            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
             const int64_t s2 = (k + 2) * B;
             const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
             pref = nb2 > 0;
