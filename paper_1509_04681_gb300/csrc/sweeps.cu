@@ -168,8 +168,10 @@ struct SmemLayout {
     size_t meta;  // twice (current and next batch): sa[B], sb[B], sseg[B + 1], nseg (ints)
     size_t work;  // union: phase A ring of row chunks (kRingBytes, all stages);
                   //        phase B coefficient panels [coef_area(B)], step constants
-                  //          [PRE_N][B], corr[B] (T);
-                  //        phase C mu[B] (T)
+                  //          [PRE_N][B], corr[B] (T), then, beyond them,
+                  //        phase C mu[B] (T) at work + phc: CTA 0 copies the next batch's
+                  //          phase-B data in while its phase C runs
+    size_t phc;   // offset of phase C's area within the work area
     size_t total;
 };
 
@@ -180,9 +182,10 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
     size_t off = (size_t)2 * (3 * B + 2) * sizeof(int32_t);  // two batches' metadata
     off = (off + 15) & ~size_t(15);
     s.work = off;
-    const size_t phb = ((size_t)coef_area(B) + PRE_N * B + B + 8) * sizeof(T);
+    const size_t phb = (((size_t)coef_area(B) + PRE_N * B + B + 8) * sizeof(T) + 15) & ~size_t(15);
     const size_t phc = (size_t)(B + 4) * sizeof(T);
-    size_t w = phb > phc ? phb : phc;
+    s.phc = phb;
+    size_t w = phb + phc;
     w = w > kRingBytes ? w : kRingBytes;
     s.total = off + w;
     return s;
@@ -221,14 +224,20 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
     int issued = npan < NBUF ? npan : NBUF;  // panels whose copies have been started
     bool bad = false;
     int lost = -1;  // first panel whose data did not arrive
-    if (!mbar_wait(&mb[NS], (phase >> NS) & 1u, err)) {
+    // the step constants land on mb[NS], the carried corrections on mb[NS + 1]
+    const bool pre_ok = mbar_wait(&mb[NS], (phase >> NS) & 1u, err);
+    if (pre_ok) phase ^= 1u << NS;
+    const bool corr_ok = pre_ok && mbar_wait(&mb[NS + 1], (phase >> (NS + 1)) & 1u, err);
+    if (corr_ok) phase ^= 1u << (NS + 1);
+    if (!corr_ok) {  // give up: wait (bounded) for the copies still in flight
         for (int s = 0; s < issued; s++)
             if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
                 phase ^= 1u << (s % NBUF);
-        if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
+        if (!pre_ok && mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
+        if (mbar_wait(&mb[NS + 1], (phase >> (NS + 1)) & 1u, err, false))
+            phase ^= 1u << (NS + 1);
         return;
     }
-    phase ^= 1u << NS;
     T acc[NS];  // correction sums, starting from the corrections carried from the previous batch
 #pragma unroll
     for (int s = 0; s < NS; s++) acc[s] = acc0[s * 32 + lane];
@@ -289,28 +298,50 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
     if (bad) set_err(err, DEV_NONFINITE);
 }
 
-// Phase B body shared by both passes: one thread starts bulk copies of the step constants
-// and carried corrections (completing on mb[NS]) and of each panel's coefficient columns
-// (panel s on mb[s]) into shared memory; warp 0 runs the substitution, starting each panel
-// as soon as its coefficients have landed.  The step constants of padding coordinates
-// (l >= nb) and their corrections were written in global memory with the batch, so the
-// copies bring whole arrays.  Coefficient slots of padding coordinates are never used by a
-// real coordinate: they only reach the correction sums of padding coordinates.
+// Starts (one thread) the bulk copies of a batch's step constants (landing on mb[NS]) and of
+// its coefficient panels that the buffers hold (panel s on mb[s % buffers]) into shared
+// memory.  The sources were written by other CTAs, ordered before this point by a grid
+// barrier; the destination was last read through the generic proxy.
 template <typename T, int NS>
-__device__ void phase_b(int nb, const T *gcoef, const T *gpre, const T *gcorr, T *scoef, T *spre,
-                        uint64_t *mb, uint32_t &phase, double *mu, int *err) {
+__device__ __forceinline__ void phase_b_issue(int nb, const T *gcoef, const T *gpre, T *scoef,
+                                              T *spre, uint64_t *mb) {
+    constexpr int B = NS * 32;
+    fence_proxy_async();
+    mbar_expect_tx(&mb[NS], (uint32_t)(PRE_N * B * sizeof(T)));
+    bulk_load(spre, gpre, (uint32_t)(PRE_N * B * sizeof(T)), &mb[NS]);
+    for (int s = 0; s * 32 < nb && s < panel_bufs(B); s++) issue_panel<T, NS>(s, gcoef, scoef, mb);
+}
+
+// Waits (bounded, thread 0) for the copies phase_b_issue started, on a path that leaves the
+// kernel before phase B would have consumed them.
+template <typename T, int NS>
+__device__ void phase_b_drain(int nb, uint64_t *mb, uint32_t &phase, int *err) {
+    constexpr int B = NS * 32;
+    for (int s = 0; s * 32 < nb && s < panel_bufs(B); s++)
+        if (mbar_wait(&mb[s], (phase >> s) & 1u, err, false)) phase ^= 1u << s;
+    if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
+}
+
+// Phase B body shared by both passes.  The batch's step constants and first panels were
+// copied in during the previous batch's phase C (issued_ahead), or are copied now; the
+// carried corrections, formed in that phase C, are copied now (mb[NS + 1]).  Warp 0 runs
+// the substitution, starting each panel as soon as its coefficients have landed.  The step
+// constants of padding coordinates (l >= nb) and their corrections were written in global
+// memory with the batch, so the copies bring whole arrays.  Coefficient slots of padding
+// coordinates are never used by a real coordinate: they only reach the correction sums of
+// padding coordinates.
+template <typename T, int NS>
+__device__ void phase_b(int nb, bool issued_ahead, const T *gcoef, const T *gpre,
+                        const T *gcorr, T *scoef, T *spre, uint64_t *mb, uint32_t &phase,
+                        double *mu, int *err) {
     constexpr int B = NS * 32;
     T *scorr = spre + PRE_N * B;
     if ((threadIdx.x >> 5) == 0) {
         if (threadIdx.x == 0) {
-            // the sources were written by other CTAs (ordered before this point by the grid
-            // barrier) and the destination was last used through the generic proxy
+            if (!issued_ahead) phase_b_issue<T, NS>(nb, gcoef, gpre, scoef, spre, mb);
             fence_proxy_async();
-            mbar_expect_tx(&mb[NS], (uint32_t)((PRE_N * B + B) * sizeof(T)));
-            bulk_load(spre, gpre, (uint32_t)(PRE_N * B * sizeof(T)), &mb[NS]);
-            bulk_load(scorr, gcorr, (uint32_t)(B * sizeof(T)), &mb[NS]);
-            for (int s = 0; s * 32 < nb && s < panel_bufs(B); s++)
-                issue_panel<T, NS>(s, gcoef, scoef, mb);
+            mbar_expect_tx(&mb[NS + 1], (uint32_t)(B * sizeof(T)));
+            bulk_load(scorr, gcorr, (uint32_t)(B * sizeof(T)), &mb[NS + 1]);
         }
         __syncwarp();
         forward_substitution<T, NS>(nb, spre, scorr, gcoef, scoef, mb, phase, mu, err);
@@ -556,7 +587,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 6];
     __shared__ StepHead<T> s_head[2];  // the scalar part of the two coordinates' constants
-    __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
+    __shared__ uint64_t s_mb[NS + 2];  // phase B (CTA 0): panels, step constants, corrections
     __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
     uint32_t mb_phase = 0, ring_phase = 0;
     unsigned bar_round = 0;  // grid barriers passed (every CTA of the group passes the same)
@@ -738,7 +769,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     if (bid == 0) {
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
         if (threadIdx.x == 0) {
-            for (int k = 0; k <= NS; k++) mbar_init(&s_mb[k], 1);
+            for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
             mbar_init_fence();
         }
     }
@@ -757,7 +788,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
 
         // ---- phase B of batch k on CTA 0, phase A of batch k+1 on the others ----
         if (bid == 0) {
-            phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
+            phase_b<T, NS>(nbk, k > 0, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
                            scr.err);
         } else if (nbn > 0) {
@@ -809,11 +840,17 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             if (!grid_wait(scr.bar, scr.err, tk)) return;
         }
 
+        // CTA 0: batch k+1's step constants and coefficients are complete (phase A ended
+        // before the barrier); their copies into shared memory run while phase C does
+        if (bid == 0 && threadIdx.x == 0 && nbn > 0)
+            phase_b_issue<T, NS>(nbn, coef_n, pre_n, reinterpret_cast<T *>(work),
+                                 reinterpret_cast<T *>(work) + coef_area(B), s_mb);
+
         // ---- phase C: batch k's update on this CTA's rows; corrections for batch k+1 ----
         // coordinate (a, b) of a segment with row a: U_a += mu Sigma_b, U_b += mu Sigma_a
         // (b != a); transposed: Ut[t][a] += sum mu Sigma[t][b], Ut[t][b] += mu Sigma[t][a]
         {
-            T *smu = reinterpret_cast<T *>(work);
+            T *smu = reinterpret_cast<T *>(work + L.phc);
             for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
                 const double mu = __ldcg(scr.mu + l);
                 smu[l] = (T)mu;
@@ -874,7 +911,11 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
             pref = nb2 > 0;
             if (pref) fetch_batch(ai, aj, s2, nb2, breg);
-            if (!grid_wait(scr.bar, scr.err, tk)) return;
+            if (!grid_wait(scr.bar, scr.err, tk)) {
+                if (bid == 0 && threadIdx.x == 0 && nbn > 0)  // batch k+1's copies in flight
+                    phase_b_drain<T, NS>(nbn, s_mb, mb_phase, scr.err);
+                return;
+            }
         }
         BatchMeta tmp = cur;
         cur = nxt;
@@ -898,7 +939,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 2];
     __shared__ StepHead<T> s_head[2];
-    __shared__ uint64_t s_mb[NS + 1];  // phase B (CTA 0): panels, then step constants
+    __shared__ uint64_t s_mb[NS + 2];  // phase B (CTA 0): panels, step constants, corrections
     __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
     uint32_t mb_phase = 0, ring_phase = 0;
     unsigned bar_round = 0;  // grid barriers passed (every CTA of the group passes the same)
@@ -1037,7 +1078,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     if (bid == 0) {
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
         if (threadIdx.x == 0) {
-            for (int k = 0; k <= NS; k++) mbar_init(&s_mb[k], 1);
+            for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
             mbar_init_fence();
         }
     }
@@ -1055,7 +1096,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
         }
 
         if (bid == 0) {
-            phase_b<T, NS>(nbk, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
+            phase_b<T, NS>(nbk, k > 0, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
                            reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
                            scr.err);
         } else if (nbn > 0) {
@@ -1094,9 +1135,14 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             if (!grid_wait(scr.bar, scr.err, tk)) return;
         }
 
+        // CTA 0: batch k+1's phase-B data are complete; their copies run while phase C does
+        if (bid == 0 && threadIdx.x == 0 && nbn > 0)
+            phase_b_issue<T, NS>(nbn, coef_n, pre_n, reinterpret_cast<T *>(work),
+                                 reinterpret_cast<T *>(work) + coef_area(B), s_mb);
+
         // ---- phase C: dVt[t][i] += sum over the segment of row i of mu Sigma[t][j] ----
         {
-            T *smu = reinterpret_cast<T *>(work);
+            T *smu = reinterpret_cast<T *>(work + L.phc);
             for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
                 const double mu = __ldcg(scr.mu + l);
                 smu[l] = (T)mu;
@@ -1149,7 +1195,11 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
             pref = nb2 > 0;
             if (pref) fetch_batch(ti, tj, s2, nb2, breg);
-            if (!grid_wait(scr.bar, scr.err, tk)) return;
+            if (!grid_wait(scr.bar, scr.err, tk)) {
+                if (bid == 0 && threadIdx.x == 0 && nbn > 0)  // batch k+1's copies in flight
+                    phase_b_drain<T, NS>(nbn, s_mb, mb_phase, scr.err);
+                return;
+            }
         }
         BatchMeta tmp = cur;
         cur = nxt;
