@@ -10,11 +10,18 @@ iterations start from Lambda = I, Theta = 0; the K timed iterations continue fro
 
 Printed (rank 0, one JSON line): Newton iterations per second over all ranks, the
 roofline of the dominant kernel (the coordinate pass with the larger share of the timed
-region), the oracle's CPU rate on a bounded sample, the same iterations end to end
-through the C ABI from host buffers, and the time to a 1e-6 relative objective gap of
-the mixed and the FP64 paths on the small chain workload (p=200, q=100, n=100), where a
-whole solve fits in seconds.  With --gpus N (torchrun) every rank solves an independent
-replica (another seed): the solve does not shard.
+region) and of the other pass, the same iterations end to end through the C ABI from host
+buffers, the double-precision path's rate on the same workload (fp64), a served
+regularisation-path run at the served workload's full request sizes (trimmed in count and
+iterations, and saying so), the time to a 1e-6 relative objective gap of the mixed and the
+FP64 paths on the small chain workload (p=200, q=100, n=100), where a whole solve fits in
+seconds, and the oracle's CPU rate on a bounded sample.  With --gpus N (torchrun) every rank
+solves an independent replica (another seed): the solve does not shard.
+
+Other modes: --gap-trace S records f against device time for both precisions on the
+5000 x 5000 workload (S seconds each); --large K runs K iterations of the 40000 x 20000
+workload with a KKT check; --serve runs the served paths alone; --profile-sweep and
+--profile-contract are the bounded cases of the ncu captures.
 
 --impl reference times the CPU oracle (the plain double-precision restatement of the
 method) on a bounded sample of the same workload and prints the same kind of line.
@@ -703,8 +710,10 @@ def run_cuda(args):
                               "sec_sweep_theta": info["sec_sweep_theta"] / max(1, iters),
                               "coords_per_s": (info["coords_lambda"] + info["coords_theta"]) /
                               max(1e-9, info["sec_sweep_lambda"] + info["sec_sweep_theta"])},
-            "reported_as": "Newton iterations/s on the 5000 x 5000 workload; time-to-gap on "
-                           "the 200 x 100 workload (time_to_gap)"}
+            "reported_as": "Newton iterations/s on the 5000 x 5000 workload (mixed; fp64 beside "
+                           "it); time-to-gap on the 200 x 100 workload (time_to_gap); the "
+                           "5000 x 5000 time-to-gap trace is bench.py --gap-trace; served "
+                           "lambda-point solves/s with p50/p99 (serving)"}
 
     # end to end through the C ABI from host buffers (copies inside the timed region)
     if not args.no_e2e:
