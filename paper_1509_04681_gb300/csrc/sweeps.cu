@@ -224,42 +224,26 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
     int issued = npan < NBUF ? npan : NBUF;  // panels whose copies have been started
     bool bad = false;
     int lost = -1;  // first panel whose data did not arrive
-    // The step constants land on mb[NS].  The sums carried from the previous batch are in
-    // shared memory already for panel 0 (CTA 0 formed them); those of panels 1.. are copied
-    // in on mb[NS + 1] while panel 0 runs, and added to the panels' running sums before
-    // panel 1.
-    bool corr_pending = NS > 1;
-    auto wait_corr = [&](bool record) -> bool {
-        const bool ok = mbar_wait(&mb[NS + 1], (phase >> (NS + 1)) & 1u, err, record);
-        if (ok) phase ^= 1u << (NS + 1);
-        corr_pending = false;
-        return ok;
-    };
-    if (!mbar_wait(&mb[NS], (phase >> NS) & 1u, err)) {
-        // give up: wait (bounded) for the copies still in flight
+    // the step constants land on mb[NS], the carried corrections on mb[NS + 1]
+    const bool pre_ok = mbar_wait(&mb[NS], (phase >> NS) & 1u, err);
+    if (pre_ok) phase ^= 1u << NS;
+    const bool corr_ok = pre_ok && mbar_wait(&mb[NS + 1], (phase >> (NS + 1)) & 1u, err);
+    if (corr_ok) phase ^= 1u << (NS + 1);
+    if (!corr_ok) {  // give up: wait (bounded) for the copies still in flight
         for (int s = 0; s < issued; s++)
             if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
                 phase ^= 1u << (s % NBUF);
-        if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
-        if (corr_pending) wait_corr(false);
+        if (!pre_ok && mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
+        if (mbar_wait(&mb[NS + 1], (phase >> (NS + 1)) & 1u, err, false))
+            phase ^= 1u << (NS + 1);
         return;
     }
-    phase ^= 1u << NS;
-    T acc[NS];  // correction sums: panel 0's start from the carried sums, the others from 0
-    acc[0] = acc0[lane];
+    T acc[NS];  // correction sums, starting from the corrections carried from the previous batch
 #pragma unroll
-    for (int s = 1; s < NS; s++) acc[s] = T(0);
+    for (int s = 0; s < NS; s++) acc[s] = acc0[s * 32 + lane];
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         if (s * 32 >= nb) break;
-        if (s == 1) {  // the carried sums of panels 1.. (copied while panel 0 ran)
-            if (!wait_corr(true)) {
-                lost = 1;
-                break;
-            }
-#pragma unroll
-            for (int s2 = 1; s2 < NS; s2++) acc[s2] += acc0[s2 * 32 + lane];
-        }
         // the coefficients of panel s (columns 32 s .. 32 s + 31) land on its buffer's mbarrier
         const int bi = s % NBUF;
         if (!mbar_wait(&mb[bi], (phase >> bi) & 1u, err)) {
@@ -311,7 +295,6 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
             if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
                 phase ^= 1u << (s % NBUF);
     }
-    if (corr_pending) wait_corr(false);  // copied but not needed (a batch of one panel)
     if (bad) set_err(err, DEV_NONFINITE);
 }
 
@@ -356,11 +339,9 @@ __device__ void phase_b(int nb, bool issued_ahead, const T *gcoef, const T *gpre
     if ((threadIdx.x >> 5) == 0) {
         if (threadIdx.x == 0) {
             if (!issued_ahead) phase_b_issue<T, NS>(nb, gcoef, gpre, scoef, spre, mb);
-            if (NS > 1) {  // panel 0's sums are in shared memory already
-                fence_proxy_async();
-                mbar_expect_tx(&mb[NS + 1], (uint32_t)((B - 32) * sizeof(T)));
-                bulk_load(scorr + 32, gcorr + 32, (uint32_t)((B - 32) * sizeof(T)), &mb[NS + 1]);
-            }
+            fence_proxy_async();
+            mbar_expect_tx(&mb[NS + 1], (uint32_t)(B * sizeof(T)));
+            bulk_load(scorr, gcorr, (uint32_t)(B * sizeof(T)), &mb[NS + 1]);
         }
         __syncwarp();
         forward_substitution<T, NS>(nb, spre, scorr, gcoef, scoef, mb, phase, mu, err);
@@ -566,50 +547,29 @@ __device__ __forceinline__ BatchMeta meta_at(unsigned char *base, int B, int whi
     return BatchMeta{p, p + B, p + 2 * B, p + 3 * B + 1};
 }
 
-// The first coordinate (of the next batch's correction sums) that warp `warp` of CTA `bid`
-// forms: the group's CTA 0 forms those of the first panel (l < 32, from l = warp, every
-// kWarps), the other CTAs the rest (from 32 + their global warp index, one warp per
-// coordinate).
-__device__ __forceinline__ int first_corr(unsigned bid, int warp) {
-    return bid == 0 ? warp : 32 + (int)((bid - 1) * kWarps) + warp;
-}
-
-// corr[l] = sum_{l'} X[l][l'] mu[l'] for l < nbn.  CTA 0 writes the first panel's sums
-// (l < 32) into its own shared memory (scorr), so that the next phase B starts without
-// waiting for them; the other CTAs write the rest to global memory (corr), from which phase
-// B copies them while it steps through the first panel.  The row of X of a warp's first
-// coordinate was loaded into xw before the cache update, so that its latency overlapped that
-// update.  The sums of padding coordinates are zeroed.
+// corr[l] = sum_{l'} X[l][l'] mu[l'] for l < nbn, one warp per coordinate over the grid;
+// the row of X of this warp's first coordinate (l = its global warp index) was loaded into
+// xw before the cache update, so that its latency overlapped that update.  The corrections
+// of padding coordinates are zeroed.
 template <typename T, int NS>
 __device__ void cross_corrections(int nbn, int nbk, const T *X, const T *smu, const T (&xw)[NS],
-                                  T *corr, T *scorr, unsigned bid, unsigned nblk) {
+                                  T *corr, unsigned bid, unsigned nblk) {
     constexpr int B = NS * 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int l_first = first_corr(bid, warp);
-    auto sum_row = [&](int l) -> T {
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)(bid * kWarps + (threadIdx.x >> 5));
+    const int gwarps = (int)(nblk * kWarps);
+    for (int l = gw; l < nbn; l += gwarps) {
         T acc = T(0);
 #pragma unroll
         for (int kk = 0; kk < NS; kk++) {
             const int l1 = lane + 32 * kk;
-            if (l1 < nbk)
-                acc = fma(l == l_first ? xw[kk] : __ldcg(X + (size_t)l * B + l1), smu[l1], acc);
+            if (l1 < nbk) acc = fma(l == gw ? xw[kk] : __ldcg(X + (size_t)l * B + l1), smu[l1], acc);
         }
-        return warp_sum(acc);
-    };
-    if (bid == 0) {
-        for (int l = warp; l < 32 && l < B; l += kWarps) {
-            const T v = l < nbn ? sum_row(l) : T(0);
-            if (lane == 0) scorr[l] = v;
-        }
-        return;
-    }
-    const int gwarps = (int)((nblk - 1) * kWarps);
-    for (int l = l_first; l < nbn; l += gwarps) {
-        const T v = sum_row(l);
-        if (lane == 0) corr[l] = v;
+        acc = warp_sum(acc);
+        if (lane == 0) corr[l] = acc;
     }
     if (bid == nblk - 1)
-        for (int l = (nbn > 32 ? nbn : 32) + threadIdx.x; l < B; l += blockDim.x) corr[l] = T(0);
+        for (int l = nbn + threadIdx.x; l < B; l += blockDim.x) corr[l] = T(0);
 }
 
 // The pass on a group of nblk CTAs of a cooperative launch, this CTA being number bid of
@@ -807,9 +767,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     bool pref = false;  // breg holds the batch after the current one
     phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
     if (bid == 0) {
-        T *scorr0 = reinterpret_cast<T *>(work) + coef_area(B) + PRE_N * B;
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
-        for (int l = threadIdx.x; l < 32 && l < B; l += blockDim.x) scorr0[l] = T(0);
         if (threadIdx.x == 0) {
             for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
             mbar_init_fence();
@@ -905,12 +863,11 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
             __syncthreads();
             T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
             {
-                const int lx = first_corr(bid, warp);
+                const int gw = (int)(bid * kWarps + warp);
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++) {
                     const int l1 = lane + 32 * kk;
-                    xw[kk] = (lx < nbn && lx < B && l1 < nbk) ? __ldcg(gX + (size_t)lx * B + l1)
-                                                              : T(0);
+                    xw[kk] = (gw < nbn && l1 < nbk) ? __ldcg(gX + (size_t)gw * B + l1) : T(0);
                 }
             }
             const int nseg = *cur.snseg;
@@ -945,10 +902,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 }
                 __syncwarp();  // this segment's writes before the next segment's reads
             }
-            if (nbn > 0)
-                cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr,
-                                         reinterpret_cast<T *>(work) + coef_area(B) + PRE_N * B,
-                                         bid, nblk);
+            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr, bid, nblk);
         }
         {
             // the indices of batch k + 2 are fetched while this barrier completes
@@ -1122,9 +1076,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     bool pref = false;  // breg holds the batch after the current one
     phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
     if (bid == 0) {
-        T *scorr0 = reinterpret_cast<T *>(work) + coef_area(B) + PRE_N * B;
         for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
-        for (int l = threadIdx.x; l < 32 && l < B; l += blockDim.x) scorr0[l] = T(0);
         if (threadIdx.x == 0) {
             for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
             mbar_init_fence();
@@ -1202,12 +1154,11 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
             __syncthreads();
             T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
             {
-                const int lx = first_corr(bid, warp);
+                const int gw = (int)(bid * kWarps + warp);
 #pragma unroll
                 for (int kk = 0; kk < NS; kk++) {
                     const int l1 = lane + 32 * kk;
-                    xw[kk] = (lx < nbn && lx < B && l1 < nbk) ? __ldcg(gX + (size_t)lx * B + l1)
-                                                              : T(0);
+                    xw[kk] = (gw < nbn && l1 < nbk) ? __ldcg(gX + (size_t)gw * B + l1) : T(0);
                 }
             }
             const int nseg = *cur.snseg;
@@ -1235,10 +1186,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                     }
                 }
             }
-            if (nbn > 0)
-                cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr,
-                                         reinterpret_cast<T *>(work) + coef_area(B) + PRE_N * B,
-                                         bid, nblk);
+            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr, bid, nblk);
         }
         {
             // the indices of batch k + 2 are fetched while this barrier completes
