@@ -343,6 +343,35 @@ def run_profile_sweep(args):
                                         "d_abs_sum": float(np.abs(D).sum())}}))
 
 
+def run_profile_theta(args):
+    """A bounded Theta coordinate pass at p = q = 5000, n = 1000 (S_xx, Delta V^T and Sigma,
+    100 MB each, exceed L2): every column of 40 rows spread evenly over the inputs (so that
+    the dot products' lengths average those of a whole pass), ~2e5 coordinates, run twice
+    through cggm_theta_sweep.  Used for ncu captures of the Theta sweep kernel."""
+    import numpy as np
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    p = q = 5000
+    n = 1000
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((n, p))
+    A = rng.standard_normal((q, q + 8)) / np.sqrt(q)
+    Sig = A @ A.T + np.eye(q)
+    Sxy = rng.standard_normal((p, q)) * 0.05
+    Th = np.zeros((p, q))
+    rows = np.arange(0, p, p // 40)[:40]
+    ti = np.repeat(rows, q).astype(np.int32)
+    tj = np.tile(np.arange(q), rows.size).astype(np.int32)
+    prec = cg.CGGM_MIXED if args.precision == "mixed" else cg.CGGM_FP64
+    with cg.Context(0) as ctx:
+        for _ in range(2):
+            T = ctx.cggm_theta_sweep(X, Sxy, Sig, Th, ti, tj, 0.01, precision=prec)
+    print(json.dumps({"profile_theta": {"p": p, "q": q, "n": n, "coordinates": int(ti.size),
+                                        "precision": args.precision,
+                                        "theta_abs_sum": float(np.abs(T).sum())}}))
+
+
 def run_profile_contract(args):
     """The tensor-core contraction alone at 8192 x 8192 x 4096 (3xTF32 split mode, the mode
     the mixed path uses), twice through cggm_contract: for ncu captures of gemm_tc_kernel."""
@@ -794,11 +823,15 @@ def main():
     ap.add_argument("--line-serve-max-iter", type=int, default=8)
     ap.add_argument("--profile-sweep", action="store_true",
                     help="run only a bounded Lambda pass at q=5000 (for ncu captures)")
+    ap.add_argument("--profile-theta", action="store_true",
+                    help="run only a bounded Theta pass at p = q = 5000 (for ncu captures)")
     ap.add_argument("--profile-contract", action="store_true",
                     help="run only the tensor-core contraction at 8192^2 x 4096 (for ncu captures)")
     args = ap.parse_args()
     if args.profile_sweep:
         run_profile_sweep(args)
+    elif args.profile_theta:
+        run_profile_theta(args)
     elif args.profile_contract:
         run_profile_contract(args)
     elif args.gap_trace > 0:
