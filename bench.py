@@ -372,6 +372,66 @@ def run_profile_theta(args):
                                         "theta_abs_sum": float(np.abs(T).sum())}}))
 
 
+def run_profile_chol(args):
+    """FP64 factorisation throughput: cggm_cholesky (Cholesky of Lambda, log det and Sigma =
+    Lambda^-1, the step every Newton iteration and every Armijo trial runs) on device buffers
+    at q = 5000 and 20000, timed with CUDA events; flops q^3/3 for the factor and 2 q^3/3 for
+    Sigma (W = L^-1 with a triangular right-hand side, then W^T W).  Beside it, cuBLAS's
+    double-precision GEMM rate (torch.matmul at 8192^3) as the reference FP64 rate."""
+    import ctypes
+    import torch
+    import paper_1509_04681_gb300 as cg
+    from paper_1509_04681_gb300 import build as pkg_build
+    pkg_build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    ctx = cg.Context(0, stream=stream.cuda_stream)
+    lib = cg.cggm._lib()
+    g = torch.Generator(device=dev).manual_seed(0)
+    out = {}
+    for q in (5000, 20000):
+        M = torch.randn(q, q, device=dev, dtype=torch.float64, generator=g) / q ** 0.5
+        Lam = M @ M.T + torch.eye(q, device=dev, dtype=torch.float64)
+        del M
+        L = torch.empty_like(Lam)
+        S = torch.empty_like(Lam)
+        ld = ctypes.c_double()
+        times = []
+        for rep in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = lib.cggm_cholesky(ctx._h, q, Lam.data_ptr(), L.data_ptr(), ctypes.byref(ld),
+                                   S.data_ptr(), cg.CGGM_FP64)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            assert st == 0, st
+            if rep:
+                times.append(e0.elapsed_time(e1) / 1e3)
+        sec = min(times)
+        flops = q ** 3 / 3 + 2 * q ** 3 / 3
+        out[f"q{q}"] = {"seconds": sec, "tflops": flops / sec / 1e12,
+                        "flops": "q^3/3 (factor) + 2 q^3/3 (Sigma)"}
+        del Lam, L, S
+        torch.cuda.empty_cache()
+    a = torch.randn(8192, 8192, device=dev, dtype=torch.float64, generator=g)
+    b = torch.randn(8192, 8192, device=dev, dtype=torch.float64, generator=g)
+    best = None
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(a, b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        best = t if best is None else min(best, t)
+    ref = 2 * 8192 ** 3 / best / 1e12
+    for k in out:
+        out[k]["frac_of_cublas_dgemm"] = out[k]["tflops"] / ref
+    ctx.close()
+    print(json.dumps({"profile_chol": out, "cublas_dgemm_tflops": ref}), flush=True)
+
+
 def run_profile_contract(args):
     """The tensor-core contraction alone at 8192 x 8192 x 4096 (3xTF32 split mode, the mode
     the mixed path uses), twice through cggm_contract: for ncu captures of gemm_tc_kernel."""
@@ -825,6 +885,8 @@ def main():
                     help="run only a bounded Lambda pass at q=5000 (for ncu captures)")
     ap.add_argument("--profile-theta", action="store_true",
                     help="run only a bounded Theta pass at p = q = 5000 (for ncu captures)")
+    ap.add_argument("--profile-chol", action="store_true",
+                    help="time the FP64 Cholesky and inverse against cuBLAS double GEMM")
     ap.add_argument("--profile-contract", action="store_true",
                     help="run only the tensor-core contraction at 8192^2 x 4096 (for ncu captures)")
     args = ap.parse_args()
@@ -832,6 +894,8 @@ def main():
         run_profile_sweep(args)
     elif args.profile_theta:
         run_profile_theta(args)
+    elif args.profile_chol:
+        run_profile_chol(args)
     elif args.profile_contract:
         run_profile_contract(args)
     elif args.gap_trace > 0:
