@@ -44,15 +44,17 @@ class EdgeMatch:
     solves: int
 
 
-def lambdas_for_edges(ctx, X, Y, target_L: int, target_T: int, lam_lo: float = 1e-3,
-                      lam_hi: float = 1.0, rounds: int = 14, rel_tol: float = 0.05,
+def lambdas_for_edges(ctx, X, Y, target_L: int, target_T: int, lam_lo: float = 1e-4,
+                      lam_hi: float = 1e3, rounds: int = 20, rel_tol: float = 0.05,
                       tol: float = 0.01, opts=None) -> EdgeMatch:
     """lambda_Lambda and lambda_Theta whose solution has about target_L edges in Lambda and
     target_T in Theta (Section 5's choice of the penalties).  Each round solves at the current
     pair (warm-started from the previous solution) and halves, on a log scale, the bracket
     of each penalty whose edge count is off by more than rel_tol: fewer edges than wanted
     means the penalty is too large.  The two counts depend mostly on their own penalty, so
-    the brackets are narrowed side by side.  Returns the closest pair found."""
+    the brackets are narrowed side by side.  The default bracket, 1e-4 to 1e3, spans the
+    gradients' scale for data of unit-order variance (the penalty that empties an active set
+    is the largest gradient entry).  Returns the closest pair found."""
     lo = [math.log(lam_lo), math.log(lam_lo)]
     hi = [math.log(lam_hi), math.log(lam_hi)]
     cur = [0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1])]
