@@ -556,6 +556,56 @@ cggm_status cggm_permute_csr(int64_t q, const int64_t *row_ptr, const int32_t *c
 cggm_status cggm_chol_supernodes(int64_t q, const int32_t *parent, const int64_t *colcount,
                                  int64_t *start_out, int64_t *nsuper_out);
 
+/* Numeric sparse Cholesky factorisation in double precision on the GPU.  Section 4 keeps
+ * Lambda sparse in the block regime of Algorithm 2, and the Armijo rule of Algorithm 1
+ * needs log det(Lambda + alpha D) and the positive definiteness that a Cholesky factor
+ * certifies (Section 2.3 takes both from the factor); columns of Sigma = Lambda^-1 follow
+ * from two triangular solves with it.  With the pivot order P (perm[k] = the original
+ * index of pivot k), P A P^T = L L^T, L lower triangular with a positive diagonal (so L is
+ * unique).  L is stored by supernodes (cggm_chol_supernodes): supernode s owns pivots
+ * super_start[s] .. super_start[s+1]-1 (nc of them) and its rows rows[rows_ptr[s] ..
+ * rows_ptr[s+1]) (nr of them, its own pivots first, ascending), and keeps the dense nr x nc
+ * block L[rows, own pivots] row-major at blocks[block_ptr[s] ..]; the strict upper triangle
+ * of its top nc x nc square is zero.
+ *
+ * cggm_spchol_create: symbolic analysis (host: cggm_chol_symbolic, cggm_chol_supernodes,
+ *   cggm_chol_structure) of a q x q symmetric pattern and the device structures of the
+ *   numeric work, on the context's device.
+ *   row_ptr (q + 1), col: the matrix in CSR (host memory), both triangles or the lower one:
+ *   the values used are those of entries with col <= row (the lower triangle with the
+ *   diagonal); entries above the diagonal only add to the pattern.  ordering, perm_in: as
+ *   for cggm_chol_symbolic.  *out: the plan, released by cggm_spchol_destroy, which must be
+ *   called before the context is destroyed; one thread at a time per plan, and it shares
+ *   the context's stream.
+ *   Errors: CGGM_EINVAL (q < 1, a null pointer, a malformed CSR, a bad ordering or perm_in),
+ *   CGGM_ENOMEM (device memory, or one supernode's block beyond 2^31 entries).
+ * cggm_spchol_factor: factor the matrix with values val (row_ptr[q] doubles in the CSR
+ *   order given to cggm_spchol_create, host or device memory; repeated entries add up).
+ *   logdet_out (optional): log det A = 2 sum_k log L_kk.  Errors: CGGM_ENOTPD (a pivot not
+ *   positive: A is not positive definite), CGGM_ENONFINITE (a value not finite),
+ *   CGGM_ETIMEDOUT (a device-side wait gave up), CGGM_EINVAL.
+ * cggm_spchol_solve: X = A^-1 B with the last successful factorisation.  B: q x k row-major
+ *   double (host or device), or NULL for the identity columns c0 .. c0 + k - 1 (then X =
+ *   Sigma[:, c0 : c0 + k]); X: q x k row-major double (host or device).  CGGM_EINVAL for
+ *   k < 1, columns outside [0, q) or no factorisation yet.
+ * cggm_spchol_export: the structure and the factor (host memory, each output optional):
+ *   nsuper, nblock (entries of blocks), nnz_L (entries of L); perm (q), super_start,
+ *   rows_ptr and block_ptr (nsuper + 1 each), rows (rows_ptr[nsuper]), blocks (nblock;
+ *   CGGM_EINVAL before a successful factorisation).
+ * cggm_spchol_destroy: releases the plan (NULL is allowed). */
+typedef struct cggm_spchol cggm_spchol;
+cggm_status cggm_spchol_create(cggm_ctx *ctx, int64_t q, const int64_t *row_ptr,
+                               const int32_t *col, int ordering, const int32_t *perm_in,
+                               cggm_spchol **out);
+cggm_status cggm_spchol_factor(cggm_spchol *f, const double *val, double *logdet_out);
+cggm_status cggm_spchol_solve(cggm_spchol *f, int64_t k, const double *B, int64_t c0,
+                              double *X);
+cggm_status cggm_spchol_export(cggm_spchol *f, int64_t *nsuper_out, int64_t *nblock_out,
+                               int64_t *nnz_L_out, int32_t *perm_out,
+                               int64_t *super_start_out, int64_t *rows_ptr_out,
+                               int32_t *rows_out, int64_t *block_ptr_out, double *blocks_out);
+cggm_status cggm_spchol_destroy(cggm_spchol *f);
+
 /*
  * No-allocation variant of cggm_lambda_sweep (the paper has no counterpart: this is an
  * interface for embedding).  Some callers cannot call cudaMalloc: code that runs under

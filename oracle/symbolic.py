@@ -117,3 +117,14 @@ def minimum_degree_order(A: np.ndarray, dense_rest: float = 0.9) -> np.ndarray:
         G[:, v] = False
         order.append(v)
     return np.array(order, dtype=np.int64)
+
+
+def numeric_factor(A: np.ndarray, perm):
+    """The numeric factor the sparse Cholesky computes, by its definition: L lower
+    triangular with a positive diagonal and L L^T = P A P^T (A symmetric positive definite,
+    dense; perm[k] = original index of pivot k), which fixes L uniquely.  Returns
+    (L, log det A) with log det A = 2 sum_k log L_kk (Section 2.3 takes log det from the
+    factor).  LAPACK's dense Cholesky is the library step."""
+    perm = np.asarray(perm)
+    L = np.linalg.cholesky(A[np.ix_(perm, perm)])
+    return L, 2.0 * float(np.sum(np.log(np.diag(L))))

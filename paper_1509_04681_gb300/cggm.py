@@ -36,7 +36,8 @@ EXPORTED = [
     "cggm_spd_solve", "cggm_grad_lambda_block", "cggm_tuned_batch", "cggm_partition_columns",
     "cggm_partition_theta_columns", "cggm_chol_symbolic", "cggm_chol_supernodes",
     "cggm_block_order", "cggm_permute_csr", "cggm_chol_structure", "cggm_tuner_save",
-    "cggm_tuner_load", "cggm_block_count",
+    "cggm_tuner_load", "cggm_block_count", "cggm_spchol_create", "cggm_spchol_factor",
+    "cggm_spchol_solve", "cggm_spchol_export", "cggm_spchol_destroy",
 ]
 
 
@@ -162,6 +163,12 @@ def _lib():
         lib.cggm_tuner_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(i64)]
         lib.cggm_block_count.argtypes = [ip, i64, i64, i64, ctypes.POINTER(i64),
                                          ctypes.POINTER(i64)]
+        lib.cggm_spchol_create.argtypes = [vp, i64, vp, vp, ip, vp, ctypes.POINTER(vp)]
+        lib.cggm_spchol_factor.argtypes = [vp, vp, ctypes.POINTER(dbl)]
+        lib.cggm_spchol_solve.argtypes = [vp, i64, vp, i64, vp]
+        lib.cggm_spchol_export.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                           ctypes.POINTER(i64), vp, vp, vp, vp, vp, vp]
+        lib.cggm_spchol_destroy.argtypes = [vp]
         for name in EXPORTED:
             f = getattr(lib, name)
             if f.restype is ctypes.c_int or name in ("cggm_create", "cggm_solve",
@@ -493,6 +500,11 @@ class Context:
         _check(st, "cggm_spd_solve", (CGGM_OK, CGGM_EMAXITER) if allow_maxiter else (CGGM_OK,))
         return X, it.value, res.value
 
+    def cggm_spchol(self, indptr, indices, ordering=CGGM_ORDER_AMD, perm=None):
+        """Sparse Cholesky plan (cggm_spchol_create) for the q x q pattern in CSR; see
+        SparseCholesky."""
+        return SparseCholesky(self, indptr, indices, ordering, perm)
+
     def cggm_grad_lambda_block(self, X, Y, indptr, indices, data, Th, c0, k, tol=1e-10,
                                max_iter=1000):
         """Columns c0 .. c0 + k - 1 of the Lambda gradient from the sparse Lambda (CSR) by
@@ -536,6 +548,89 @@ def tuned_batch(q: int, m: int, precision: int) -> int:
 def _host_i32(a):
     a = np.ascontiguousarray(a, dtype=np.int32)
     return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+class SparseCholesky:
+    """Numeric sparse Cholesky in double precision on the context's GPU (cggm_spchol_*):
+    P A P^T = L L^T for a q x q symmetric matrix in CSR whose lower triangle (with the
+    diagonal) carries the values.  factor(values) returns log det A; solve() gives A^-1 B
+    or columns of A^-1; export() the supernodal structure and blocks; dense_factor() L as a
+    dense q x q array in pivot order (small cases)."""
+
+    def __init__(self, ctx, indptr, indices, ordering=CGGM_ORDER_AMD, perm=None):
+        rp = np.ascontiguousarray(indptr, dtype=np.int64)
+        self.q = q = rp.size - 1
+        self.nnz = int(rp[-1]) if q >= 0 else 0
+        ci, pci = _host_i32(indices)
+        ppi = None
+        if perm is not None:
+            perm, ppi = _host_i32(perm)
+        self._ctx = ctx
+        self._h = ctypes.c_void_p()
+        _check(_lib().cggm_spchol_create(ctx._h, q, rp.ctypes.data_as(ctypes.c_void_p), pci,
+                                         int(ordering), ppi, ctypes.byref(self._h)),
+               "cggm_spchol_create")
+
+    def factor(self, values) -> float:
+        v = _Arr(values, np.float64)
+        ld = ctypes.c_double()
+        _check(_lib().cggm_spchol_factor(self._h, v.ptr, ctypes.byref(ld)), "cggm_spchol_factor")
+        return ld.value
+
+    def solve(self, B=None, c0=0, k=None):
+        if B is not None:
+            b = _Arr(B, np.float64)
+            k = b.obj.shape[1] if b.obj.ndim == 2 else 1
+        X = np.empty((self.q, int(k)))
+        _check(_lib().cggm_spchol_solve(self._h, int(k), b.ptr if B is not None else None,
+                                        int(c0), X.ctypes.data), "cggm_spchol_solve")
+        return X
+
+    def export(self, blocks=True) -> dict:
+        ns, nb, nl = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        lib = _lib()
+        _check(lib.cggm_spchol_export(self._h, ctypes.byref(ns), ctypes.byref(nb),
+                                      ctypes.byref(nl), None, None, None, None, None, None),
+               "cggm_spchol_export")
+        out = {"nsuper": ns.value, "nblock": nb.value, "nnz_L": nl.value,
+               "perm": np.empty(self.q, np.int32), "super_start": np.empty(ns.value + 1, np.int64),
+               "rows_ptr": np.empty(ns.value + 1, np.int64),
+               "block_ptr": np.empty(ns.value + 1, np.int64)}
+        _check(lib.cggm_spchol_export(self._h, None, None, None, out["perm"].ctypes.data,
+                                      out["super_start"].ctypes.data, out["rows_ptr"].ctypes.data,
+                                      None, out["block_ptr"].ctypes.data, None),
+               "cggm_spchol_export")
+        out["rows"] = np.empty(int(out["rows_ptr"][-1]), np.int32)
+        blk = np.empty(nb.value) if blocks else None
+        _check(lib.cggm_spchol_export(self._h, None, None, None, None, None, None,
+                                      out["rows"].ctypes.data, None,
+                                      blk.ctypes.data if blocks else None),
+               "cggm_spchol_export")
+        out["blocks"] = blk
+        return out
+
+    def dense_factor(self):
+        """L (pivot order) as a dense q x q array from the exported blocks."""
+        e = self.export()
+        L = np.zeros((self.q, self.q))
+        for s in range(e["nsuper"]):
+            f, l = int(e["super_start"][s]), int(e["super_start"][s + 1])
+            rows = e["rows"][e["rows_ptr"][s]:e["rows_ptr"][s + 1]]
+            nc = l - f
+            blk = e["blocks"][e["block_ptr"][s]:e["block_ptr"][s + 1]].reshape(rows.size, nc)
+            L[np.ix_(rows, np.arange(f, l))] = blk
+        return np.tril(L)
+
+    def close(self):
+        if self._h:
+            _lib().cggm_spchol_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def partition_columns(q: int, ei, ej, max_block: int, w=None):

@@ -20,6 +20,7 @@
 #include "gemm_tc.cuh"
 #include "iter.cuh"
 #include "load.cuh"
+#include "spchol.cuh"
 #include "sweeps.cuh"
 
 using namespace cggm;
@@ -1584,3 +1585,55 @@ cggm_status cggm_contract(cggm_ctx *c, int64_t M, int64_t N, int64_t K, float al
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------
+// Numeric sparse Cholesky (spchol.cu): a plan bound to a context's device and stream.
+// ---------------------------------------------------------------------------------
+struct cggm_spchol {
+    cggm_ctx *ctx;
+    SpCholPlan *plan;
+};
+
+extern "C" cggm_status cggm_spchol_create(cggm_ctx *c, int64_t q, const int64_t *row_ptr,
+                                          const int32_t *col, int ordering,
+                                          const int32_t *perm_in, cggm_spchol **out) {
+    if (!out) return CGGM_EINVAL;
+    *out = nullptr;
+    if (!c) return CGGM_EINVAL;
+    CGGM_TRY(set_device(c));
+    SpCholPlan *p = nullptr;
+    CGGM_TRY(spchol_analyse(c->device, q, row_ptr, col, ordering, perm_in, &p));
+    *out = new cggm_spchol{c, p};
+    return CGGM_OK;
+}
+
+extern "C" cggm_status cggm_spchol_factor(cggm_spchol *f, const double *val,
+                                          double *logdet_out) {
+    if (!f) return CGGM_EINVAL;
+    CGGM_TRY(set_device(f->ctx));
+    return spchol_factor(f->plan, val, logdet_out, f->ctx->st);
+}
+
+extern "C" cggm_status cggm_spchol_solve(cggm_spchol *f, int64_t k, const double *B,
+                                         int64_t c0, double *X) {
+    if (!f) return CGGM_EINVAL;
+    CGGM_TRY(set_device(f->ctx));
+    return spchol_solve(f->plan, k, B, c0, X, f->ctx->st);
+}
+
+extern "C" cggm_status cggm_spchol_export(cggm_spchol *f, int64_t *nsuper_out,
+                                          int64_t *nblock_out, int64_t *nnz_L_out,
+                                          int32_t *perm_out, int64_t *super_start_out,
+                                          int64_t *rows_ptr_out, int32_t *rows_out,
+                                          int64_t *block_ptr_out, double *blocks_out) {
+    if (!f) return CGGM_EINVAL;
+    return spchol_export(f->plan, nsuper_out, nblock_out, nnz_L_out, perm_out, super_start_out,
+                         rows_ptr_out, rows_out, block_ptr_out, blocks_out, f->ctx->st);
+}
+
+extern "C" cggm_status cggm_spchol_destroy(cggm_spchol *f) {
+    if (!f) return CGGM_OK;
+    spchol_free(f->plan);
+    delete f;
+    return CGGM_OK;
+}

@@ -133,3 +133,50 @@ def test_minimum_degree_dense_rest():
     A[0, 1] = A[1, 0] = False                           # degrees 78, 78, then 79 ...
     order = symbolic.minimum_degree_order(A)
     assert order.tolist() == list(range(q))
+
+
+# ---- the numeric factor (oracle.symbolic.numeric_factor) ----
+
+def second_difference(q):
+    """T_q: 2 on the diagonal, -1 beside it; det T_q = q + 1."""
+    return 2.0 * np.eye(q) - np.eye(q, k=1) - np.eye(q, k=-1)
+
+
+@pytest.mark.parametrize("q", [1, 2, 7, 50])
+def test_numeric_factor_second_difference_closed_form(q):
+    L, ld = symbolic.numeric_factor(second_difference(q), np.arange(q))
+    k = np.arange(q)
+    # the recurrence d_k = 2 - 1 / d_{k-1}, d_0 = 2, gives d_k = (k + 2) / (k + 1)
+    np.testing.assert_allclose(np.diag(L), np.sqrt((k + 2) / (k + 1)), rtol=1e-14)
+    np.testing.assert_allclose(np.diag(L, -1), -np.sqrt((k[:-1] + 1) / (k[:-1] + 2)),
+                               rtol=1e-14)
+    assert abs(ld - np.log(q + 1)) <= 1e-13 * max(1.0, np.log(q + 1))
+
+
+def test_numeric_factor_any_pivot_order_same_determinant():
+    q = 40
+    rng = np.random.default_rng(5)
+    perm = rng.permutation(q)
+    A = second_difference(q)
+    L, ld = symbolic.numeric_factor(A, perm)
+    assert abs(ld - np.log(q + 1)) <= 1e-12
+    np.testing.assert_allclose(L @ L.T, A[np.ix_(perm, perm)], atol=1e-13)
+    assert np.all(np.triu(L, 1) == 0) and np.all(np.diag(L) > 0)
+
+
+def test_numeric_factor_against_lu_determinant():
+    import scipy.linalg as sla
+    import synth
+    rng = np.random.default_rng(11)
+    q = 80
+    A = synth.random_sparse_precision(q, 4.0, rng, base=synth.chain_precision(q)).toarray()
+    perm = rng.permutation(q)
+    L, ld = symbolic.numeric_factor(A, perm)
+    lu, piv = sla.lu_factor(A)  # a different factorisation of the same matrix
+    sign = np.prod(np.sign(np.diag(lu))) * (-1) ** np.count_nonzero(piv != np.arange(q))
+    assert sign > 0
+    assert abs(ld - np.sum(np.log(np.abs(np.diag(lu))))) <= 1e-11 * abs(ld)
+    np.testing.assert_allclose(L @ L.T, A[np.ix_(perm, perm)], atol=1e-12)
+    # its nonzeros lie inside the elimination game's pattern for the same order
+    P = symbolic.cholesky_pattern(A != 0, perm)
+    assert not np.any((np.abs(L) > 0) & ~P)
