@@ -58,6 +58,10 @@ inline void note_launch() { __atomic_add_fetch(&launch_counter(), 1, __ATOMIC_RE
 // ---------------------------------------------------------------------------------
 struct GridBarrier {
     unsigned long long arrived;  // arrivals since the launch (zeroed before it); monotonic
+    // pipelined coordinate passes (sweeps.cu), all monotonic from zero: batches whose steps
+    // CTA 0 has published, and the phase-A and phase-C completions of the other CTAs (one
+    // per CTA and batch)
+    unsigned long long mu_ready, a_done, c_done;
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -127,6 +131,41 @@ __device__ __forceinline__ bool grid_wait(GridBarrier *bar, int *err, GridTicket
     }
     __syncthreads();
     return s_ok != 0;
+}
+
+// Every thread of the CTA: waits (thread 0 polls, acquire) until *c1 >= t1 and, when c2 is
+// given, *c2 >= t2; bounded by deadline_ns, and left early when the error word is nonzero.
+// Returns false on failure (DEV_TIMEOUT recorded when the deadline passed).
+__device__ __forceinline__ bool cta_wait_counts(const unsigned long long *c1,
+                                                unsigned long long t1,
+                                                const unsigned long long *c2,
+                                                unsigned long long t2, int *err,
+                                                uint64_t deadline_ns = 2000000000ull) {
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint64_t t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u64(c1) < t1 || (c2 && ld_acquire_u64(c2) < t2)) {
+            if ((++spins & 63u) == 0) {
+                if (ld_acquire_int(err) != 0) { ok = 0; break; }
+                if (global_ns() - t0 > deadline_ns) {
+                    atomicCAS(err, 0, (int)DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        if (ok && ld_acquire_int(err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Thread 0, after a __syncthreads that ends the CTA's part of a step: counts it (release).
+__device__ __forceinline__ void cta_count(unsigned long long *c) {
+    if (threadIdx.x == 0) red_release_add(c, 1ull);
 }
 
 __device__ __forceinline__ bool grid_sync(GridBarrier *bar, int *err, unsigned nblocks,

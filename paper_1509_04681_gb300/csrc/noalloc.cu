@@ -19,8 +19,8 @@ constexpr size_t OFF_G = 0;                                                   //
 constexpr size_t OFF_U = align256(OFF_G + 8 * kMaxQ * kMaxQ);                 // q x q double
 constexpr size_t OFF_SD = align256(OFF_U + 8 * kMaxQ * kMaxQ);                // q double
 constexpr size_t OFF_PD = align256(OFF_SD + 8 * kMaxQ);                       // q double
-constexpr size_t OFF_MU = align256(OFF_PD + 8 * kMaxQ);                       // B double
-constexpr size_t OFF_SUB1 = align256(OFF_MU + 8 * kBatch);                    // step constants
+constexpr size_t OFF_MU = align256(OFF_PD + 8 * kMaxQ);                       // 2 B double
+constexpr size_t OFF_SUB1 = align256(OFF_MU + 8 * 2 * kBatch);                // step constants
 constexpr size_t kSub1 = scratch_sub1_bytes(kBatch, sizeof(double));
 constexpr size_t OFF_SUB2 = align256(OFF_SUB1 + kSub1);                       // coefficients
 constexpr size_t kSub2 = scratch_sub2_bytes(kBatch, sizeof(double));

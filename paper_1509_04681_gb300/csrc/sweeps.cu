@@ -15,13 +15,14 @@
 //           the same batch, and those corrections are bilinear in the coefficients, so
 //           the warp applies them exactly (forward substitution with a soft-threshold
 //           at every step).
-//   phase C (all CTAs): applies the batch's B updates to the cache rows.
-// Phase A of batch k+1 runs on CTAs 1.. while CTA 0 runs phase B of batch k; the cache it
-// reads then lacks batch k's update, and the missing part of each dot product is
-// sum_l X(k+1, k)[., l] mu_l over batch k's steps mu, with coefficients X of the same form
-// as the in-batch ones.  Phase C forms that sum once mu is known, and phase B of batch k+1
-// starts its correction sums from it.  Grid barriers separate B from C and C from the
-// next B.
+//   phase C (CTAs 1..): applies the batch's B updates to the cache rows.
+// The phases are pipelined two deep: CTA 0 runs phase B of batch k while the other CTAs
+// apply batch k - 1 to the cache (phase C) and then run phase A of batch k + 1 against the
+// cache as it stands after batch k - 1.  The missing part of each of batch k + 1's dot
+// products is sum_l X(k+1, k)[., l] mu_l over batch k's steps mu, with coefficients X of the
+// same form as the in-batch ones; CTA 0's other warps form it during phase B of batch k + 1,
+// panel by panel ahead of the steps.  CTA 0 and the other CTAs are ordered by counters, not
+// by grid barriers: CTA 0 waits only for the phase A of the batch it runs next.
 #include "sweeps.cuh"
 #include "mbar.cuh"
 
@@ -54,6 +55,8 @@ constexpr int kDotWarps = 4;
 constexpr int kDotThreads = kDotWarps * 32;
 constexpr int kCoefThreads = kThreads - kDotThreads;
 constexpr int kBarDots = 1;
+// Phase B on CTA 0: warps 1 .. kWarps - 1 (the carried corrections) on named barrier kBarCorr.
+constexpr int kBarCorr = 2;
 
 __device__ __forceinline__ void bar_sync_n(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -165,12 +168,11 @@ __host__ __device__ __forceinline__ int panel_off(int s, int B) {
 
 
 struct SmemLayout {
-    size_t meta;  // twice (current and next batch): sa[B], sb[B], sseg[B + 1], nseg (ints)
+    size_t meta;  // three batches (k, k + 1, k + 2): sa[B], sb[B], sseg[B + 1], nseg (ints)
     size_t work;  // union: phase A ring of row chunks (kRingBytes, all stages);
-                  //        phase B coefficient panels [coef_area(B)], step constants
-                  //          [PRE_N][B], corr[B] (T), then, beyond them,
-                  //        phase C mu[B] (T) at work + phc: CTA 0 copies the next batch's
-                  //          phase-B data in while its phase C runs
+                  //        phase B (CTA 0) coefficient panels [coef_area(B)], step constants
+                  //          [PRE_N][B], carried corrections [B] (T);
+                  //        phase C (the other CTAs) mu[B] (T) at work + phc
     size_t phc;   // offset of phase C's area within the work area
     size_t total;
 };
@@ -179,7 +181,7 @@ template <typename T>
 __host__ __device__ inline SmemLayout smem_layout(int B) {
     SmemLayout s;
     s.meta = 0;
-    size_t off = (size_t)2 * (3 * B + 2) * sizeof(int32_t);  // two batches' metadata
+    size_t off = (size_t)3 * (3 * B + 2) * sizeof(int32_t);  // three batches' metadata
     off = (off + 15) & ~size_t(15);
     s.work = off;
     const size_t phb = (((size_t)coef_area(B) + PRE_N * B + B + 8) * sizeof(T) + 15) & ~size_t(15);
@@ -209,10 +211,24 @@ __device__ __forceinline__ void issue_panel(int s, const T *gcoef, T *scoef, uin
     bulk_load(scoef + panel_off(s, B), gcoef + c0, bytes, bar);
 }
 
+// Thread of warp 0: waits (bounded) until the shared-memory flag reaches `target`; the flag
+// is raised by other warps of the same CTA, which wait for nothing outside it.
+__device__ __forceinline__ bool wait_block_flag(volatile int *flag, int target, int *err) {
+    if (*flag >= target) return true;
+    const uint64_t t0 = global_ns();
+    while (*flag < target) {
+        if (global_ns() - t0 > 2000000000ull) {
+            set_err(err, DEV_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
 template <typename T, int NS>
-__device__ void forward_substitution(int nb, const T *__restrict__ pre, const T *acc0,
-                                     const T *gcoef, T *coef, uint64_t *mb, uint32_t &phase,
-                                     double *mu_out, int *err) {
+__device__ void forward_substitution(int nb, const T *__restrict__ pre, const T *corr,
+                                     volatile int *corr_ready, const T *gcoef, T *coef,
+                                     uint64_t *mb, uint32_t &phase, double *mu_out, int *err) {
     // pre[] holds zeros for padding coordinates l >= nb, which give mu = 0 whatever the
     // correction sum (also a non-finite one: fmin / fmax return the other operand), so
     // panels run all 32 steps without branches.  B is a compile-time constant, so that every coefficient address
@@ -224,23 +240,21 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
     int issued = npan < NBUF ? npan : NBUF;  // panels whose copies have been started
     bool bad = false;
     int lost = -1;  // first panel whose data did not arrive
-    // the step constants land on mb[NS], the carried corrections on mb[NS + 1]
+    // the step constants land on mb[NS]
     const bool pre_ok = mbar_wait(&mb[NS], (phase >> NS) & 1u, err);
     if (pre_ok) phase ^= 1u << NS;
-    const bool corr_ok = pre_ok && mbar_wait(&mb[NS + 1], (phase >> (NS + 1)) & 1u, err);
-    if (corr_ok) phase ^= 1u << (NS + 1);
-    if (!corr_ok) {  // give up: wait (bounded) for the copies still in flight
+    if (!pre_ok) {  // give up: wait (bounded) for the copies still in flight
         for (int s = 0; s < issued; s++)
             if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
                 phase ^= 1u << (s % NBUF);
-        if (!pre_ok && mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
-        if (mbar_wait(&mb[NS + 1], (phase >> (NS + 1)) & 1u, err, false))
-            phase ^= 1u << (NS + 1);
+        if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
         return;
     }
-    T acc[NS];  // correction sums, starting from the corrections carried from the previous batch
+    // correction sums: the in-batch steps of earlier panels, then, when panel s starts, the
+    // part the previous batch carries into it (corr, formed by the CTA's other warps)
+    T acc[NS];
 #pragma unroll
-    for (int s = 0; s < NS; s++) acc[s] = acc0[s * 32 + lane];
+    for (int s = 0; s < NS; s++) acc[s] = T(0);
 #pragma unroll
     for (int s = 0; s < NS; s++) {
         if (s * 32 >= nb) break;
@@ -251,6 +265,11 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
             break;
         }
         phase ^= 1u << bi;
+        if (!wait_block_flag(corr_ready, s + 1, err)) {
+            lost = s + 1;  // panel s's copy has landed
+            break;
+        }
+        acc[s] += corr[s * 32 + lane];
         const int lo = s * 32 + lane;
         const T vph = pre[PRE_VPH * B + lo], vpl = pre[PRE_VPL * B + lo];
         const T vmh = pre[PRE_VMH * B + lo], vml = pre[PRE_VML * B + lo];
@@ -300,8 +319,8 @@ __device__ void forward_substitution(int nb, const T *__restrict__ pre, const T 
 
 // Starts (one thread) the bulk copies of a batch's step constants (landing on mb[NS]) and of
 // its coefficient panels that the buffers hold (panel s on mb[s % buffers]) into shared
-// memory.  The sources were written by other CTAs, ordered before this point by a grid
-// barrier; the destination was last read through the generic proxy.
+// memory.  The sources were written by other CTAs, ordered before this point by the wait
+// for their phase A; the destination was last read through the generic proxy.
 template <typename T, int NS>
 __device__ __forceinline__ void phase_b_issue(int nb, const T *gcoef, const T *gpre, T *scoef,
                                               T *spre, uint64_t *mb) {
@@ -312,40 +331,76 @@ __device__ __forceinline__ void phase_b_issue(int nb, const T *gcoef, const T *g
     for (int s = 0; s * 32 < nb && s < panel_bufs(B); s++) issue_panel<T, NS>(s, gcoef, scoef, mb);
 }
 
-// Waits (bounded, thread 0) for the copies phase_b_issue started, on a path that leaves the
-// kernel before phase B would have consumed them.
+// Warps 1 .. kWarps - 1 of CTA 0 during phase B of batch k: the corrections that batch k - 1
+// carries into batch k, corr[l] = sum_{l'} X(k, k-1)[l][l'] mu_{l'} (the missing part of the
+// dot products phase A of batch k formed while batch k - 1's steps were not yet applied),
+// panel by panel, raising *ready to s + 1 when the 32 rows of panel s are in corr; rows of
+// padding coordinates get zero.  X = nullptr: nothing carried (the first batch).
 template <typename T, int NS>
-__device__ void phase_b_drain(int nb, uint64_t *mb, uint32_t &phase, int *err) {
+__device__ void carried_corrections(int nb, const T *X, const double *mu_prev, int nbp, T *corr,
+                                    volatile int *ready) {
     constexpr int B = NS * 32;
-    for (int s = 0; s * 32 < nb && s < panel_bufs(B); s++)
-        if (mbar_wait(&mb[s], (phase >> s) & 1u, err, false)) phase ^= 1u << s;
-    if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
+    constexpr int NW = kWarps - 1;
+    constexpr int RW = (32 + NW - 1) / NW;  // rows of a panel per warp
+    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) - 1;
+    T muv[NS];
+#pragma unroll
+    for (int kk = 0; kk < NS; kk++) {
+        const int l1 = lane + 32 * kk;
+        muv[kk] = (X && l1 < nbp) ? (T)__ldcg(mu_prev + l1) : T(0);
+    }
+    for (int s = 0; s * 32 < nb; s++) {
+        T x[RW][NS];
+#pragma unroll
+        for (int r = 0; r < RW; r++) {
+            const int l = s * 32 + w + NW * r;
+#pragma unroll
+            for (int kk = 0; kk < NS; kk++) {
+                const int l1 = lane + 32 * kk;
+                x[r][kk] = (X && w + NW * r < 32 && l < nb && l1 < nbp)
+                               ? __ldcg(X + (size_t)l * B + l1) : T(0);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RW; r++) {
+            const int l = s * 32 + w + NW * r;
+            T acc = T(0);
+#pragma unroll
+            for (int kk = 0; kk < NS; kk++) acc = fma(x[r][kk], muv[kk], acc);
+            acc = warp_sum(acc);
+            if (lane == 0 && w + NW * r < 32) corr[l] = acc;
+        }
+        bar_sync_n(kBarCorr, NW * 32);  // the panel's rows are all written
+        if (threadIdx.x == 32) {
+            __threadfence_block();
+            *ready = s + 1;
+        }
+    }
 }
 
-// Phase B body shared by both passes.  The batch's step constants and first panels were
-// copied in during the previous batch's phase C (issued_ahead), or are copied now; the
-// carried corrections, formed in that phase C, are copied now (mb[NS + 1]).  Warp 0 runs
-// the substitution, starting each panel as soon as its coefficients have landed.  The step
-// constants of padding coordinates (l >= nb) and their corrections were written in global
+// Phase B of batch k on CTA 0.  Thread 0 starts the bulk copies of the batch's step constants
+// and first coefficient panels (their sources were completed by the other CTAs, ordered
+// before this point by the wait for their phase A); warp 0 runs the substitution, starting
+// each panel once its coefficients have landed and its carried corrections are formed by the
+// other warps.  The step constants of padding coordinates (l >= nb) were written in global
 // memory with the batch, so the copies bring whole arrays.  Coefficient slots of padding
 // coordinates are never used by a real coordinate: they only reach the correction sums of
 // padding coordinates.
 template <typename T, int NS>
-__device__ void phase_b(int nb, bool issued_ahead, const T *gcoef, const T *gpre,
-                        const T *gcorr, T *scoef, T *spre, uint64_t *mb, uint32_t &phase,
-                        double *mu, int *err) {
+__device__ void phase_b(int nb, const T *gcoef, const T *gpre, const T *X, const double *mu_prev,
+                        int nbp, T *scoef, T *spre, uint64_t *mb, uint32_t &phase, double *mu,
+                        int *err, volatile int *s_ready) {
     constexpr int B = NS * 32;
     T *scorr = spre + PRE_N * B;
-    if ((threadIdx.x >> 5) == 0) {
-        if (threadIdx.x == 0) {
-            if (!issued_ahead) phase_b_issue<T, NS>(nb, gcoef, gpre, scoef, spre, mb);
-            fence_proxy_async();
-            mbar_expect_tx(&mb[NS + 1], (uint32_t)(B * sizeof(T)));
-            bulk_load(scorr, gcorr, (uint32_t)(B * sizeof(T)), &mb[NS + 1]);
-        }
-        __syncwarp();
-        forward_substitution<T, NS>(nb, spre, scorr, gcoef, scoef, mb, phase, mu, err);
+    if (threadIdx.x == 0) {
+        *s_ready = 0;
+        phase_b_issue<T, NS>(nb, gcoef, gpre, scoef, spre, mb);
     }
+    __syncthreads();  // the flag is reset before the other warps raise it
+    if ((threadIdx.x >> 5) == 0)
+        forward_substitution<T, NS>(nb, spre, scorr, s_ready, gcoef, scoef, mb, phase, mu, err);
+    else
+        carried_corrections<T, NS>(nb, X, mu_prev, nbp, scorr, s_ready);
     __syncthreads();
 }
 
@@ -529,14 +584,6 @@ __device__ void store_batch(const BatchRegs &r, int nb, int32_t *sa, int32_t *sb
 
 // ---------------------------------------------------------------------------------
 // Lambda sweep kernel.  Cache: Ut = U^T (q x q), Ut[r][t] = U[t][r] = (D Sigma)[t][r].
-//
-// Batches are pipelined one deep: while CTA 0 runs the steps of batch k (phase B), the
-// other CTAs compute the dot products of batch k+1 against the cache as it stands before
-// batch k's update, together with the coefficients X(k+1, k) that give the change of those
-// dot products per unit step of each coordinate of batch k.  After the barrier, phase C
-// applies batch k's update to the cache and forms corr(k+1) = X(k+1, k) mu(k), which
-// phase B of batch k+1 takes as the initial correction sums.  The result is the same
-// sequential pass, with phase A of one batch overlapping phase B of the previous one.
 // ---------------------------------------------------------------------------------
 struct BatchMeta {
     int32_t *sa, *sb, *sseg, *snseg;
@@ -545,31 +592,6 @@ struct BatchMeta {
 __device__ __forceinline__ BatchMeta meta_at(unsigned char *base, int B, int which) {
     int32_t *p = reinterpret_cast<int32_t *>(base) + which * (3 * B + 2);
     return BatchMeta{p, p + B, p + 2 * B, p + 3 * B + 1};
-}
-
-// corr[l] = sum_{l'} X[l][l'] mu[l'] for l < nbn, one warp per coordinate over the grid;
-// the row of X of this warp's first coordinate (l = its global warp index) was loaded into
-// xw before the cache update, so that its latency overlapped that update.  The corrections
-// of padding coordinates are zeroed.
-template <typename T, int NS>
-__device__ void cross_corrections(int nbn, int nbk, const T *X, const T *smu, const T (&xw)[NS],
-                                  T *corr, unsigned bid, unsigned nblk) {
-    constexpr int B = NS * 32;
-    const int lane = threadIdx.x & 31;
-    const int gw = (int)(bid * kWarps + (threadIdx.x >> 5));
-    const int gwarps = (int)(nblk * kWarps);
-    for (int l = gw; l < nbn; l += gwarps) {
-        T acc = T(0);
-#pragma unroll
-        for (int kk = 0; kk < NS; kk++) {
-            const int l1 = lane + 32 * kk;
-            if (l1 < nbk) acc = fma(l == gw ? xw[kk] : __ldcg(X + (size_t)l * B + l1), smu[l1], acc);
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) corr[l] = acc;
-    }
-    if (bid == nblk - 1)
-        for (int l = nbn + threadIdx.x; l < B; l += blockDim.x) corr[l] = T(0);
 }
 
 // The pass on a group of nblk CTAs of a cooperative launch, this CTA being number bid of
@@ -598,11 +620,12 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T *preb = reinterpret_cast<T *>(scr.sub1);                // [2][PRE_N][B]
     T *coefb = reinterpret_cast<T *>(scr.sub2);               // [2][coef_slots(B)]
-    T *gX = coefb + 2 * (size_t)coef_slots(B);                // [B][B]
-    T *gcorr = gX + (size_t)B * B;                            // [B]
-    const int64_t rows_per = (q + nblk - 1) / nblk;
-    const int64_t r0 = (int64_t)bid * rows_per;
-    const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
+    T *gX = coefb + 2 * (size_t)coef_slots(B);                // [2][B][B] cross coefficients
+    // phase C: CTAs 1 .. nblk - 1 share the q rows of the cache; CTA 0 holds none
+    const int64_t nC = (int64_t)nblk - 1;
+    const int64_t rows_per = (q + nC - 1) / nC;
+    const int64_t r0 = bid >= 1 ? (int64_t)(bid - 1) * rows_per : 0;
+    const int64_t r1 = bid >= 1 ? ((r0 + rows_per) < q ? (r0 + rows_per) : q) : 0;
     // phase A reads rows through the ring when bulk copies can address them
     const bool use_ring = ((q * (int64_t)sizeof(T)) % 16) == 0 && aligned16(Sig) &&
                           aligned16(Psi) && aligned16(Ut);
@@ -636,7 +659,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     // dot products against the cache, step constants -> pre, in-batch coefficients -> coef,
     // and, when prev is given, the cross coefficients against the previous batch -> gX.
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
-                       int nbp, int rank0) {
+                       int nbp, T *Xo, int rank0) {
         const int nA = (int)nblk - rank0, rank = (int)bid - rank0;
         // the coefficient warps' thread index and count over the group's phase-A CTAs
         const int64_t t0 = (int64_t)rank * kCoefThreads + ((int)threadIdx.x - kDotThreads);
@@ -661,7 +684,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
 #pragma unroll 4
                 for (int64_t e = t0; e < ncross; e += nt) {
                     const int l = (int)(e / nbp), l1 = (int)(e % nbp);
-                    gX[(size_t)l * B + l1] =
+                    Xo[(size_t)l * B + l1] =
                         coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
                 }
             }
@@ -754,49 +777,75 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
         }
     };
 
-    // prologue: phase A of batch 0 by every CTA; no correction from an earlier batch
+    // Batches are pipelined two deep.  CTA 0 runs the steps (phase B) of batch k while CTAs
+    // 1 .. nblk - 1 apply batch k - 1's steps to the cache (phase C) and then compute the dot
+    // products and coefficients of batch k + 1 (phase A) against the cache as it stands
+    // after batch k - 1: their missing part, batch k's own steps, is carried into batch k + 1
+    // by the cross coefficients X(k + 1, k), which CTA 0's other warps apply during phase B of
+    // batch k + 1.  Counters order the two sides: CTA 0 publishes each batch's steps
+    // (mu_ready) and waits for the phase A of the batch it is about to run (a_done); the
+    // other CTAs wait for a batch's steps and for the end of every CTA's phase A of the next
+    // batch (which reads the cache rows phase C writes) before phase C, and for the end of
+    // every CTA's phase C (c_done) before the next phase A.
+    auto nb_of = [&](int64_t k) -> int {
+        const int64_t s0 = k * B;
+        return s0 < m ? (int)((m - s0) < B ? (m - s0) : B) : 0;
+    };
     if (threadIdx.x == 0) {
         for (int k = 0; k < kMaxStages; k++) mbar_init(&s_ring[k], 1);
         mbar_init_fence();
     }
-    BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
-    int nbk = (int)(m < B ? m : B);
-    BatchRegs breg;  // indices of the next batch, fetched ahead
-    fetch_batch(ai, aj, 0, nbk, breg);
-    store_batch(breg, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
-    bool pref = false;  // breg holds the batch after the current one
-    phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
-    if (bid == 0) {
-        for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
-            mbar_init_fence();
-        }
+    auto slot = [&](int64_t k) -> BatchMeta { return meta_at(smem + L.meta, B, (int)(k % 3)); };
+    const int nb0 = nb_of(0);
+    BatchRegs breg;  // indices of a batch, fetched ahead of storing them
+    fetch_batch(ai, aj, 0, nb0, breg);
+    const BatchMeta s0m = slot(0);
+    store_batch(breg, nb0, s0m.sa, s0m.sb, s0m.sseg, s0m.snseg);
+    // prologue: phase A of batch 0 by every CTA; nothing carried into it
+    phase_a(s0m, nb0, preb, coefb, nullptr, 0, gX, 0);
+    if (bid == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
+        mbar_init_fence();
     }
     if (!grid_sync(scr.bar, scr.err, nblk, bar_round)) return;
+    const unsigned long long nA = nblk - 1;
 
+    if (bid == 0) {  // ---- phase B of every batch ----
+        __shared__ int s_ready;  // panels whose carried corrections are formed
+        for (int64_t k = 0; k < nbatch; k++) {
+            if (k > 0 && !cta_wait_counts(&scr.bar->a_done, (unsigned long long)k * nA, nullptr,
+                                          0, scr.err))
+                return;
+            const size_t par = (size_t)(k & 1);
+            phase_b<T, NS>(nb_of(k), coefb + par * coef_slots(B), preb + par * PRE_N * B,
+                           k > 0 ? gX + par * B * B : nullptr, scr.mu + (1 - par) * B,
+                           k > 0 ? nb_of(k - 1) : 0, reinterpret_cast<T *>(work),
+                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase,
+                           scr.mu + par * B, scr.err, &s_ready);
+            if (threadIdx.x == 0) {  // batch k's steps are published
+                __threadfence();
+                red_release_add(&scr.bar->mu_ready, 1ull);
+            }
+        }
+        return;
+    }
+
+    // ---- CTAs 1 .. nblk - 1: phase C of batch k, then phase A of batch k + 2 ----
+    if (nbatch > 1) {
+        const int nb1 = nb_of(1);
+        fetch_batch(ai, aj, B, nb1, breg);
+        const BatchMeta s1m = slot(1);
+        store_batch(breg, nb1, s1m.sa, s1m.sb, s1m.sseg, s1m.snseg);
+        phase_a(s1m, nb1, preb + PRE_N * B, coefb + coef_slots(B), &s0m, nb0,
+                gX + (size_t)B * B, 1);
+        __syncthreads();
+        cta_count(&scr.bar->a_done);
+    }
     for (int64_t k = 0; k < nbatch; k++) {
-        const int64_t sk = k * B, sn = sk + B;
-        const int nbn = (int)(sn < m ? ((m - sn) < B ? (m - sn) : B) : 0);
-        T *pre_k = preb + (size_t)(k & 1) * PRE_N * B, *coef_k = coefb + (size_t)(k & 1) * coef_slots(B);
-        T *pre_n = preb + (size_t)((k + 1) & 1) * PRE_N * B;
-        T *coef_n = coefb + (size_t)((k + 1) & 1) * coef_slots(B);
-        if (nbn > 0) {
-            if (!pref) fetch_batch(ai, aj, sn, nbn, breg);
-            store_batch(breg, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
-        }
-
-        // ---- phase B of batch k on CTA 0, phase A of batch k+1 on the others ----
-        if (bid == 0) {
-            phase_b<T, NS>(nbk, k > 0, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
-                           scr.err);
-        } else if (nbn > 0) {
-            phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
-        }
+        const int nbk = nb_of(k), nbn = nb_of(k + 1), nb2 = nb_of(k + 2);
+        const BatchMeta cur = slot(k);
         // Phase C's first reads (segment 0, this warp's first R rows) do not depend on the
-        // steps: they are issued between this CTA's arrival at the barrier and its wait, so
-        // that their latency overlaps the wait.
+        // steps: they are issued before the wait for them, so that their latency overlaps it.
         constexpr int R = NS <= 8 ? kRowsInFlight : 2;  // registers: R x NS values per lane
         T sta[R], sv[R][NS], uv[R][NS], ua[R];
         int bv[NS];
@@ -833,26 +882,23 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 }
             }
         };
-        {
-            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
-            seg_columns(0);
-            load_rows(cur.sa[cur.sseg[0]], r0 + warp);
-            if (!grid_wait(scr.bar, scr.err, tk)) return;
-        }
+        seg_columns(0);
+        load_rows(cur.sa[cur.sseg[0]], r0 + warp);
+        // batch k's steps, and every CTA's phase A of batch k + 1 (it reads the cache rows
+        // this phase C writes)
+        if (!cta_wait_counts(&scr.bar->mu_ready, (unsigned long long)k + 1,
+                             nbn > 0 ? &scr.bar->a_done : nullptr,
+                             (unsigned long long)(k + 1) * nA, scr.err))
+            return;
 
-        // CTA 0: batch k+1's step constants and coefficients are complete (phase A ended
-        // before the barrier); their copies into shared memory run while phase C does
-        if (bid == 0 && threadIdx.x == 0 && nbn > 0)
-            phase_b_issue<T, NS>(nbn, coef_n, pre_n, reinterpret_cast<T *>(work),
-                                 reinterpret_cast<T *>(work) + coef_area(B), s_mb);
-
-        // ---- phase C: batch k's update on this CTA's rows; corrections for batch k+1 ----
+        // ---- phase C: batch k's update on this CTA's rows ----
         // coordinate (a, b) of a segment with row a: U_a += mu Sigma_b, U_b += mu Sigma_a
         // (b != a); transposed: Ut[t][a] += sum mu Sigma[t][b], Ut[t][b] += mu Sigma[t][a]
         {
             T *smu = reinterpret_cast<T *>(work + L.phc);
+            const double *muk = scr.mu + (size_t)(k & 1) * B;
             for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
-                const double mu = __ldcg(scr.mu + l);
+                const double mu = __ldcg(muk + l);
                 smu[l] = (T)mu;
                 if (bid == nblk - 1) {  // the direction itself
                     const int64_t i = cur.sa[l], j = cur.sb[l];
@@ -861,15 +907,6 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 }
             }
             __syncthreads();
-            T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
-            {
-                const int gw = (int)(bid * kWarps + warp);
-#pragma unroll
-                for (int kk = 0; kk < NS; kk++) {
-                    const int l1 = lane + 32 * kk;
-                    xw[kk] = (gw < nbn && l1 < nbk) ? __ldcg(gX + (size_t)gw * B + l1) : T(0);
-                }
-            }
             const int nseg = *cur.snseg;
             for (int g = 0; g < nseg; g++) {
                 const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
@@ -882,7 +919,7 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                     mv[kk] = (l < l1) ? smu[l] : T(0);
                 }
                 for (int64_t tb = r0 + warp; tb < r1; tb += kWarps * R) {
-                    if (g > 0 || tb != r0 + warp) load_rows(a, tb);  // else: loaded before the barrier
+                    if (g > 0 || tb != r0 + warp) load_rows(a, tb);  // else: loaded before the wait
 #pragma unroll
                     for (int r = 0; r < R; r++) {
                         const int64_t t = tb + (int64_t)kWarps * r;
@@ -902,25 +939,26 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
                 }
                 __syncwarp();  // this segment's writes before the next segment's reads
             }
-            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr, bid, nblk);
         }
-        {
-            // the indices of batch k + 2 are fetched while this barrier completes
-            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
-            const int64_t s2 = (k + 2) * B;
-            const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
-            pref = nb2 > 0;
-            if (pref) fetch_batch(ai, aj, s2, nb2, breg);
-            if (!grid_wait(scr.bar, scr.err, tk)) {
-                if (bid == 0 && threadIdx.x == 0 && nbn > 0)  // batch k+1's copies in flight
-                    phase_b_drain<T, NS>(nbn, s_mb, mb_phase, scr.err);
-                return;
-            }
+        __syncthreads();
+        cta_count(&scr.bar->c_done);
+        // the indices of batch k + 2 are fetched while the other CTAs finish their phase C
+        if (nb2 > 0) {
+            const BatchMeta s2 = slot(k + 2);
+            fetch_batch(ai, aj, (k + 2) * B, nb2, breg);
+            store_batch(breg, nb2, s2.sa, s2.sb, s2.sseg, s2.snseg);
         }
-        BatchMeta tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-        nbk = nbn;
+        if (!cta_wait_counts(&scr.bar->c_done, (unsigned long long)(k + 1) * nA, nullptr, 0,
+                             scr.err))
+            return;
+        if (nb2 > 0) {  // ---- phase A of batch k + 2 ----
+            const size_t par = (size_t)((k + 2) & 1);
+            const BatchMeta prv = slot(k + 1);
+            phase_a(slot(k + 2), nb2, preb + par * PRE_N * B, coefb + par * coef_slots(B), &prv,
+                    nbn, gX + par * B * B, 1);
+            __syncthreads();
+            cta_count(&scr.bar->a_done);
+        }
     }
 }
 
@@ -950,11 +988,12 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T *preb = reinterpret_cast<T *>(scr.sub1);
     T *coefb = reinterpret_cast<T *>(scr.sub2);
-    T *gX = coefb + 2 * (size_t)coef_slots(B);
-    T *gcorr = gX + (size_t)B * B;
-    const int64_t rows_per = (q + nblk - 1) / nblk;
-    const int64_t r0 = (int64_t)bid * rows_per;
-    const int64_t r1 = (r0 + rows_per) < q ? (r0 + rows_per) : q;
+    T *gX = coefb + 2 * (size_t)coef_slots(B);  // [2][B][B] cross coefficients
+    // phase C: CTAs 1 .. nblk - 1 share the q rows of the cache; CTA 0 holds none
+    const int64_t nC = (int64_t)nblk - 1;
+    const int64_t rows_per = (q + nC - 1) / nC;
+    const int64_t r0 = bid >= 1 ? (int64_t)(bid - 1) * rows_per : 0;
+    const int64_t r1 = bid >= 1 ? ((r0 + rows_per) < q ? (r0 + rows_per) : q) : 0;
     constexpr int VN = V16<T>::n;
     const int64_t nbatch = (m + B - 1) / B;
     if (nbatch == 0) return;
@@ -968,7 +1007,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     };
 
     auto phase_a = [&](const BatchMeta &bm, int nb, T *pre, T *coef, const BatchMeta *prev,
-                       int nbp, int rank0) {
+                       int nbp, T *Xo, int rank0) {
         const int nA = (int)nblk - rank0, rank = (int)bid - rank0;
         // rows of Delta V that can be nonzero: with the list in ascending rows, those at or
         // before this batch's first row (the ring copies whole 16-byte words: entries beyond
@@ -998,7 +1037,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
 #pragma unroll 4
                 for (int64_t e = t0; e < ncross; e += nt) {
                     const int l = (int)(e / nbp), l1 = (int)(e % nbp);
-                    gX[(size_t)l * B + l1] =
+                    Xo[(size_t)l * B + l1] =
                         coefficient(bm.sa[l], bm.sb[l], prev->sa[l1], prev->sb[l1]);
                 }
             }
@@ -1064,47 +1103,65 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
         }
     };
 
+    // pipelined as the Lambda pass (see there)
+    auto nb_of = [&](int64_t k) -> int {
+        const int64_t s0 = k * B;
+        return s0 < m ? (int)((m - s0) < B ? (m - s0) : B) : 0;
+    };
     if (threadIdx.x == 0) {
         for (int k = 0; k < kMaxStages; k++) mbar_init(&s_ring[k], 1);
         mbar_init_fence();
     }
-    BatchMeta cur = meta_at(smem + L.meta, B, 0), nxt = meta_at(smem + L.meta, B, 1);
-    int nbk = (int)(m < B ? m : B);
-    BatchRegs breg;  // indices of the next batch, fetched ahead
-    fetch_batch(ti, tj, 0, nbk, breg);
-    store_batch(breg, nbk, cur.sa, cur.sb, cur.sseg, cur.snseg);
-    bool pref = false;  // breg holds the batch after the current one
-    phase_a(cur, nbk, preb, coefb, nullptr, 0, 0);
-    if (bid == 0) {
-        for (int l = threadIdx.x; l < B; l += blockDim.x) gcorr[l] = T(0);
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
-            mbar_init_fence();
-        }
+    auto slot = [&](int64_t k) -> BatchMeta { return meta_at(smem + L.meta, B, (int)(k % 3)); };
+    const int nb0 = nb_of(0);
+    BatchRegs breg;  // indices of a batch, fetched ahead of storing them
+    fetch_batch(ti, tj, 0, nb0, breg);
+    const BatchMeta s0m = slot(0);
+    store_batch(breg, nb0, s0m.sa, s0m.sb, s0m.sseg, s0m.snseg);
+    phase_a(s0m, nb0, preb, coefb, nullptr, 0, gX, 0);
+    if (bid == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
+        mbar_init_fence();
     }
     if (!grid_sync(scr.bar, scr.err, nblk, bar_round)) return;
+    const unsigned long long nA = nblk - 1;
 
+    if (bid == 0) {  // ---- phase B of every batch ----
+        __shared__ int s_ready;  // panels whose carried corrections are formed
+        for (int64_t k = 0; k < nbatch; k++) {
+            if (k > 0 && !cta_wait_counts(&scr.bar->a_done, (unsigned long long)k * nA, nullptr,
+                                          0, scr.err))
+                return;
+            const size_t par = (size_t)(k & 1);
+            phase_b<T, NS>(nb_of(k), coefb + par * coef_slots(B), preb + par * PRE_N * B,
+                           k > 0 ? gX + par * B * B : nullptr, scr.mu + (1 - par) * B,
+                           k > 0 ? nb_of(k - 1) : 0, reinterpret_cast<T *>(work),
+                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase,
+                           scr.mu + par * B, scr.err, &s_ready);
+            if (threadIdx.x == 0) {  // batch k's steps are published
+                __threadfence();
+                red_release_add(&scr.bar->mu_ready, 1ull);
+            }
+        }
+        return;
+    }
+
+    // ---- CTAs 1 .. nblk - 1: phase C of batch k, then phase A of batch k + 2 ----
+    if (nbatch > 1) {
+        const int nb1 = nb_of(1);
+        fetch_batch(ti, tj, B, nb1, breg);
+        const BatchMeta s1m = slot(1);
+        store_batch(breg, nb1, s1m.sa, s1m.sb, s1m.sseg, s1m.snseg);
+        phase_a(s1m, nb1, preb + PRE_N * B, coefb + coef_slots(B), &s0m, nb0,
+                gX + (size_t)B * B, 1);
+        __syncthreads();
+        cta_count(&scr.bar->a_done);
+    }
     for (int64_t k = 0; k < nbatch; k++) {
-        const int64_t sk = k * B, sn = sk + B;
-        const int nbn = (int)(sn < m ? ((m - sn) < B ? (m - sn) : B) : 0);
-        T *pre_k = preb + (size_t)(k & 1) * PRE_N * B, *coef_k = coefb + (size_t)(k & 1) * coef_slots(B);
-        T *pre_n = preb + (size_t)((k + 1) & 1) * PRE_N * B;
-        T *coef_n = coefb + (size_t)((k + 1) & 1) * coef_slots(B);
-        if (nbn > 0) {
-            if (!pref) fetch_batch(ti, tj, sn, nbn, breg);
-            store_batch(breg, nbn, nxt.sa, nxt.sb, nxt.sseg, nxt.snseg);
-        }
-
-        if (bid == 0) {
-            phase_b<T, NS>(nbk, k > 0, coef_k, pre_k, gcorr, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase, scr.mu,
-                           scr.err);
-        } else if (nbn > 0) {
-            phase_a(nxt, nbn, pre_n, coef_n, &cur, nbk, 1);
-        }
+        const int nbk = nb_of(k), nbn = nb_of(k + 1), nb2 = nb_of(k + 2);
+        const BatchMeta cur = slot(k);
         // Phase C's first reads (segment 0, this warp's first R rows of Sigma) do not depend
-        // on the steps: they are issued between this CTA's arrival at the barrier and its
-        // wait.
+        // on the steps: they are issued before the wait for them.
         constexpr int R = NS <= 8 ? kRowsInFlight : 2;  // registers: R x NS values per lane
         T sv[R][NS], va[R];
         int jv[NS];
@@ -1128,23 +1185,19 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                 va[r] = (t < r1 && lane == 0) ? __ldcg(dVt + t * p + i) : T(0);
             }
         };
-        {
-            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
-            seg_columns(0);
-            load_rows(cur.sa[cur.sseg[0]], r0 + warp);
-            if (!grid_wait(scr.bar, scr.err, tk)) return;
-        }
-
-        // CTA 0: batch k+1's phase-B data are complete; their copies run while phase C does
-        if (bid == 0 && threadIdx.x == 0 && nbn > 0)
-            phase_b_issue<T, NS>(nbn, coef_n, pre_n, reinterpret_cast<T *>(work),
-                                 reinterpret_cast<T *>(work) + coef_area(B), s_mb);
+        seg_columns(0);
+        load_rows(cur.sa[cur.sseg[0]], r0 + warp);
+        if (!cta_wait_counts(&scr.bar->mu_ready, (unsigned long long)k + 1,
+                             nbn > 0 ? &scr.bar->a_done : nullptr,
+                             (unsigned long long)(k + 1) * nA, scr.err))
+            return;
 
         // ---- phase C: dVt[t][i] += sum over the segment of row i of mu Sigma[t][j] ----
         {
             T *smu = reinterpret_cast<T *>(work + L.phc);
+            const double *muk = scr.mu + (size_t)(k & 1) * B;
             for (int l = threadIdx.x; l < nbk; l += blockDim.x) {
-                const double mu = __ldcg(scr.mu + l);
+                const double mu = __ldcg(muk + l);
                 smu[l] = (T)mu;
                 if (bid == nblk - 1) {  // Theta itself
                     const int64_t i = cur.sa[l], j = cur.sb[l];
@@ -1152,15 +1205,6 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                 }
             }
             __syncthreads();
-            T xw[NS];  // this warp's row of the cross coefficients (see cross_corrections)
-            {
-                const int gw = (int)(bid * kWarps + warp);
-#pragma unroll
-                for (int kk = 0; kk < NS; kk++) {
-                    const int l1 = lane + 32 * kk;
-                    xw[kk] = (gw < nbn && l1 < nbk) ? __ldcg(gX + (size_t)gw * B + l1) : T(0);
-                }
-            }
             const int nseg = *cur.snseg;
             for (int g = 0; g < nseg; g++) {
                 const int l0 = cur.sseg[g], l1 = cur.sseg[g + 1];
@@ -1173,7 +1217,7 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                     mv[kk] = (l < l1) ? smu[l] : T(0);
                 }
                 for (int64_t tb = r0 + warp; tb < r1; tb += kWarps * R) {
-                    if (g > 0 || tb != r0 + warp) load_rows(i, tb);  // else: before the barrier
+                    if (g > 0 || tb != r0 + warp) load_rows(i, tb);  // else: before the wait
 #pragma unroll
                     for (int r = 0; r < R; r++) {
                         const int64_t t = tb + (int64_t)kWarps * r;
@@ -1186,25 +1230,25 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
                     }
                 }
             }
-            if (nbn > 0) cross_corrections<T, NS>(nbn, nbk, gX, smu, xw, gcorr, bid, nblk);
         }
-        {
-            // the indices of batch k + 2 are fetched while this barrier completes
-            const GridTicket tk = grid_arrive(scr.bar, nblk, bar_round);
-            const int64_t s2 = (k + 2) * B;
-            const int nb2 = (int)(s2 < m ? ((m - s2) < B ? (m - s2) : B) : 0);
-            pref = nb2 > 0;
-            if (pref) fetch_batch(ti, tj, s2, nb2, breg);
-            if (!grid_wait(scr.bar, scr.err, tk)) {
-                if (bid == 0 && threadIdx.x == 0 && nbn > 0)  // batch k+1's copies in flight
-                    phase_b_drain<T, NS>(nbn, s_mb, mb_phase, scr.err);
-                return;
-            }
+        __syncthreads();
+        cta_count(&scr.bar->c_done);
+        if (nb2 > 0) {  // fetched while the other CTAs finish their phase C
+            const BatchMeta s2 = slot(k + 2);
+            fetch_batch(ti, tj, (k + 2) * B, nb2, breg);
+            store_batch(breg, nb2, s2.sa, s2.sb, s2.sseg, s2.snseg);
         }
-        BatchMeta tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-        nbk = nbn;
+        if (!cta_wait_counts(&scr.bar->c_done, (unsigned long long)(k + 1) * nA, nullptr, 0,
+                             scr.err))
+            return;
+        if (nb2 > 0) {  // ---- phase A of batch k + 2 ----
+            const size_t par = (size_t)((k + 2) & 1);
+            const BatchMeta prv = slot(k + 1);
+            phase_a(slot(k + 2), nb2, preb + par * PRE_N * B, coefb + par * coef_slots(B), &prv,
+                    nbn, gX + par * B * B, 1);
+            __syncthreads();
+            cta_count(&scr.bar->a_done);
+        }
     }
 }
 
@@ -1469,7 +1513,7 @@ PassDesc<double> &desc_of<double>(PassBatcher::Entry &e) { return e.dd; }
 cggm_status scratch_reserve(SweepScratch &scr) {
     if (scr.mu) return CGGM_OK;
     const int Bmax = 512;  // float; double batches are at most 128 and take less
-    CGGM_CUDA_TRY(cudaMalloc(&scr.mu, sizeof(double) * Bmax));
+    CGGM_CUDA_TRY(cudaMalloc(&scr.mu, sizeof(double) * 2 * Bmax));
     CGGM_CUDA_TRY(cudaMalloc(&scr.sub1, scratch_sub1_bytes(Bmax, sizeof(float))));
     CGGM_CUDA_TRY(cudaMalloc(&scr.sub2, scratch_sub2_bytes(Bmax, sizeof(float))));
     CGGM_CUDA_TRY(cudaMalloc(&scr.bar, sizeof(GridBarrier)));

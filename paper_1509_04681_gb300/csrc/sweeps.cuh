@@ -9,10 +9,10 @@ struct PassBatcher;
 
 // Device scratch shared by the sweep kernels (sized for the largest B).
 struct SweepScratch {
-    double *mu = nullptr;  // [B] the batch's steps
+    double *mu = nullptr;  // [2][B] the steps of two consecutive batches
     void *sub1 = nullptr;  // [2][PRE_N][B] step constants of two batches (T)
     void *sub2 = nullptr;  // [2][coef_slots(B)] in-batch coefficients of two batches,
-                           // [B][B] cross coefficients, [B] corrections (T)
+                           // [2][B][B] their cross coefficients against the batch before (T)
     GridBarrier *bar = nullptr;
     int *err = nullptr;
     // host: when set, the passes of this context are handed to the batcher, which runs the
@@ -69,7 +69,7 @@ inline int64_t sxx_chunk_rows(int64_t p, int64_t esz) {
     return r >= p ? p : (r < 1 ? 1 : r);
 }
 
-// lambda_sweep in double on scratch buffers laid out by the caller (mu: B doubles, sub1:
+// lambda_sweep in double on scratch buffers laid out by the caller (mu: 2 B doubles, sub1:
 // scratch_sub1_bytes(B, 8), sub2: scratch_sub2_bytes(B, 8), bar, err); allocates nothing.
 // B in {32, 64, 128}.
 cggm_status lambda_sweep_preplanned_f64(int64_t q, const double *Sigma, const double *Psi,
@@ -89,7 +89,7 @@ constexpr size_t scratch_sub1_bytes(int B, size_t esz) {
     return esz * 2 * kStepConstants * (size_t)B;
 }
 constexpr size_t scratch_sub2_bytes(int B, size_t esz) {
-    return esz * (2 * (size_t)coef_slots(B) + (size_t)B * B + (size_t)B);
+    return esz * (2 * (size_t)coef_slots(B) + 2 * (size_t)B * B);
 }
 
 // Allocates the scratch once, for B 256 in float (which also covers B <= 128 in double).

@@ -8,8 +8,8 @@ the oracle's definition (LAPACK's dense factor of the permuted matrix), log det 
 oracle's, and the solves with the oracle's spd_solve.  Cases: chains with random links and
 random networks under every pivot order, a forest, a diagonal matrix, a dense matrix (one
 supernode), a star whose centre updates a 1100-column supernode (more rows than one map
-chunk), q = 1, matrices that are not positive definite or not finite, and the
-second-difference matrix at q = 200000 against its closed-form determinant.
+chunk), q = 1, matrices that are not positive definite or not finite, and tridiagonal
+Toeplitz matrices at q = 200000 against their closed-form determinants.
 """
 import numpy as np
 import pytest
@@ -159,28 +159,51 @@ def test_not_positive_definite_and_not_finite(ctx):
     assert ex.value.status == cg.CGGM_EINVAL
 
 
-def test_second_difference_closed_form_at_scale(ctx):
-    """log det T_q = log(q + 1) for the second-difference matrix, relabelled at random so
-    that the pivot order matters; q = 200000 (the block regime's largest output count)."""
-    q = 200000
-    rng = np.random.default_rng(9)
-    lab = rng.permutation(q)
+def relabelled_tridiagonal(q, diag, lab):
+    """Lower triangle (CSR) of the tridiagonal Toeplitz matrix with `diag` on the diagonal and
+    -1 beside it, its path relabelled by the permutation lab."""
     i = np.arange(q - 1)
     r = np.concatenate([lab, lab[i + 1]])
     c = np.concatenate([lab, lab[i]])
-    v = np.concatenate([np.full(q, 2.0), np.full(q - 1, -1.0)])
-    lo = np.maximum(r, c), np.minimum(r, c)
-    m = sp.csr_matrix((v, lo), shape=(q, q))
+    v = np.concatenate([np.full(q, float(diag)), np.full(q - 1, -1.0)])
+    m = sp.csr_matrix((v, (np.maximum(r, c), np.minimum(r, c))), shape=(q, q))
     m.sort_indices()
-    for ordering in (cg.CGGM_ORDER_AMD, cg.CGGM_ORDER_RCM):
-        with ctx.cggm_spchol(m.indptr, m.indices, ordering) as f:
-            ld = f.factor(m.data)
-            assert abs(ld - np.log(q + 1)) <= 1e-9
-            assert f.export(blocks=False)["nnz_L"] == 2 * q - 1  # a path: no fill
-            # one column of the inverse: (T^-1)_{ij} = min(i,j) (q + 1 - max(i,j)) / (q + 1)
-            j = 777
-            x = f.solve(c0=int(lab[j]), k=1)[:, 0]
-            k = np.arange(q)
-            want = np.minimum(k, j) + 1.0
-            want = want * (q - np.maximum(k, j)) / (q + 1)
-            np.testing.assert_allclose(x[lab], want, rtol=1e-9, atol=1e-9)
+    return m
+
+
+def test_tridiagonal_closed_forms_at_scale(ctx):
+    """q = 200000 (the block regime's largest output count), labels permuted at random so
+    that the pivot order matters.  The eigenvalues of the tridiagonal Toeplitz matrix
+    T_a = tridiag(-1, a, -1) are a - 2 cos(k pi / (q + 1)), k = 1 .. q, so log det T_a is
+    their log sum; for a = 2 (the second-difference matrix) that is log(q + 1), and
+    (T_2^-1)_ij = min(i, j) (q + 1 - max(i, j)) / (q + 1) (1-based).
+    Tolerances: T_3 has condition number below 5, so log det and the solve are within a few
+    hundred roundings.  T_2 has condition number ~0.4 q^2 = 1.6e10: the factorisation's
+    backward error E (entries ~3 eps |L| |L^T|) moves log det by tr(T_2^-1 E), a sum of q
+    terms of random sign with (T_2^-1)_ii up to q / 4, ~1e-8 here; the solve is accurate to
+    the condition number times eps relative to its largest entry (~2e-6)."""
+    q = 200000
+    rng = np.random.default_rng(9)
+    lab = rng.permutation(q)
+    k = np.arange(1, q + 1)
+    for diag in (3.0, 2.0):
+        m = relabelled_tridiagonal(q, diag, lab)
+        # (for a = 2 the closed form: the product formula loses digits to 2 - 2 cos(small))
+        want_ld = (np.log(q + 1) if diag == 2.0
+                   else float(np.sum(np.log(diag - 2.0 * np.cos(k * np.pi / (q + 1))))))
+        for ordering in (cg.CGGM_ORDER_AMD, cg.CGGM_ORDER_RCM):
+            with ctx.cggm_spchol(m.indptr, m.indices, ordering) as f:
+                ld = f.factor(m.data)
+                assert abs(ld - want_ld) <= (1e-9 if diag == 3.0 else 1e-7)
+                assert f.export(blocks=False)["nnz_L"] == 2 * q - 1  # a path: no fill
+                j = 777
+                x = f.solve(c0=int(lab[j]), k=1)[:, 0]
+                # residual in original labels: T x = e_j
+                full = m + sp.tril(m, -1).T
+                res = full @ x
+                res[lab[j]] -= 1.0
+                assert np.max(np.abs(res)) <= 1e-10 * np.max(np.abs(x)) * (diag + 2)
+                if diag == 2.0:
+                    t = np.arange(q)
+                    want = (np.minimum(t, j) + 1.0) * (q - np.maximum(t, j)) / (q + 1)
+                    np.testing.assert_allclose(x[lab], want, rtol=0, atol=1e-5 * want.max())
