@@ -55,7 +55,7 @@ constexpr int kDotWarps = 4;
 constexpr int kDotThreads = kDotWarps * 32;
 constexpr int kCoefThreads = kThreads - kDotThreads;
 constexpr int kBarDots = 1;
-// Phase B on CTA 0: warps 1 .. kWarps - 1 (the carried corrections) on named barrier kBarCorr.
+// Phase B on CTA 0: warps 1 .. kWarps - 2 (the carried corrections) on named barrier kBarCorr.
 constexpr int kBarCorr = 2;
 
 __device__ __forceinline__ void bar_sync_n(int id, int n) {
@@ -171,11 +171,19 @@ struct SmemLayout {
     size_t meta;  // three batches (k, k + 1, k + 2): sa[B], sb[B], sseg[B + 1], nseg (ints)
     size_t work;  // union: phase A ring of row chunks (kRingBytes, all stages);
                   //        phase B (CTA 0) coefficient panels [coef_area(B)], step constants
-                  //          [PRE_N][B], carried corrections [B] (T);
+                  //          [2][PRE_N][B], carried corrections [B] (T), steps [2][B]
+                  //          (double);
                   //        phase C (the other CTAs) mu[B] (T) at work + phc
     size_t phc;   // offset of phase C's area within the work area
     size_t total;
 };
+
+// Phase B's shared memory on CTA 0: coefficient panels, two batches' step constants and the
+// carried corrections (T, with copy slack), then two batches' steps (double) at this offset.
+template <typename T>
+__host__ __device__ constexpr size_t phase_b_steps_offset(int B) {
+    return (((size_t)coef_area(B) + 2 * PRE_N * B + B + 8) * sizeof(T) + 15) & ~size_t(15);
+}
 
 template <typename T>
 __host__ __device__ inline SmemLayout smem_layout(int B) {
@@ -184,7 +192,7 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
     size_t off = (size_t)3 * (3 * B + 2) * sizeof(int32_t);  // three batches' metadata
     off = (off + 15) & ~size_t(15);
     s.work = off;
-    const size_t phb = (((size_t)coef_area(B) + PRE_N * B + B + 8) * sizeof(T) + 15) & ~size_t(15);
+    const size_t phb = phase_b_steps_offset<T>(B) + 2 * (size_t)B * sizeof(double);
     const size_t phc = (size_t)(B + 4) * sizeof(T);
     s.phc = phb;
     size_t w = phb + phc;
@@ -193,13 +201,6 @@ __host__ __device__ inline SmemLayout smem_layout(int B) {
     return s;
 }
 
-// Forward substitution of one batch on warp 0: for l = 0..nb-1,
-//   b_l = base_l + sum_{l' < l} coef(l, l') mu_l',  mu_l = -c_l + S_{lam_l/a_l}(c_l - b_l/a_l)
-// (exact minimiser of (a/2) mu^2 + b mu + lam |c + mu|, Appendix A.1), written with the
-// step constants above.  coef is the strictly lower triangle, row-major packed, in shared
-// memory (column-packed, see colbase).  Lane k owns coordinates 32 s + k; at step l every lane forms the candidate
-// step of its own coordinate of the current panel and the owner's candidate is broadcast,
-// so the dependent chain per coordinate is a few T operations and one warp shuffle.
 // Issues the bulk copy of panel s's coefficient columns into its buffer (one thread).
 template <typename T, int NS>
 __device__ __forceinline__ void issue_panel(int s, const T *gcoef, T *scoef, uint64_t *mb) {
@@ -211,197 +212,281 @@ __device__ __forceinline__ void issue_panel(int s, const T *gcoef, T *scoef, uin
     bulk_load(scoef + panel_off(s, B), gcoef + c0, bytes, bar);
 }
 
-// Thread of warp 0: waits (bounded) until the shared-memory flag reaches `target`; the flag
-// is raised by other warps of the same CTA, which wait for nothing outside it.
-__device__ __forceinline__ bool wait_block_flag(volatile int *flag, int target, int *err) {
-    if (*flag >= target) return true;
-    const uint64_t t0 = global_ns();
-    while (*flag < target) {
-        if (global_ns() - t0 > 2000000000ull) {
-            set_err(err, DEV_TIMEOUT);
-            return false;
-        }
-    }
-    return true;
+// Shared-memory flags between the warps of CTA 0 (release / acquire at CTA scope).
+__device__ __forceinline__ int ld_acquire_cta(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared.s32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(int *p, int v) {
+    asm volatile("st.release.cta.shared.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
 }
 
+// Waits (bounded) until the flag reaches target; returns the value seen, or -1 at the
+// deadline (DEV_TIMEOUT recorded) or when another thread has recorded an error.  The flags
+// are raised by other warps of the same CTA.
+__device__ int wait_flag(const int *flag, int target, int *err, unsigned sleep_ns) {
+    int v = ld_acquire_cta(flag);
+    if (v >= target) return v;
+    const uint64_t t0 = global_ns();
+    for (unsigned it = 1;; it++) {
+        if (sleep_ns) __nanosleep(sleep_ns);
+        v = ld_acquire_cta(flag);
+        if (v >= target) return v;
+        if ((it & 63u) == 0) {
+            if (*(volatile int *)err != 0) return -1;
+            if (global_ns() - t0 > 2000000000ull) {
+                set_err(err, DEV_TIMEOUT);
+                return -1;
+            }
+        }
+    }
+}
+
+// One thread: waits (bounded) until the device-wide counter reaches target (acquire).
+__device__ bool wait_counter(const unsigned long long *c, unsigned long long target, int *err) {
+    if (ld_acquire_u64(c) >= target) return true;
+    const uint64_t t0 = global_ns();
+    for (unsigned it = 1;; it++) {
+        if (ld_acquire_u64(c) >= target) return true;
+        if ((it & 63u) == 0) {
+            if (ld_acquire_int(err) != 0) return false;
+            if (global_ns() - t0 > 2000000000ull) {
+                set_err(err, DEV_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// CTA 0's part of a pass: phase B of every batch, by three groups of warps that meet only
+// through shared-memory flags and mbarriers, so that the serial chain never waits for a
+// copy, a correction or a device-wide counter that could have been ready earlier.
+//   warp 0 (the chain): for each batch in turn, the forward substitution
+//     b_l = base_l + sum_{l' < l} coef(l, l') mu_l',  mu_l = -c_l + S_{lam_l/a_l}(c_l - b_l/a_l)
+//     (the exact minimiser of (a/2) mu^2 + b mu + lam |c + mu|, Appendix A.1, written with
+//     the step constants), panel by panel: lane k owns coordinates 32 s + k; at step l every
+//     lane forms the candidate step of its own coordinate and the owner's candidate is
+//     broadcast, so the dependent chain per coordinate is a few T operations and one warp
+//     shuffle.  coef is the strictly lower triangle, column-packed (colbase), in shared
+//     memory.  After each panel it stores the panel's steps (device memory for the other
+//     CTAs, shared memory for warps 1..6) and raises `prog` (panels done, counted over the
+//     pass: batch k's panel s is number k NS + s).
+//   warp 7, lane 0 (the feeder): for each batch k, once the other CTAs' phase A of batch k
+//     is complete (a_done), the bulk copies of its step constants into one of two buffers and
+//     of each coefficient panel into its buffer as soon as the chain has finished the
+//     panel that last occupied it; and, when the chain has finished batch k - 1, publishes
+//     that batch's steps to the other CTAs (mu_ready).
+//   warps 1..6 (the corrections): for each batch k > 0, the part that batch k - 1 carries
+//     into it, corr[l] = sum_{l'} X(k, k-1)[l][l'] mu_{l'} (phase A of batch k ran against the
+//     cache without batch k - 1's steps), panel by panel, raising `corr_prog` (same
+//     numbering as prog); the rows of panel 0 are loaded ahead, while batch k - 1 still runs.
+// Shared memory (the work area): coefficient panels [coef_area(B)], step constants [2][PRE_N][B]
+// and corrections [B] (T), then the steps of two batches [2][B] (double).
 template <typename T, int NS>
-__device__ void forward_substitution(int nb, const T *__restrict__ pre, const T *corr,
-                                     volatile int *corr_ready, const T *gcoef, T *coef,
-                                     uint64_t *mb, uint32_t &phase, double *mu_out, int *err) {
-    // pre[] holds zeros for padding coordinates l >= nb, which give mu = 0 whatever the
-    // correction sum (also a non-finite one: fmin / fmax return the other operand), so
-    // panels run all 32 steps without branches.  B is a compile-time constant, so that every coefficient address
-    // below is the lane index plus an immediate offset.
+__device__ void phase_b_cta0(int64_t nbatch, int64_t m, const T *preb, const T *coefb,
+                             const T *gX, unsigned long long nA, unsigned char *work,
+                             uint64_t *mb, uint64_t *mbpre, int *prog, int *corr_prog,
+                             SweepScratch scr) {
     constexpr int B = NS * 32;
     constexpr int NBUF = panel_bufs(B);
-    const int lane = threadIdx.x & 31;
-    const int npan = (nb + 31) / 32;
-    int issued = npan < NBUF ? npan : NBUF;  // panels whose copies have been started
-    bool bad = false;
-    int lost = -1;  // first panel whose data did not arrive
-    // the step constants land on mb[NS]
-    const bool pre_ok = mbar_wait(&mb[NS], (phase >> NS) & 1u, err);
-    if (pre_ok) phase ^= 1u << NS;
-    if (!pre_ok) {  // give up: wait (bounded) for the copies still in flight
-        for (int s = 0; s < issued; s++)
-            if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
-                phase ^= 1u << (s % NBUF);
-        if (mbar_wait(&mb[NS], (phase >> NS) & 1u, err, false)) phase ^= 1u << NS;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T *scoef = reinterpret_cast<T *>(work);
+    T *spre = scoef + coef_area(B);  // [2][PRE_N][B]
+    T *scorr = spre + 2 * PRE_N * B;
+    double *smu = reinterpret_cast<double *>(work + phase_b_steps_offset<T>(B));
+    int *err = scr.err;
+    auto nb_of = [&](int64_t k) -> int {
+        const int64_t s0 = k * B;
+        return s0 < m ? (int)((m - s0) < B ? (m - s0) : B) : 0;
+    };
+
+    if (warp == 0) {  // ---- the chain ----
+        uint32_t phase = 0, pphase = 0;
+        for (int64_t k = 0; k < nbatch; k++) {
+            const int nb = nb_of(k);
+            const int pb = (int)(k & 1);
+            const T *pre = spre + (size_t)pb * PRE_N * B;
+            double *mu_g = scr.mu + (size_t)pb * B;
+            double *mu_s = smu + (size_t)pb * B;
+            if (!mbar_wait(&mbpre[pb], (pphase >> pb) & 1u, err)) return;
+            pphase ^= 1u << pb;
+            // pre[] holds zeros for padding coordinates l >= nb, which give mu = 0 whatever
+            // the correction sum (also a non-finite one: fmin / fmax return the other
+            // operand), so panels run all 32 steps without branches
+            T acc[NS];  // correction sums: the in-batch steps of earlier panels, then the
+                        // carried part, added when the panel starts
+#pragma unroll
+            for (int s = 0; s < NS; s++) acc[s] = T(0);
+            bool bad = false;
+#pragma unroll
+            for (int s = 0; s < NS; s++) {
+                if (s * 32 >= nb) break;
+                const int bi = s % NBUF;
+                if (!mbar_wait(&mb[bi], (phase >> bi) & 1u, err)) return;
+                phase ^= 1u << bi;
+                if (k > 0) {
+                    if (wait_flag(corr_prog, (int)(k * NS) + s + 1, err, 0) < 0) return;
+                    acc[s] += scorr[s * 32 + lane];
+                }
+                const int lo = s * 32 + lane;
+                const T vph = pre[PRE_VPH * B + lo], vpl = pre[PRE_VPL * B + lo];
+                const T vmh = pre[PRE_VMH * B + lo], vml = pre[PRE_VML * B + lo];
+                const T ai = pre[PRE_AI * B + lo], mc = pre[PRE_MC * B + lo];
+                // the two branch values of this lane's coordinate with the corrections so far
+                T xp = fma(-acc[s], ai, vph) + vpl;
+                T xm = fma(-acc[s], ai, vmh) + vml;
+                T mymu = T(0);
+                // Steps are unrolled by four only: fully unrolled, the batch is tens of
+                // kilobytes of straight-line code that the instruction cache has to bring back
+                // for every batch.  col points at column l of the packed coefficients,
+                // col[l2] = coef(l2, l), l2 > l.
+                const T *col = scoef + panel_off(s, B) - 32 * s - 1;
+#pragma unroll 4
+                for (int o = 0; o < 32; o++) {
+                    const int l = s * 32 + o;
+                    const T y = (lane > o) ? ai * col[lane > o ? lo : l + 1] : T(0);
+                    const T cand = fmax(xp, fmin(xm, mc));
+                    const T mu = __shfl_sync(0xffffffffu, cand, o);
+                    mymu = (lane == o) ? cand : mymu;
+                    xp = fma(-y, mu, xp);
+                    xm = fma(-y, mu, xm);
+#pragma unroll
+                    for (int s2 = s + 1; s2 < NS; s2++)
+                        acc[s2] = fma(col[s2 * 32 + lane], mu, acc[s2]);
+                    col += B - l - 2;  // colbase(l + 1) - (l + 1) - 1 = colbase(l) - l - 1 + (B - l - 2)
+                }
+                if (lo < nb) {
+                    double mv = (double)mymu;
+                    if (!isfinite(mv)) {
+                        bad = true;
+                        mv = 0.0;
+                    }
+                    mu_g[lo] = mv;
+                    mu_s[lo] = mv;
+                }
+                __syncwarp();  // the panel's steps stored and its buffer read
+                if (lane == 0) st_release_cta(prog, (int)(k * NS) + s + 1);
+            }
+            if (bad) set_err(err, DEV_NONFINITE);
+        }
         return;
     }
-    // correction sums: the in-batch steps of earlier panels, then, when panel s starts, the
-    // part the previous batch carries into it (corr, formed by the CTA's other warps)
-    T acc[NS];
-#pragma unroll
-    for (int s = 0; s < NS; s++) acc[s] = T(0);
-#pragma unroll
-    for (int s = 0; s < NS; s++) {
-        if (s * 32 >= nb) break;
-        // the coefficients of panel s (columns 32 s .. 32 s + 31) land on its buffer's mbarrier
-        const int bi = s % NBUF;
-        if (!mbar_wait(&mb[bi], (phase >> bi) & 1u, err)) {
-            lost = s;
-            break;
-        }
-        phase ^= 1u << bi;
-        if (!wait_block_flag(corr_ready, s + 1, err)) {
-            lost = s + 1;  // panel s's copy has landed
-            break;
-        }
-        acc[s] += corr[s * 32 + lane];
-        const int lo = s * 32 + lane;
-        const T vph = pre[PRE_VPH * B + lo], vpl = pre[PRE_VPL * B + lo];
-        const T vmh = pre[PRE_VMH * B + lo], vml = pre[PRE_VML * B + lo];
-        const T ai = pre[PRE_AI * B + lo], mc = pre[PRE_MC * B + lo];
-        // the two branch values of this lane's coordinate with the corrections so far
-        T xp = fma(-acc[s], ai, vph) + vpl;
-        T xm = fma(-acc[s], ai, vmh) + vml;
-        T mymu = T(0);
-        // Steps are unrolled by four only: fully unrolled, the batch is tens of kilobytes of
-        // straight-line code that the instruction cache has to bring back for every batch.
-        // col points at column l of the packed coefficients, col[l2] = coef(l2, l), l2 > l.
-        const T *col = coef + panel_off(s, B) - 32 * s - 1;
-#pragma unroll 4
-        for (int o = 0; o < 32; o++) {
-            const int l = s * 32 + o;
-            const T y = (lane > o) ? ai * col[lane > o ? lo : l + 1] : T(0);
-            const T cand = fmax(xp, fmin(xm, mc));
-            const T mu = __shfl_sync(0xffffffffu, cand, o);
-            mymu = (lane == o) ? cand : mymu;
-            xp = fma(-y, mu, xp);
-            xm = fma(-y, mu, xm);
-#pragma unroll
-            for (int s2 = s + 1; s2 < NS; s2++) acc[s2] = fma(col[s2 * 32 + lane], mu, acc[s2]);
-            col += B - l - 2;  // colbase(l + 1) - (l + 1) - 1 = colbase(l) - l - 1 + (B - l - 2)
-        }
-        if (lo < nb) {
-            double m = (double)mymu;
-            if (!isfinite(m)) { bad = true; m = 0.0; }
-            mu_out[lo] = m;
-        }
-        if (issued < npan) {  // this panel's buffer is free: bring in panel s + NBUF
-            __syncwarp();
-            if (lane == 0) {
+
+    if (warp == kWarps - 1) {  // ---- the feeder ----
+        if (lane != 0) return;
+        int nuse[NBUF > 2 ? NBUF : 2] = {};  // copies issued into each panel buffer
+        int npre[2] = {0, 0};
+        bool ok = true;
+        int64_t published = 0;  // batches whose steps are published
+        auto publish_upto = [&](int64_t done) {  // batches 0 .. done - 1 are complete
+            if (done > published) {
+                __threadfence();
+                red_release_add(&scr.bar->mu_ready, (unsigned long long)(done - published));
+                published = done;
+            }
+        };
+        for (int64_t k = 0; k < nbatch && ok; k++) {
+            const int nb = nb_of(k), npan = (nb + 31) / 32;
+            const int pb = (int)(k & 1);
+            if (k > 0 && !wait_counter(&scr.bar->a_done, (unsigned long long)k * nA, err)) break;
+            // the step constants' buffer was last read by batch k - 2
+            if (k >= 2) {
+                const int v = wait_flag(prog, (int)((k - 1) * NS), err, 64);
+                if (v < 0) break;
+                publish_upto(v / NS);
+            }
+            fence_proxy_async();
+            mbar_expect_tx(&mbpre[pb], (uint32_t)(PRE_N * B * sizeof(T)));
+            bulk_load(spre + (size_t)pb * PRE_N * B, preb + (size_t)pb * PRE_N * B,
+                      (uint32_t)(PRE_N * B * sizeof(T)), &mbpre[pb]);
+            npre[pb]++;
+            const T *gcoef = coefb + (size_t)pb * coef_slots(B);
+            for (int s = 0; s < npan; s++) {
+                // the panel that last occupied this buffer: number k NS + s - NBUF
+                const int64_t prev = k * NS + s - NBUF;
+                if (prev >= 0) {
+                    const int v = wait_flag(prog, (int)prev + 1, err, 64);
+                    if (v < 0) {
+                        ok = false;
+                        break;
+                    }
+                    publish_upto(v / NS);
+                }
                 fence_proxy_async();
-                issue_panel<T, NS>(issued, gcoef, coef, mb);
+                issue_panel<T, NS>(s, gcoef, scoef, mb);
+                nuse[s % NBUF]++;
             }
-            issued++;
+            if (ok && k >= 1) {  // batch k - 1 (whose last panels a short batch k skips)
+                const int v = wait_flag(prog, (int)(k * NS), err, 64);
+                if (v < 0) break;
+                publish_upto(v / NS);
+            }
         }
+        if (ok) {  // the last batch's steps
+            const int last = (int)((nbatch - 1) * NS) + (nb_of(nbatch - 1) + 31) / 32;
+            if (wait_flag(prog, last, err, 64) >= 0) publish_upto(nbatch);
+        }
+        // the copies still in flight land before the CTA may leave (bounded)
+        for (int b = 0; b < NBUF; b++)
+            if (nuse[b] > 0) mbar_wait(&mb[b], (uint32_t)(nuse[b] - 1) & 1u, err, false);
+        for (int b = 0; b < 2; b++)
+            if (npre[b] > 0) mbar_wait(&mbpre[b], (uint32_t)(npre[b] - 1) & 1u, err, false);
+        return;
     }
-    if (lost >= 0) {  // the pass is abandoned; wait (bounded) for the copies still in flight
-        for (int s = lost; s < issued; s++)
-            if (mbar_wait(&mb[s % NBUF], (phase >> (s % NBUF)) & 1u, err, false))
-                phase ^= 1u << (s % NBUF);
-    }
-    if (bad) set_err(err, DEV_NONFINITE);
-}
 
-// Starts (one thread) the bulk copies of a batch's step constants (landing on mb[NS]) and of
-// its coefficient panels that the buffers hold (panel s on mb[s % buffers]) into shared
-// memory.  The sources were written by other CTAs, ordered before this point by the wait
-// for their phase A; the destination was last read through the generic proxy.
-template <typename T, int NS>
-__device__ __forceinline__ void phase_b_issue(int nb, const T *gcoef, const T *gpre, T *scoef,
-                                              T *spre, uint64_t *mb) {
-    constexpr int B = NS * 32;
-    fence_proxy_async();
-    mbar_expect_tx(&mb[NS], (uint32_t)(PRE_N * B * sizeof(T)));
-    bulk_load(spre, gpre, (uint32_t)(PRE_N * B * sizeof(T)), &mb[NS]);
-    for (int s = 0; s * 32 < nb && s < panel_bufs(B); s++) issue_panel<T, NS>(s, gcoef, scoef, mb);
-}
-
-// Warps 1 .. kWarps - 1 of CTA 0 during phase B of batch k: the corrections that batch k - 1
-// carries into batch k, corr[l] = sum_{l'} X(k, k-1)[l][l'] mu_{l'} (the missing part of the
-// dot products phase A of batch k formed while batch k - 1's steps were not yet applied),
-// panel by panel, raising *ready to s + 1 when the 32 rows of panel s are in corr; rows of
-// padding coordinates get zero.  X = nullptr: nothing carried (the first batch).
-template <typename T, int NS>
-__device__ void carried_corrections(int nb, const T *X, const double *mu_prev, int nbp, T *corr,
-                                    volatile int *ready) {
-    constexpr int B = NS * 32;
-    constexpr int NW = kWarps - 1;
+    // ---- the corrections: warps 1 .. kWarps - 2 ----
+    constexpr int NW = kWarps - 2;
     constexpr int RW = (32 + NW - 1) / NW;  // rows of a panel per warp
-    const int lane = threadIdx.x & 31, w = (threadIdx.x >> 5) - 1;
-    T muv[NS];
-#pragma unroll
-    for (int kk = 0; kk < NS; kk++) {
-        const int l1 = lane + 32 * kk;
-        muv[kk] = (X && l1 < nbp) ? (T)__ldcg(mu_prev + l1) : T(0);
-    }
-    for (int s = 0; s * 32 < nb; s++) {
+    const int w = warp - 1;
+    __shared__ int s_ok1, s_ok2;
+    for (int64_t k = 1; k < nbatch; k++) {
+        const int nb = nb_of(k), nbp = nb_of(k - 1);
+        const T *X = gX + (size_t)(k & 1) * B * B;
+        // X(k, k-1) is complete with the other CTAs' phase A of batch k
+        if (threadIdx.x == 32) s_ok1 = wait_counter(&scr.bar->a_done, (unsigned long long)k * nA, err);
+        bar_sync_n(kBarCorr, NW * 32);
+        if (!s_ok1) return;
         T x[RW][NS];
+        auto load_panel = [&](int s) {
 #pragma unroll
-        for (int r = 0; r < RW; r++) {
-            const int l = s * 32 + w + NW * r;
+            for (int r = 0; r < RW; r++) {
+                const int l = s * 32 + w + NW * r;
 #pragma unroll
-            for (int kk = 0; kk < NS; kk++) {
-                const int l1 = lane + 32 * kk;
-                x[r][kk] = (X && w + NW * r < 32 && l < nb && l1 < nbp)
-                               ? __ldcg(X + (size_t)l * B + l1) : T(0);
+                for (int kk = 0; kk < NS; kk++) {
+                    const int l1 = lane + 32 * kk;
+                    x[r][kk] = (w + NW * r < 32 && l < nb && l1 < nbp)
+                                   ? __ldcg(X + (size_t)l * B + l1) : T(0);
+                }
             }
-        }
+        };
+        load_panel(0);
+        // batch k - 1's steps are all in shared memory
+        if (threadIdx.x == 32) s_ok2 = wait_flag(prog, (int)(k * NS), err, 32) >= 0;
+        bar_sync_n(kBarCorr, NW * 32);
+        if (!s_ok2) return;
+        T muv[NS];
+        const double *mu_s = smu + (size_t)((k - 1) & 1) * B;
 #pragma unroll
-        for (int r = 0; r < RW; r++) {
-            const int l = s * 32 + w + NW * r;
-            T acc = T(0);
-#pragma unroll
-            for (int kk = 0; kk < NS; kk++) acc = fma(x[r][kk], muv[kk], acc);
-            acc = warp_sum(acc);
-            if (lane == 0 && w + NW * r < 32) corr[l] = acc;
+        for (int kk = 0; kk < NS; kk++) {
+            const int l1 = lane + 32 * kk;
+            muv[kk] = l1 < nbp ? (T)mu_s[l1] : T(0);
         }
-        bar_sync_n(kBarCorr, NW * 32);  // the panel's rows are all written
-        if (threadIdx.x == 32) {
-            __threadfence_block();
-            *ready = s + 1;
+        for (int s = 0; s * 32 < nb; s++) {
+            if (s > 0) load_panel(s);
+#pragma unroll
+            for (int r = 0; r < RW; r++) {
+                const int l = s * 32 + w + NW * r;
+                T a = T(0);
+#pragma unroll
+                for (int kk = 0; kk < NS; kk++) a = fma(x[r][kk], muv[kk], a);
+                a = warp_sum(a);
+                if (lane == 0 && w + NW * r < 32) scorr[l] = a;
+            }
+            bar_sync_n(kBarCorr, NW * 32);  // the panel's rows are all written
+            if (threadIdx.x == 32) st_release_cta(corr_prog, (int)(k * NS) + s + 1);
         }
     }
-}
-
-// Phase B of batch k on CTA 0.  Thread 0 starts the bulk copies of the batch's step constants
-// and first coefficient panels (their sources were completed by the other CTAs, ordered
-// before this point by the wait for their phase A); warp 0 runs the substitution, starting
-// each panel once its coefficients have landed and its carried corrections are formed by the
-// other warps.  The step constants of padding coordinates (l >= nb) were written in global
-// memory with the batch, so the copies bring whole arrays.  Coefficient slots of padding
-// coordinates are never used by a real coordinate: they only reach the correction sums of
-// padding coordinates.
-template <typename T, int NS>
-__device__ void phase_b(int nb, const T *gcoef, const T *gpre, const T *X, const double *mu_prev,
-                        int nbp, T *scoef, T *spre, uint64_t *mb, uint32_t &phase, double *mu,
-                        int *err, volatile int *s_ready) {
-    constexpr int B = NS * 32;
-    T *scorr = spre + PRE_N * B;
-    if (threadIdx.x == 0) {
-        *s_ready = 0;
-        phase_b_issue<T, NS>(nb, gcoef, gpre, scoef, spre, mb);
-    }
-    __syncthreads();  // the flag is reset before the other warps raise it
-    if ((threadIdx.x >> 5) == 0)
-        forward_substitution<T, NS>(nb, spre, scorr, s_ready, gcoef, scoef, mb, phase, mu, err);
-    else
-        carried_corrections<T, NS>(nb, X, mu_prev, nbp, scorr, s_ready);
-    __syncthreads();
 }
 
 // 16-byte vector of the cache type
@@ -609,9 +694,9 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 6];
     __shared__ StepHead<T> s_head[2];  // the scalar part of the two coordinates' constants
-    __shared__ uint64_t s_mb[NS + 2];  // phase B (CTA 0): panels, step constants, corrections
+    __shared__ uint64_t s_mb[NS + 2];  // phase B (CTA 0): panel buffers, two step-constant buffers
     __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
-    uint32_t mb_phase = 0, ring_phase = 0;
+    uint32_t ring_phase = 0;
     unsigned bar_round = 0;  // grid barriers passed (every CTA of the group passes the same)
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
@@ -803,30 +888,19 @@ lambda_pass(int64_t q, const T *__restrict__ Sig, const T *__restrict__ Psi,
     store_batch(breg, nb0, s0m.sa, s0m.sb, s0m.sseg, s0m.snseg);
     // prologue: phase A of batch 0 by every CTA; nothing carried into it
     phase_a(s0m, nb0, preb, coefb, nullptr, 0, gX, 0);
+    __shared__ int s_prog, s_corr_prog;  // CTA 0: phase B's progress flags
     if (bid == 0 && threadIdx.x == 0) {
         for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
         mbar_init_fence();
+        s_prog = 0;
+        s_corr_prog = 0;
     }
     if (!grid_sync(scr.bar, scr.err, nblk, bar_round)) return;
     const unsigned long long nA = nblk - 1;
 
     if (bid == 0) {  // ---- phase B of every batch ----
-        __shared__ int s_ready;  // panels whose carried corrections are formed
-        for (int64_t k = 0; k < nbatch; k++) {
-            if (k > 0 && !cta_wait_counts(&scr.bar->a_done, (unsigned long long)k * nA, nullptr,
-                                          0, scr.err))
-                return;
-            const size_t par = (size_t)(k & 1);
-            phase_b<T, NS>(nb_of(k), coefb + par * coef_slots(B), preb + par * PRE_N * B,
-                           k > 0 ? gX + par * B * B : nullptr, scr.mu + (1 - par) * B,
-                           k > 0 ? nb_of(k - 1) : 0, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase,
-                           scr.mu + par * B, scr.err, &s_ready);
-            if (threadIdx.x == 0) {  // batch k's steps are published
-                __threadfence();
-                red_release_add(&scr.bar->mu_ready, 1ull);
-            }
-        }
+        phase_b_cta0<T, NS>(nbatch, m, preb, coefb, gX, nA, work, s_mb, s_mb + NS, &s_prog,
+                            &s_corr_prog, scr);
         return;
     }
 
@@ -977,9 +1051,9 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[kWarps * 2];
     __shared__ StepHead<T> s_head[2];
-    __shared__ uint64_t s_mb[NS + 2];  // phase B (CTA 0): panels, step constants, corrections
+    __shared__ uint64_t s_mb[NS + 2];  // phase B (CTA 0): panel buffers, two step-constant buffers
     __shared__ uint64_t s_ring[kMaxStages];  // phase A ring
-    uint32_t mb_phase = 0, ring_phase = 0;
+    uint32_t ring_phase = 0;
     unsigned bar_round = 0;  // grid barriers passed (every CTA of the group passes the same)
     constexpr int B = NS * 32;
     if (B_arg != B) return;  // the host launches the instance of its batch size
@@ -1119,30 +1193,19 @@ theta_pass(int64_t p, int64_t q, const T *__restrict__ Sxx, int64_t x0,
     const BatchMeta s0m = slot(0);
     store_batch(breg, nb0, s0m.sa, s0m.sb, s0m.sseg, s0m.snseg);
     phase_a(s0m, nb0, preb, coefb, nullptr, 0, gX, 0);
+    __shared__ int s_prog, s_corr_prog;  // CTA 0: phase B's progress flags
     if (bid == 0 && threadIdx.x == 0) {
         for (int k = 0; k < NS + 2; k++) mbar_init(&s_mb[k], 1);
         mbar_init_fence();
+        s_prog = 0;
+        s_corr_prog = 0;
     }
     if (!grid_sync(scr.bar, scr.err, nblk, bar_round)) return;
     const unsigned long long nA = nblk - 1;
 
     if (bid == 0) {  // ---- phase B of every batch ----
-        __shared__ int s_ready;  // panels whose carried corrections are formed
-        for (int64_t k = 0; k < nbatch; k++) {
-            if (k > 0 && !cta_wait_counts(&scr.bar->a_done, (unsigned long long)k * nA, nullptr,
-                                          0, scr.err))
-                return;
-            const size_t par = (size_t)(k & 1);
-            phase_b<T, NS>(nb_of(k), coefb + par * coef_slots(B), preb + par * PRE_N * B,
-                           k > 0 ? gX + par * B * B : nullptr, scr.mu + (1 - par) * B,
-                           k > 0 ? nb_of(k - 1) : 0, reinterpret_cast<T *>(work),
-                           reinterpret_cast<T *>(work) + coef_area(B), s_mb, mb_phase,
-                           scr.mu + par * B, scr.err, &s_ready);
-            if (threadIdx.x == 0) {  // batch k's steps are published
-                __threadfence();
-                red_release_add(&scr.bar->mu_ready, 1ull);
-            }
-        }
+        phase_b_cta0<T, NS>(nbatch, m, preb, coefb, gX, nA, work, s_mb, s_mb + NS, &s_prog,
+                            &s_corr_prog, scr);
         return;
     }
 
