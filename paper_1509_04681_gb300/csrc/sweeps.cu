@@ -275,8 +275,8 @@ __device__ bool wait_counter(const unsigned long long *c, unsigned long long tar
 //   warp 7, lane 0 (the feeder): for each batch k, once the other CTAs' phase A of batch k
 //     is complete (a_done), the bulk copies of its step constants into one of two buffers and
 //     of each coefficient panel into its buffer as soon as the chain has finished the
-//     panel that last occupied it; and, when the chain has finished batch k - 1, publishes
-//     that batch's steps to the other CTAs (mu_ready).
+//     panel that last occupied it; and, as soon as the chain has finished a batch, also
+//     while it waits, publishes that batch's steps to the other CTAs (mu_ready).
 //   warps 1..6 (the corrections): for each batch k > 0, the part that batch k - 1 carries
 //     into it, corr[l] = sum_{l'} X(k, k-1)[l][l'] mu_{l'} (phase A of batch k ran against the
 //     cache without batch k - 1's steps), panel by panel, raising `corr_prog` (same
@@ -389,7 +389,25 @@ __device__ void phase_b_cta0(int64_t nbatch, int64_t m, const T *preb, const T *
         for (int64_t k = 0; k < nbatch && ok; k++) {
             const int nb = nb_of(k), npan = (nb + 31) / 32;
             const int pb = (int)(k & 1);
-            if (k > 0 && !wait_counter(&scr.bar->a_done, (unsigned long long)k * nA, err)) break;
+            if (k > 0) {  // batch k's phase A; batches the chain completes meanwhile are published
+                const uint64_t t0 = global_ns();
+                for (unsigned it = 1; ld_acquire_u64(&scr.bar->a_done) < (unsigned long long)k * nA;
+                     it++) {
+                    publish_upto(ld_acquire_cta(prog) / NS);
+                    if ((it & 63u) == 0) {
+                        if (ld_acquire_int(err) != 0) {
+                            ok = false;
+                            break;
+                        }
+                        if (global_ns() - t0 > 2000000000ull) {
+                            set_err(err, DEV_TIMEOUT);
+                            ok = false;
+                            break;
+                        }
+                    }
+                }
+                if (!ok) break;
+            }
             // the step constants' buffer was last read by batch k - 2
             if (k >= 2) {
                 const int v = wait_flag(prog, (int)((k - 1) * NS), err, 64);
