@@ -557,7 +557,8 @@ def fp64_leg(ctx, cg, Xd, Yd, pr, p, q, dev, steps, warmup):
             "steps": info["iterations"], "warmup": warmup, "ms_per_step": 1e3 * sec / it,
             "dtype": "f64",
             "per_iteration": {k: info[k] / it for k in ("sec_products", "sec_sweep_lambda",
-                                                          "sec_linesearch", "sec_sweep_theta")},
+                                                          "sec_linesearch", "sec_factor",
+                                                          "sec_sweep_theta")},
             "roofline_lambda_pass": rl, "roofline_theta_pass": rt,
             "gpu_launches": info["launches"]}
 
@@ -704,7 +705,7 @@ def run_large(args):
         "seconds": info["seconds"], "seconds_per_iteration": info["seconds"] / it,
         "per_iteration": {k: info[k] / it for k in ("sec_products", "sec_active",
                                                       "sec_sweep_lambda", "sec_linesearch",
-                                                      "sec_sweep_theta")},
+                                                      "sec_factor", "sec_sweep_theta")},
         "ls_trials": info["ls_trials"], "m_lambda_last": info["m_lambda"],
         "m_theta_last": info["m_theta"], "f": f,
         "subgrad_ratio_at_last_check": info["subgrad"] / max(1e-300, info["l1norm"]),
@@ -796,6 +797,7 @@ def run_cuda(args):
                               "sec_products": info["sec_products"] / max(1, iters),
                               "sec_sweep_lambda": info["sec_sweep_lambda"] / max(1, iters),
                               "sec_linesearch": info["sec_linesearch"] / max(1, iters),
+                              "sec_factor": info["sec_factor"] / max(1, iters),
                               "sec_sweep_theta": info["sec_sweep_theta"] / max(1, iters),
                               "coords_per_s": (info["coords_lambda"] + info["coords_theta"]) /
                               max(1e-9, info["sec_sweep_lambda"] + info["sec_sweep_theta"])},

@@ -94,11 +94,12 @@ typedef struct {
     int ls_trials;          /* Armijo trials summed over iterations                      */
     double seconds;         /* device time of the solve (CUDA events)                    */
     double sec_products;    /* R, P, Psi, gradients                                      */
-    double sec_factor;      /* Cholesky, log det, Sigma                                  */
+    double sec_factor;      /* Sigma from the accepted step's factor, and W for the Theta */
+                            /* pass (the Armijo trials' factorisations: sec_linesearch)   */
     double sec_active;      /* subgradient, active sets                                  */
-    double sec_sweep_lambda;
-    double sec_linesearch;
-    double sec_sweep_theta;
+    double sec_sweep_lambda;  /* the Lambda pass                                         */
+    double sec_linesearch;    /* Armijo: trial factorisations and objectives             */
+    double sec_sweep_theta;   /* the Theta pass                                          */
     int64_t launches;       /* CUDA kernels this library launched during the call        */
     int64_t coords_lambda;  /* coordinate steps taken by all Lambda passes of the call   */
     int64_t coords_theta;   /* coordinate steps taken by all Theta passes of the call    */

@@ -719,18 +719,21 @@ struct Solver {
                 gemm<double>(false, true, p, q, n, 1.0 / (double)n, P<double>(c->Xt), n,
                              P<double>(c->Pt), n, 1.0, P<double>(c->W), q, st);
             }
+            cudaEventRecord(ev[2], st);  // Sigma and W formed
             CGGM_CUDA_TRY(cudaMemsetAsync(c->dV.p, 0, sizeof(T) * pq, st));
             CGGM_TRY(theta_pass(hc[1], B));
             cudaEventRecord(ev[6], st);
             CGGM_TRY(sync_err(c));
             CGGM_TRY(tc_check());
             {
-                float a, b, d2;
+                float a, b, d1, d2;
                 cudaEventElapsedTime(&a, ev[3], ev[4]);
                 cudaEventElapsedTime(&b, ev[4], ev[5]);
-                cudaEventElapsedTime(&d2, ev[5], ev[6]);
+                cudaEventElapsedTime(&d1, ev[5], ev[2]);
+                cudaEventElapsedTime(&d2, ev[2], ev[6]);
                 t_swl += a * 1e-3;
                 t_ls += b * 1e-3;
+                t_fac += d1 * 1e-3;
                 t_swt += d2 * 1e-3;
             }
         }
