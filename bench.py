@@ -589,13 +589,15 @@ def run_gap_trace(args):
     stream = torch.cuda.current_stream(dev)
     ctx = cg.Context(0, stream=stream.cuda_stream)
     traces = {}
+    budgets = {"fp64": args.gap_fp64 if args.gap_fp64 > 0 else args.gap_trace,
+               "mixed": args.gap_trace}
     for name, prec in (("fp64", cg.CGGM_FP64), ("mixed", cg.CGGM_MIXED)):
         L = torch.empty((q, q), device=dev, dtype=torch.float64)
         T = torch.empty((p, q), device=dev, dtype=torch.float64)
         t_dev, its, first = 0.0, 0, True
         rows = []
         with Clocks(0) as clk:
-            while t_dev < args.gap_trace:
+            while t_dev < budgets[name]:
                 kw = {} if first else {"warm_Lambda": L, "warm_Theta": T}
                 r = ctx.cggm_solve_dense(Xd, Yd, pr.lam_L, pr.lam_T, tol=1e-12,
                                    opts=cg.make_opts(precision=prec, max_iter=args.gap_chunk),
@@ -623,7 +625,7 @@ def run_gap_trace(args):
         if d1 < 0 and d2 < 0 and abs(d2) < abs(d1):
             f_star = f3 - d2 * d2 / (d2 - d1)
     out = {"gap_trace": {"workload": WORKLOAD, "p": p, "q": q, "n": n, "lambda": pr.lam_L,
-                         "budget_s_per_path": args.gap_trace, "chunk": args.gap_chunk,
+                         "budget_s": budgets, "chunk": args.gap_chunk,
                          "f_best": f_best, "f_star_extrapolated": f_star}}
     for name, t in traces.items():
         rows = t["rows"]
@@ -865,6 +867,8 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--sweep-batch", type=int, default=0,
                     help="coordinates per blocked Gauss-Seidel batch (0: the library default)")
+    ap.add_argument("--gap-fp64", type=float, default=0.0,
+                    help="device-time budget of the FP64 path in --gap-trace (default: the same)")
     ap.add_argument("--gap-trace", type=float, default=0.0,
                     help="seconds of device time per precision: record f against time on the "
                          "5000 x 5000 workload instead of the default line")

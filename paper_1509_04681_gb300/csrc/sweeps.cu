@@ -43,10 +43,12 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kRowsInFlight = 5;
 // Phase A: rows per CTA held at once, chunks in flight, bytes per row and chunk.
 constexpr int kRingRows = 10;
-constexpr int kChunkBytes = 4096;
+constexpr int kChunkBytes = 8192;
 // The ring holds as many stages of the plan's rows as fit in kRingBytes, up to kMaxStages
-// (three stages of ten rows; more of fewer rows).  A larger ring (200 KB) was slower: the
-// shared memory it takes comes out of the L1 cache that the coefficient gathers use.
+// (two stages of ten rows, three of seven; more of fewer rows).  Measured on the 5000 x 5000
+// workload: 8 KB chunks in 168 KB took 0.66 s per Lambda pass against 0.72 s with 4 KB in
+// 120 KB (fewer, larger copies) and 0.70 s with 16 KB chunks; a larger ring costs L1 cache,
+// which the coefficient gathers use (the Theta pass, 0.61 s, barely moves).
 constexpr int kMaxStages = 16;
 // Phase A: warps 0 .. kDotWarps - 1 compute the dot products (through the ring) while the
 // other warps form the coefficients; the dot warps synchronise among themselves on named
@@ -72,7 +74,7 @@ __device__ __forceinline__ bool bar_and_n(int id, int n, bool p) {
         : "memory");
     return r != 0;
 }
-constexpr size_t kRingBytes = (size_t)3 * kRingRows * kChunkBytes;
+constexpr size_t kRingBytes = (size_t)168 << 10;
 
 __device__ __forceinline__ void set_err(int *err, int code) { atomicCAS(err, 0, code); }
 
