@@ -15,9 +15,9 @@ carried corrections read X(k, k-1) and the steps of batch k-1; phase C of batch 
 k's steps; no buffer is overwritten while a reader still needs it.  A planted mistake (a
 feeder that does not wait for a panel buffer to be released, phase C that does not wait for
 every phase A, corrections formed before the previous batch's steps are all in) must be
-caught.  compute-sanitizer is closed on this machine, so this model
-is the race check of the protocol; the kernels' outputs are checked against the oracle by
-the GPU tests.
+caught.  This model is the race check of the protocol (no memory
+checker runs the kernels); the kernels' outputs are checked against the oracle by the GPU
+tests.
 """
 import random
 
