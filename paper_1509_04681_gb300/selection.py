@@ -14,7 +14,10 @@ This module provides those steps:
                        are solved along the path with warm starts, and the held-out rows score
                        each point by the smooth part of Eq. 1 (cggm_objective with zero
                        penalties: the held-out negative log-likelihood up to constants);
-  support_f1           precision, recall and F1 of the recovered support against a true one.
+  support_f1           precision, recall and F1 of the recovered support against a true one;
+  recovery_versus_n    the edge-recovery study: at each sample size n, samples from the true
+                       model, penalties matched to the true edge counts, and the F1 of the
+                       recovered supports of Lambda and Theta.
 """
 from __future__ import annotations
 
@@ -148,3 +151,37 @@ def support_f1(est, true, threshold: float = 0.0, upper: bool = False) -> Suppor
     recall = tp / nr if nr else 1.0
     f1 = 2 * precision * recall / (precision + recall) if precision + recall > 0 else 0.0
     return SupportScore(precision, recall, f1, nr, nf)
+
+
+@dataclasses.dataclass
+class RecoveryPoint:
+    n: int
+    lam_L: float
+    lam_T: float
+    lambda_support: SupportScore  # off-diagonal pairs i < j of Lambda
+    theta_support: SupportScore
+    solves: int
+
+
+def recovery_versus_n(ctx, sample, Lambda_true, Theta_true, ns: Sequence[int], seed: int = 0,
+                      tol: float = 0.01, opts=None, **edge_kw) -> list:
+    """The edge-recovery study of Section 5 (Fig. 7): for each sample size n in ns, draw n
+    samples of the true model with sample(n, rng) -> (X, Y), choose lambda_Lambda and
+    lambda_Theta whose solution has the true numbers of edges (lambdas_for_edges, the
+    paper's choice of penalties), and score the recovered supports of Lambda (pairs i < j)
+    and Theta against the true ones (support_f1).  Lambda_true and Theta_true are dense or
+    sparse (with .toarray()); edge_kw passes the bracket and rounds to lambdas_for_edges.
+    One seeded generator draws every n's samples in turn."""
+    Lt = Lambda_true.toarray() if hasattr(Lambda_true, "toarray") else np.asarray(Lambda_true)
+    Tt = Theta_true.toarray() if hasattr(Theta_true, "toarray") else np.asarray(Theta_true)
+    target_L = int(np.count_nonzero(np.triu(Lt, 1)))
+    target_T = int(np.count_nonzero(Tt))
+    rng = np.random.default_rng(seed)
+    points = []
+    for n in ns:
+        X, Y = sample(int(n), rng)
+        m = lambdas_for_edges(ctx, X, Y, target_L, target_T, tol=tol, opts=opts, **edge_kw)
+        points.append(RecoveryPoint(int(n), m.lam_L, m.lam_T,
+                                    support_f1(m.result.Lambda, Lt, upper=True),
+                                    support_f1(m.result.Theta, Tt), m.solves))
+    return points
