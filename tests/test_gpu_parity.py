@@ -327,6 +327,20 @@ def test_solve_rejects_bad_input(ctx):
     assert e.value.status == -8
 
 
+def test_solve_line_search_exhaustion(ctx):
+    """Forced line-search exhaustion (pinned on the oracle: with sigma = 1 a full step never
+    meets the Armijo rule, the objective being strictly convex along the direction): one
+    trial gives CGGM_ELINESEARCH, and the context stays usable."""
+    pr = problem(6, 5, 40, seed=13)
+    o = cg.make_opts(precision=cg.CGGM_FP64, ls_sigma=1.0, ls_max_trials=1, max_iter=3)
+    with pytest.raises(cg.CGGMError) as e:
+        ctx.cggm_solve(pr.X, pr.Y, 0.1, 0.1, tol=1e-8, opts=o)
+    assert e.value.status == cg.CGGM_ELINESEARCH
+    r = ctx.cggm_solve(pr.X, pr.Y, 0.1, 0.1, tol=1e-8,
+                       opts=cg.make_opts(precision=cg.CGGM_FP64, max_iter=3))
+    assert np.all(np.isfinite(r.Lambda)) and r.info["iterations"] >= 1
+
+
 def test_device_inputs(ctx):
     torch = pytest.importorskip("torch")
     pr = problem(30, 20, 40, seed=12)

@@ -357,3 +357,15 @@ def test_prediction_at_lambda_zero_is_the_least_squares_fit():
     assert B1[0, 0] == -1.5 and np.allclose(Yh[:, 0], [-1.5, 3.0])
     with pytest.raises(oracle.NotPositiveDefinite):
         oracle.predict(X, -np.eye(4), r.Theta)
+
+
+def test_full_step_never_meets_sigma_one():
+    """Forced line-search exhaustion: the smooth part of Eq. 1 is strictly convex along the
+    Newton direction, so at alpha = 1 the objective lies strictly above f + delta (its
+    linearisation plus the exact l1 change); with sigma = 1 and a single trial the Armijo
+    rule must fail, while the default sigma accepts a step on the same problem."""
+    X, Y = small_problem(6, 5, 40, seed=13)
+    with pytest.raises(oracle.LineSearchFailed):
+        oracle.solve(X, Y, 0.1, 0.1, tol=1e-8, max_iter=3, sigma=1.0, ls_max_trials=1)
+    r = oracle.solve(X, Y, 0.1, 0.1, tol=1e-8, max_iter=3)
+    assert r.history[0].trials >= 1 and r.history[0].alpha > 0
