@@ -19,9 +19,10 @@ seconds, and the oracle's CPU rate on a bounded sample.  With --gpus N (torchrun
 solves an independent replica (another seed): the solve does not shard.
 
 Other modes: --gap-trace S records f against device time for both precisions on the
-5000 x 5000 workload (S seconds each); --large K runs K iterations of the 40000 x 20000
-workload with a KKT check; --serve runs the served paths alone; --profile-sweep and
---profile-contract are the bounded cases of the ncu captures.
+5000 x 5000 workload (S seconds each; --gap-fp64 S2 gives the FP64 path its own budget);
+--large K runs K iterations of the 40000 x 20000 workload with a KKT check; --serve runs the
+served paths alone; --profile-sweep, --profile-theta and --profile-contract are the bounded
+cases of the ncu captures; --profile-chol times the FP64 factorisation against cuBLAS DGEMM.
 
 --impl reference times the CPU oracle (the plain double-precision restatement of the
 method) on a bounded sample of the same workload and prints the same kind of line.
